@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Benchmark: exact multiplication of two 2^24-digit decimal integers on one GB300.
+
+One step = one product of two seeded random 2^24-digit operands (1,864,136 base-10^9 limbs each)
+through the full path: forward column pass, fused row pass, inverse column pass with CRT, carry
+scan.  Operands are resident in HBM before the timed region; L2 is flushed (a 512 MiB write)
+between timed steps, outside the per-step events.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the paper has no runnable code) on host cores on the
+same workload.  Under torchrun (N > 1) every rank runs an independent replica (the path does
+not shard), value = all ranks' digits / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "product digits/s"
+WORKLOAD = "2^24 x 2^24-digit random multiplication (base-10^9 uint32 limbs)"
+DIGITS = 1 << 24
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------------
+# work model (algorithmic modular multiplications and bytes per kernel launch)
+# ----------------------------------------------------------------------------------------------
+def _dft_mults(R: int) -> int:
+    """Nontrivial constant multiplications of one in-register R-point DFT (radix-2 DIF network
+    with the factor-1 butterflies peeled, Sec. 5.6; radix 3: one)."""
+    if R == 3:
+        return 1
+    n, h, total = R, R // 2, 0
+    while h >= 1:
+        total += (n // (2 * h)) * (h - 1)
+        h //= 2
+    return total
+
+
+def _transform_mults(n: int, radices: list[int]) -> float:
+    """Constant multiplications of one length-n transform with the given stage radices
+    (DFT constants + inter-stage twiddles of every stage with m > R)."""
+    m, tot = n, 0.0
+    for R in radices:
+        tot += (n // R) * _dft_mults(R)
+        if m > R:
+            tot += n * (R - 1) / R
+        m //= R
+    return tot
+
+
+def work_model(info, nx: int, ny: int, square: bool) -> dict:
+    N, N1, N2 = info.N, info.N1, info.N2
+    cr = [r for r in info.col_radix if r]
+    rr = [r for r in info.row_radix if r]
+    L = nx + ny
+    ops = 1 if square else 2
+    Rs = cr[-1]
+    col = (N2 * _transform_mults(N1, cr) + N * (2 - 1 / Rs))  # + four-step twiddles
+    row_t = N1 * _transform_mults(N2, rr)
+    k = {}
+    # Shoup products: 3 IMAD each; Montgomery products: 4 IMAD each
+    k["col_fwd"] = {"imad": 3 * 3 * ops * col, "bytes": 4 * (nx + (0 if square else ny)) + 4 * 3 * N * ops}
+    k["row_mul"] = {"imad": 3 * (3 * (ops + 1) * row_t) + 4 * 3 * N,
+                    "bytes": 4 * 3 * N * (ops + 1)}
+    k["col_inv_crt"] = {"imad": 3 * 3 * col + L * (3 * 4 + 2 * 6), "bytes": 4 * 3 * N + 4 * L + 8 * (L // 32)}
+    k["carry_scan"] = {"imad": 0.0, "bytes": 8 * L + 8 * (L // 32)}
+    return k
+
+
+# ----------------------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------------------
+def aggregate(total_ms_local: float, digits_per_step: int, steps: int, world: int, device=None):
+    """Replicas: every rank ran `steps` independent products.  Whole-job value = all ranks'
+    digits / the slowest rank's time (max over ranks).  Returns (value, max_total_ms)."""
+    total_ms = total_ms_local
+    if world > 1:
+        import torch
+        t = torch.tensor([total_ms_local], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return digits_per_step * steps * world / (total_ms * 1e-3), total_ms
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_11524_gb300 import dmul as d
+    from paper_2011_11524_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    x_np, y_np = wl.c2_random_pair(DIGITS)
+    nx, ny = len(x_np), len(y_np)
+    L = nx + ny
+    ctx = d.Context(local, flags=d.DMUL_FLAG_STAGE_TIMING)
+    stream = torch.cuda.Stream(device=dev)
+    x = d.to_device(x_np, dev)
+    y = d.to_device(y_np, dev)
+    z = torch.empty(L, dtype=torch.int32, device=dev)
+    nz = torch.zeros(1, dtype=torch.int64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    sptr = stream.cuda_stream
+
+    def step():
+        rc = d.dmul_mul(ctx.handle, x, nx, y, ny, z, L, nz, sptr)
+        if rc:
+            raise d.DmulError(rc, "dmul_mul")
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        rc = d.dmul_sync(ctx.handle, sptr)
+        if rc:
+            raise d.DmulError(rc, "warmup")
+        ctx.stage_times()  # drop warm-up stage timings
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        clk = clocks.stop()
+    rc = d.dmul_sync(ctx.handle, sptr)
+    if rc:
+        raise d.DmulError(rc, "timed region")
+    stages = ctx.stage_times()
+    digits_per_step = 2 * DIGITS
+    value, total_ms = aggregate(sum(ms), digits_per_step, args.steps, world, dev)
+    ms_per_step = total_ms / args.steps
+
+    # ---- end to end through the host-buffer entry point (pinned host memory) ----
+    hx = torch.from_numpy(x_np.view(np.int32).copy()).pin_memory()
+    hy = torch.from_numpy(y_np.view(np.int32).copy()).pin_memory()
+    hz = torch.empty(L, dtype=torch.int32).pin_memory()
+    for _ in range(max(1, args.warmup // 2)):
+        rc, _ = d.dmul_mul_host(ctx.handle, hx, nx, hy, ny, hz, L)
+    e2e = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, nzh = d.dmul_mul_host(ctx.handle, hx, nx, hy, ny, hz, L)
+        e2e.append(time.perf_counter() - t0)
+        if rc:
+            raise d.DmulError(rc, "dmul_mul_host")
+    e2e_s = sum(e2e) / len(e2e)
+
+    # ---- roofline of the dominant kernel ----
+    info = d.dmul_get_plan(ctx.handle, L)
+    model = work_model(info, nx, ny, False)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    imad_peak_t = n_sm * 64 * sm_max * 1e6 / 1e12  # T IMAD/s at the maximum SM clock
+    dom = max((k for k in stages if k in model), key=lambda k: stages[k][0])
+    dms = stages[dom][0] / max(1, stages[dom][1])
+    imad_t = model[dom]["imad"] / (dms * 1e-3) / 1e12
+    gbs = model[dom]["bytes"] / (dms * 1e-3) / 1e9
+    if imad_t / imad_peak_t >= gbs / hbm_peak:
+        roof = {"bound": "alu", "achieved": round(imad_t, 3), "peak": round(imad_peak_t, 3),
+                "unit": "TIMAD/s", "frac": round(imad_t / imad_peak_t, 4), "traffic": None,
+                "kernel": dom, "peak_source": f"{n_sm} SMs x 64 IMAD/clk x {sm_max:.0f} MHz (derived)",
+                "hbm_gbs": round(gbs, 1), "hbm_frac_of_measured": round(gbs / hbm_peak, 4)}
+    else:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(gbs / hbm_peak, 4), "traffic": None, "kernel": dom,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                "imad_tps": round(imad_t, 3), "imad_frac": round(imad_t / imad_peak_t, 4)}
+    launches = sum(v[1] for v in stages.values()) // max(1, args.steps)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "digits/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "digits_x": DIGITS, "digits_y": DIGITS, "limbs": [nx, ny],
+                   "N": int(info.N), "split": [int(info.N1), int(info.N2)], "primes": 3,
+                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": "replicas"},
+        "e2e": {"value": digits_per_step / e2e_s * world, "unit": "digits/s",
+                "h2d_bytes_per_step": 4 * (nx + ny), "d2h_bytes_per_step": 4 * L + 8,
+                "ms_per_step": e2e_s * 1e3},
+        "gpu_launches": int(launches) * args.steps,
+        "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in stages.items()},
+        "roofline": roof,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(x_np, y_np, d.to_host(z), budget_s=args.cpu_seconds)
+    ctx.close()
+    return out
+
+
+def cpu_baseline(x, y, z_gpu=None, budget_s=10.0) -> dict:
+    """The CPU oracle (slow two-prime NTT route, as it stands) on the same 2^24-digit product,
+    repeated until about budget_s seconds of CPU work.  Its product also checks, limb by limb, the
+    GPU's result of the last timed step."""
+    import numpy as np
+
+    import oracle
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        ref = oracle.mul_ntt(x, y)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= 8:
+            break
+    out = {"value": 2 * DIGITS * reps / el, "unit": "digits/s", "cores": 1, "kind": "oracle",
+           "sample": f"{reps} full 2^24 x 2^24-digit products by the oracle's two-prime NTT route "
+                     f"({el:.1f} s, single thread)"}
+    if z_gpu is not None:
+        out["gpu_result_matches_oracle"] = bool(np.array_equal(np.asarray(z_gpu), ref))
+    return out
+
+
+def run_reference(args, rank, world, local):
+    """The reference arm: the paper ships no runnable code, so its stand-in is the CPU oracle,
+    timed as it stands on the host cores, on this arm's workload and metric."""
+    if rank != 0:
+        return None
+    import numpy as np  # noqa: F401
+
+    from paper_2011_11524_gb300 import workloads as wl
+    import oracle
+    oracle.build()
+    x, y = wl.c2_random_pair(DIGITS)
+    for _ in range(min(args.warmup, 1)):
+        oracle.mul_ntt(x, y)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.mul_ntt(x, y)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = 2 * DIGITS * len(times) / tot
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "digits/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / len(times) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "none (host CPU)"},
+        "cpu_baseline": {"value": value, "unit": "digits/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{len(times)} full products, single thread"},
+        "e2e": {"value": value, "unit": "digits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = _dist()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world, local)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world, local)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * dmul.h -- C ABI of libdmul: exact multiplication of large decimal integers on one GB300 GPU.
+ *
+ * Method (Krapivensky, "Speeding up decimal multiplication", arXiv 2011.11524):
+ *   the product of x = <x_0..x_{n-1}> and y = <y_0..y_{m-1}> in base B = 10^9 is recovered from the
+ *   cyclic convolution of the zero-padded limb vectors (Sec. 3.2), computed exactly by
+ *   number-theoretic transforms modulo three primes p < 2^30 of the form c*3*2^n + 1 (Sec. 3.5,
+ *   Sec. 4.5) with the matrix-Fourier four-step / six-step decomposition (Sec. 7), a pointwise
+ *   Montgomery product with the linearity trick (Sec. 6), CRT recovery of every coefficient
+ *   (Sec. 8.2.2, extended to three primes) and the decimal carry recurrence (Sec. 3.2,
+ *   eq. sigmai_and_zi), here as a decoupled-lookahead scan.
+ *
+ * Number format (all entry points): little-endian base-10^9 limbs, one uint32_t per limb, each
+ * limb < 10^9.  Leading zero limbs are allowed (the padding of Sec. 3.2).  Zero is nz = 1,
+ * z[0] = 0.
+ *
+ * Pointers: unless a function says "host", limb pointers are DEVICE pointers owned by the
+ * caller, on the context's device.  `stream` is a cudaStream_t passed as void* (NULL = the
+ * legacy default stream).  Device-pointer entry points only enqueue work: they return DMUL_OK
+ * once the work is queued, and device-side errors (an input limb >= 10^9, an expired bounded
+ * wait) are reported by the next dmul_sync() on that context.
+ *
+ * Threading: a context is not thread-safe.  Its device scratch is shared by the calls made on it,
+ * so calls on one context must be issued on one stream (or be otherwise serialized), except the
+ * served entry points dmul_submit / dmul_poll / dmul_wait, which may be called from any thread.
+ *
+ * Errors: every int-returning function returns one of the DMUL_* codes below.
+ */
+#ifndef DMUL_H
+#define DMUL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------------------------- */
+#define DMUL_OK 0
+#define DMUL_ERR_INVALID 1   /* bad argument, a limb >= 10^9, aliasing of z with x or y        */
+#define DMUL_ERR_TOO_LARGE 2 /* n+m exceeds the longest supported transform or max_limbs, or    */
+                             /* (B-1)^2 min(n,m) >= p1 p2 p3 (eq. product_inequality)         */
+#define DMUL_ERR_NOMEM 3     /* the context's HBM budget, or a device allocation, is exhausted   */
+#define DMUL_ERR_TIMEOUT 4   /* a bounded device-side wait expired (the result is not valid)    */
+#define DMUL_ERR_CUDA 5      /* a CUDA runtime call failed                                      */
+#define DMUL_ERR_CAPACITY 6  /* z_cap < nx + ny                                                 */
+#define DMUL_ERR_UNKNOWN_TICKET 7 /* dmul_poll / dmul_wait on a ticket that was never issued    */
+
+/* ---- context ------------------------------------------------------------------------------- */
+typedef struct dmul_ctx dmul_ctx;
+
+#define DMUL_FLAG_SIXSTEP 1u      /* transforms use the six-step decomposition with the in-place */
+                                  /* n x n, n x 2n and 2n x n transposes of Sec. 7.6 instead of   */
+                                  /* the four-step form (Sec. 7.1-7.2); results are identical     */
+#define DMUL_FLAG_STAGE_TIMING 2u /* record CUDA events around each pipeline stage (see          */
+                                  /* dmul_stage_times); adds a little launch overhead             */
+
+typedef struct {
+    int device;                /* CUDA device ordinal                                          */
+    uint64_t hbm_budget_bytes; /* cap on library-owned device memory; 0 = 16 GiB               */
+    uint64_t max_limbs;        /* longest product (nx + ny) the context must accept; 0 = the   */
+                               /* longest transform the primes allow                           */
+    uint32_t flags;            /* DMUL_FLAG_*                                                  */
+} dmul_config;
+
+/* Create a context on cfg->device: checks the prime set against FindPrimes (Sec. 4.5) and the
+ * bound of eq. product_inequality, uploads per-prime constants.  Plans (transform splits,
+ * twiddle tables) are built and cached per transform length on first use.  cfg may be NULL
+ * (device 0, defaults).  *out receives the context, or NULL on error. */
+int dmul_init(dmul_ctx **out, const dmul_config *cfg);
+
+/* Free every device and host resource of the context (synchronizes its device first). */
+void dmul_destroy(dmul_ctx *ctx);
+
+/* Human-readable name of a status code (static string). */
+const char *dmul_strerror(int status);
+
+/* Synchronize `stream` and return the device-side status accumulated by the work enqueued on
+ * this context since the previous dmul_sync (DMUL_OK, DMUL_ERR_INVALID, DMUL_ERR_TIMEOUT), then
+ * clear it.  Returns DMUL_ERR_CUDA if the synchronization itself fails. */
+int dmul_sync(dmul_ctx *ctx, void *stream);
+
+/* ---- the plain form -------------------------------------------------------------------------- */
+/* z = x * y (Sec. 3.2).  x: nx >= 1 limbs, y: ny >= 1 limbs, z: z_cap >= nx + ny limbs, all
+ * device pointers; z must not overlap x or y.  x == y with nx == ny is a squaring (the aliasing
+ * case of Sec. 6) and takes the cheaper dmul_sqr path.  All nx + ny limbs of z are written.
+ * nz (device pointer to one uint64_t, or NULL) receives the normalized length: the index of the
+ * highest nonzero limb + 1, or 1 for a zero product.  Asynchronous on `stream`. */
+int dmul_mul(dmul_ctx *ctx, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny,
+             uint32_t *z, size_t z_cap, uint64_t *nz, void *stream);
+
+/* z = x^2: one forward transform instead of two (Sec. 6, the x aliasing y case).  z_cap >= 2 nx.
+ * Same conventions as dmul_mul. */
+int dmul_sqr(dmul_ctx *ctx, const uint32_t *x, size_t nx, uint32_t *z, size_t z_cap,
+             uint64_t *nz, void *stream);
+
+/* Host-memory convenience: x, y, z and nz are HOST pointers.  Copies the operands to the device
+ * through the context's pinned staging buffers, multiplies, copies z back and synchronizes.
+ * x == y with nx == ny squares.  Returns the full status (including device-side errors). */
+int dmul_mul_host(dmul_ctx *ctx, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny,
+                  uint32_t *z, size_t z_cap, size_t *nz);
+
+/* ---- the batched form -------------------------------------------------------------------------- */
+typedef struct {
+    const uint32_t *x; /* device pointer                                                 */
+    uint64_t nx;
+    const uint32_t *y; /* device pointer; y == x with ny == nx makes the job a squaring   */
+    uint64_t ny;
+    uint32_t *z;       /* device pointer, z_cap >= nx + ny                                */
+    uint64_t z_cap;
+    uint64_t *nz;      /* device pointer or NULL                                          */
+} dmul_job;
+
+/* Run `count` independent multiplications (jobs: HOST array of descriptors holding device
+ * pointers).  Jobs are grouped by transform length; each group runs as batched launches that
+ * process all of its jobs at once, and a repeated batch shape replays a captured CUDA graph.
+ * Results are identical to calling dmul_mul on each job.  Asynchronous on `stream`. */
+int dmul_batch(dmul_ctx *ctx, const dmul_job *jobs, size_t count, void *stream);
+
+/* ---- the served form ------------------------------------------------------------------------- */
+/* Enqueue one job for the context's serving loop (a host thread that continuously batches
+ * pending requests by transform length onto several streams, admitting each request only when
+ * its device footprint fits the context's HBM budget).  The job's pointers are device pointers
+ * that must stay valid until the ticket completes.  *ticket receives an id for dmul_poll /
+ * dmul_wait.  Thread-safe. */
+int dmul_submit(dmul_ctx *ctx, const dmul_job *job, uint64_t *ticket);
+
+/* *done = 1 when the ticket's result is in z (and *nz), else 0.  Thread-safe. */
+int dmul_poll(dmul_ctx *ctx, uint64_t ticket, int *done);
+
+/* Block until the ticket completes; returns its status.  Thread-safe. */
+int dmul_wait(dmul_ctx *ctx, uint64_t ticket);
+
+/* ---- stage-level entry points (each step of the path on its own, for checking) --------------- */
+/* The convolution residues c_k mod p_i (Sec. 3.2 + Sec. 3.3 eq. conv_theorem + Sec. 6) for
+ * k in [0, nx+ny) and the three primes in ascending order: r[i*(nx+ny) + k].  x == y squares.
+ * Same forward transforms, pointwise product and inverse transforms as dmul_mul. */
+int dmul_conv_residues(dmul_ctx *ctx, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny,
+                       uint32_t *r, void *stream);
+
+/* The exact convolution coefficients c_k after CRT (Sec. 8.2.2): c_k = d[3k] + d[3k+1] 10^9 +
+ * d[3k+2] 10^18 with every d < 10^9, k in [0, nx+ny). */
+int dmul_conv_coeffs(dmul_ctx *ctx, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny,
+                     uint32_t *d, void *stream);
+
+/* The carry stage alone (Sec. 3.2, eq. sigmai_and_zi): z = sum_k c_k 10^(9k) for coefficients
+ * given as base-10^9 digit triples d[3k..3k+2] (each < 10^9), k in [0, L).  z_cap >= L; the
+ * result must fit in L limbs, else the device status reports DMUL_ERR_INVALID.  nz as in
+ * dmul_mul. */
+int dmul_carry(dmul_ctx *ctx, const uint32_t *d, size_t L, uint32_t *z, size_t z_cap,
+               uint64_t *nz, void *stream);
+
+/* In-place transpose of a rows x cols row-major uint32 matrix on the device (Sec. 7.5-7.6):
+ * square matrices by tile-pair swaps (TransposeSquareSubMatrix semantics); n x 2n by the paper's
+ * procedure (rho on every row, then the two n x n halves transposed in place with row stride
+ * 2n); 2n x n by its inverse (the halves first, then rho^-1 on every row).  rows and cols must
+ * be equal or one twice the other, each a multiple of 32.  The row permutation's scratch is
+ * the CTA's shared memory (2n words per row, Sec. 7.6). */
+int dmul_transpose(dmul_ctx *ctx, uint32_t *a, size_t rows, size_t cols, void *stream);
+
+/* ---- host-side information (no GPU work; usable without a device) ---------------------------- */
+typedef struct {
+    uint32_t primes[3];   /* ascending                                                     */
+    uint64_t N;           /* transform length: smallest 2^k or 3*2^k >= L the plan supports */
+    uint32_t N1, N2;      /* N = N1 * N2: column length, row length                         */
+    uint32_t col_radix[8];/* radix of each column stage, first to last (0 ends the list)   */
+    uint32_t row_radix[8];/* radix of each row stage                                        */
+    uint32_t sixstep;     /* 1 when the context uses the six-step form                      */
+} dmul_plan_info;
+
+/* Plan the transform for a product of L limbs (L >= 2).  ctx may be NULL (default plan). */
+int dmul_get_plan(const dmul_ctx *ctx, uint64_t L, dmul_plan_info *out);
+
+/* The library's prime set (ascending), found by FindPrimes(w = 31, n_min = 23, l = 3) of Sec. 4.5
+ * (primes c*3*2^n + 1 < 2^30, n >= 23, c odd, the three largest).  Host-only. */
+int dmul_primes(uint32_t out[3]);
+
+/* eq. lambda of Sec. 4.2: the largest n with (10^n - 1)^2 < (2^(w-1))^l / 2^log2M, computed in
+ * exact integer arithmetic; -1 on bad arguments.  The library sizes its bound checks with the
+ * same arithmetic.  Host-only. */
+int dmul_lambda(int w, int l, int log2M);
+
+/* Largest min(nx, ny) (in limbs) the prime set supports: (10^9 - 1)^2 * min(nx,ny) < p1 p2 p3. */
+uint64_t dmul_max_min_limbs(void);
+
+/* ---- measurement ------------------------------------------------------------------------------ */
+/* Stage timing (needs DMUL_FLAG_STAGE_TIMING): the milliseconds each pipeline stage spent on the
+ * device, summed over the calls since the previous dmul_stage_times call, measured with CUDA
+ * events recorded on the calls' stream.  names[i] (static strings) and ms[i] for i < *n, where
+ * *n is in: capacity, out: the number of stages.  Synchronizes the context's last stream. */
+int dmul_stage_times(dmul_ctx *ctx, const char **names, double *ms, uint64_t *launches, int *n);
+
+/* Integer-pipe probe: runs a kernel of independent 32-bit multiply-adds (the IMAD pipe of the
+ * modular arithmetic) on every SM and returns the achieved rate in operations per second. */
+int dmul_probe_imad(dmul_ctx *ctx, double *imad_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMUL_H */

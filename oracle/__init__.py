@@ -55,6 +55,8 @@ def _load():
         sz = ctypes.c_size_t
         lib.or_conv_schoolbook.argtypes = [u32p, sz, u32p, sz, u64p, ctypes.c_int]
         lib.or_conv_schoolbook.restype = None
+        lib.or_conv_at.argtypes = [u32p, sz, u32p, sz, sz, u64p]
+        lib.or_conv_at.restype = None
         lib.or_carry.argtypes = [u64p, sz, u32p]
         lib.or_carry.restype = ctypes.c_uint64
         lib.or_mul_schoolbook.argtypes = [u32p, sz, u32p, sz, u32p, ctypes.c_int]
@@ -122,6 +124,15 @@ def conv_schoolbook_words(x, y, nthreads: int | None = None) -> np.ndarray:
     lib.or_conv_schoolbook(_p32(x), len(x), _p32(y), len(y), _p64(c),
                            nthreads or default_threads())
     return c
+
+
+def conv_at(x, y, k: int) -> int:
+    """One exact coefficient c_k = sum_{i+j=k} x_i y_j (Sec. 3.2), for sampled checks."""
+    lib = _load()
+    x, y = _u32(x), _u32(y)
+    out = np.zeros(2, dtype=np.uint64)
+    lib.or_conv_at(_p32(x), len(x), _p32(y), len(y), k, _p64(out))
+    return int(out[0]) | (int(out[1]) << 64)
 
 
 def carry(c_words: np.ndarray) -> tuple[np.ndarray, int]:

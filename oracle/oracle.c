@@ -89,6 +89,19 @@ void or_conv_schoolbook(const uint32_t *x, size_t n, const uint32_t *y, size_t m
     for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
 }
 
+/* One coefficient c_k of the same convolution, by its definition (for sampled checks). */
+void or_conv_at(const uint32_t *x, size_t n, const uint32_t *y, size_t m, size_t k, uint64_t *out2)
+{
+    u128 s = 0;
+    if (n > 0 && m > 0 && k < n + m) {
+        size_t ilo = (k + 1 > m) ? k + 1 - m : 0;
+        size_t ihi = (k < n - 1) ? k : n - 1;
+        for (size_t i = ilo; i <= ihi; ++i) s += (u128)x[i] * (u128)y[k - i];
+    }
+    out2[0] = (uint64_t)s;
+    out2[1] = (uint64_t)(s >> 64);
+}
+
 /* Sec. 3.2, eq. sigmai_and_zi.  c is 2 words per coefficient; writes z[0..L).  Returns the   */
 /* final carry sigma_L truncated to 64 bits (0 when the product fits in L limbs).            */
 uint64_t or_carry(const uint64_t *c, size_t L, uint32_t *z)

@@ -1,0 +1,604 @@
+// api.cu -- the C ABI of libdmul (include/dmul.h): contexts, plan cache, scratch, the pipeline.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/dmul.h"
+#include "kernels.cuh"
+#include "plan.h"
+#include "ctx.h"
+#include "serve.h"
+
+using namespace dml;
+
+namespace dml {
+
+static int cuda_fail(cudaError_t e) {
+    (void)e;
+    return DMUL_ERR_CUDA;
+}
+
+#define CK(call)                                         \
+    do {                                                 \
+        cudaError_t _e = (call);                         \
+        if (_e != cudaSuccess) return cuda_fail(_e);     \
+    } while (0)
+
+static const char *kStageNames[kNumStages] = {"col_fwd", "row_mul", "col_inv_crt", "carry_scan",
+                                              "transpose", "row_dft", "crt_natural", "pack",
+                                              "small_mul", "batch"};
+
+Timed::Timed(dmul_ctx *c_, int id_, cudaStream_t s_) : c(c_), id(id_), s(s_) {
+        if (!c->timing) return;
+        if (c->ev_used == c->ev_pool.size()) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            c->ev_pool.push_back({a, b});
+        }
+        idx = c->ev_used++;
+        cudaEventRecord(c->ev_pool[idx].first, s);
+}
+
+Timed::~Timed() {
+        if (!c->timing) return;
+        cudaEventRecord(c->ev_pool[idx].second, s);
+        c->ev_log.push_back({id, idx});
+}
+
+int set_device(dmul_ctx *c) {
+    CK(cudaSetDevice(c->device));
+    return DMUL_OK;
+}
+
+int dev_alloc(dmul_ctx *c, void **p, size_t bytes) {
+    if (c->used + bytes > c->budget) return DMUL_ERR_NOMEM;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return DMUL_ERR_NOMEM;
+    }
+    c->used += bytes;
+    return DMUL_OK;
+}
+
+void dev_free(dmul_ctx *c, void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    c->used -= bytes;
+}
+
+int get_plan(dmul_ctx *c, uint64_t N, PlanEntry **out) {
+    auto it = c->plans.find(N);
+    if (it != c->plans.end()) {
+        *out = it->second.get();
+        return DMUL_OK;
+    }
+    auto pe = std::make_unique<PlanEntry>();
+    const bool six = (c->cfg.flags & DMUL_FLAG_SIXSTEP) != 0;
+    if (!(six ? make_host_plan_sixstep(N, &pe->hp) : make_host_plan(N, &pe->hp)))
+        return DMUL_ERR_TOO_LARGE;
+    std::vector<uint32_t> tab[kPrimes];
+    build_tables(pe->hp, &pe->pd, tab);
+    size_t words = tab[0].size();
+    pe->bytes = words * sizeof(uint32_t) * kPrimes;
+    int rc = dev_alloc(c, &pe->dtables, pe->bytes);
+    if (rc) return rc;
+    for (int i = 0; i < kPrimes; ++i) {
+        uint32_t *dst = (uint32_t *)pe->dtables + i * words;
+        CK(cudaMemcpy(dst, tab[i].data(), words * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        pe->pd.tw[i] = (const uint2 *)dst;
+    }
+    *out = pe.get();
+    c->plans[N] = std::move(pe);
+    return DMUL_OK;
+}
+
+int get_small_plan(dmul_ctx *c, uint64_t N, SmallPlanEntry **out) {
+    auto it = c->small_plans.find(N);
+    if (it != c->small_plans.end()) {
+        *out = it->second.get();
+        return DMUL_OK;
+    }
+    auto se = std::make_unique<SmallPlanEntry>();
+    std::vector<uint32_t> tab[kPrimes];
+    build_small_tables(N, &se->sp, tab);
+    size_t words = tab[0].size();
+    se->bytes = std::max<size_t>(words, 2) * sizeof(uint32_t) * kPrimes;
+    int rc = dev_alloc(c, &se->dtables, se->bytes);
+    if (rc) return rc;
+    for (int i = 0; i < kPrimes; ++i) {
+        uint32_t *dst = (uint32_t *)se->dtables + i * std::max<size_t>(words, 2);
+        if (words) CK(cudaMemcpy(dst, tab[i].data(), words * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        se->sp.tw[i] = (const uint2 *)dst;
+    }
+    *out = se.get();
+    c->small_plans[N] = std::move(se);
+    return DMUL_OK;
+}
+
+int ensure_scratch(dmul_ctx *c, uint64_t N, uint64_t L, bool need_y) {
+    (void)need_y;
+    const size_t words = (size_t)kPrimes * N;
+    if (words > c->res_words) {
+        dev_free(c, c->X, c->res_words * 4);
+        dev_free(c, c->Y, c->res_words * 4);
+        c->X = c->Y = nullptr;
+        c->res_words = 0;
+        int rc = dev_alloc(c, (void **)&c->X, words * 4);
+        if (rc) return rc;
+        rc = dev_alloc(c, (void **)&c->Y, words * 4);
+        if (rc) { dev_free(c, c->X, words * 4); c->X = nullptr; return rc; }
+        c->res_words = words;
+    }
+    const size_t nsp = (L + kChunk - 1) / kChunk + 1;
+    if (nsp > c->spill_cap) {
+        dev_free(c, c->spill, c->spill_cap * sizeof(uint2));
+        c->spill = nullptr;
+        c->spill_cap = 0;
+        int rc = dev_alloc(c, (void **)&c->spill, nsp * sizeof(uint2));
+        if (rc) return rc;
+        c->spill_cap = nsp;
+    }
+    const size_t cb = carry_ctl_bytes(L);
+    if (cb > c->ctl_cap) {
+        dev_free(c, c->ctl, c->ctl_cap);
+        c->ctl = nullptr;
+        c->ctl_cap = 0;
+        int rc = dev_alloc(c, &c->ctl, cb);
+        if (rc) return rc;
+        c->ctl_cap = cb;
+    }
+    return DMUL_OK;
+}
+
+bool overlaps(const void *a, size_t abytes, const void *b, size_t bbytes) {
+    uintptr_t a0 = (uintptr_t)a, a1 = a0 + abytes, b0 = (uintptr_t)b, b1 = b0 + bbytes;
+    return a0 < b1 && b0 < a1;
+}
+
+uint64_t max_min_limbs() {
+    typedef unsigned __int128 u128;
+    u128 P = (u128)kPrimeSet[0] * kPrimeSet[1] * kPrimeSet[2];
+    u128 b1 = (u128)(kBase - 1) * (kBase - 1);
+    return (uint64_t)((P - 1) / b1);
+}
+
+int check_sizes(dmul_ctx *c, size_t nx, size_t ny, uint64_t *N) {
+    if (nx == 0 || ny == 0) return DMUL_ERR_INVALID;
+    uint64_t L = (uint64_t)nx + ny;
+    if (std::min(nx, ny) > max_min_limbs()) return DMUL_ERR_TOO_LARGE;  // eq. product_inequality
+    if (c->cfg.max_limbs && L > c->cfg.max_limbs) return DMUL_ERR_TOO_LARGE;
+    *N = (c->cfg.flags & DMUL_FLAG_SIXSTEP) ? choose_N_pow2(L) : choose_N(L);
+    if (*N == 0) return DMUL_ERR_TOO_LARGE;
+    return DMUL_OK;
+}
+
+// The forward transforms of x (and y), the pointwise product and the inverse transforms; the
+// residues of the convolution are then in c->X (four-step order: inverse column pass pending).
+int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
+                       const uint32_t *y, size_t ny, bool square, cudaStream_t s);
+
+int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny,
+                uint32_t *z, size_t z_cap, uint64_t *nz, cudaStream_t s, InvMode mode,
+                uint32_t *mode_out) {
+    uint64_t N;
+    int rc = check_sizes(c, nx, ny, &N);
+    if (rc) return rc;
+    const uint64_t L = (uint64_t)nx + ny;
+    if (mode == kInvDigits) {
+        if (!z || z_cap < L) return DMUL_ERR_CAPACITY;
+        if (overlaps(z, L * 4, x, nx * 4) || overlaps(z, L * 4, y, ny * 4)) return DMUL_ERR_INVALID;
+    }
+    rc = set_device(c);
+    if (rc) return rc;
+    const uint64_t Ns = choose_N_small(L);
+    if (mode == kInvDigits && Ns && !(c->cfg.flags & DMUL_FLAG_SIXSTEP)) {
+        // the whole product in one cluster launch (batch.cu): transforms, CRT and carry in SMEM
+        SmallPlanEntry *se;
+        rc = get_small_plan(c, Ns, &se);
+        if (rc) return rc;
+        JobDev jd;
+        memset(&jd, 0, sizeof(jd));
+        jd.x = x; jd.y = y; jd.z = z; jd.nz = nz; jd.nx = nx; jd.ny = ny; jd.L = L;
+        jd.square = (x == y && nx == ny) ? 1u : 0u;
+        c->last_stream = s;
+        Timed t(c, kStSmall, s);
+        CK(launch_small_mul_one(se->sp, jd, c->status, s));
+        return DMUL_OK;
+    }
+    PlanEntry *pe;
+    rc = get_plan(c, N, &pe);
+    if (rc) return rc;
+    rc = ensure_scratch(c, N, L, true);
+    if (rc) return rc;
+    c->last_stream = s;
+    const bool square = (x == y && nx == ny);
+    rc = enqueue_transforms(c, pe, x, nx, y, ny, square, s);
+    if (rc) return rc;
+    if (c->cfg.flags & DMUL_FLAG_SIXSTEP) {
+        Timed t(c, kStCrt, s);
+        CK(launch_crt_natural(c->X, N, L, mode, mode == kInvDigits ? z : mode_out, c->spill, s));
+    } else {
+        Timed t(c, kStColInv, s);
+        CK(launch_col_inv(pe->pd, c->X, L, mode, mode == kInvDigits ? z : mode_out, c->spill, s));
+    }
+    if (mode == kInvDigits) {
+        CK(cudaMemsetAsync(c->ctl, 0, carry_ctl_bytes(L), s));
+        Timed t(c, kStCarry, s);
+        CK(launch_carry(z, c->spill, L, (CarryCtl *)c->ctl, nz, c->status, s));
+    }
+    return DMUL_OK;
+}
+
+int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
+                       const uint32_t *y, size_t ny, bool square, cudaStream_t s) {
+    const PlanDev &pd = pe->pd;
+    if (!(c->cfg.flags & DMUL_FLAG_SIXSTEP)) {
+        {
+            Timed t(c, kStColFwd, s);
+            CK(launch_col_fwd(pd, x, nx, square ? nullptr : y, ny, c->X, c->Y, c->status, s));
+        }
+        Timed t(c, kStRowMul, s);
+        CK(launch_row_mul(pd, c->X, c->Y, square, s));
+        return DMUL_OK;
+    }
+    // Six-step form (Sec. 7.2): [N1 x N2] -> transpose -> row DFTs of length N1 -> transpose
+    // back -> (twiddle fused into the row DFT kernel) -> fused row pass -> and the mirror.
+    const uint64_t N = pd.N;
+    for (int op = 0; op < (square ? 1 : 2); ++op) {
+        uint32_t *A = op ? c->Y : c->X;
+        {
+            Timed t(c, kStPack, s);
+            CK(launch_pack(op ? y : x, op ? ny : nx, N, A, c->status, s));
+        }
+        {
+            Timed t(c, kStTranspose, s);
+            CK(launch_transpose(A, pd.N1, pd.N2, kPrimes, N, s));
+        }
+        {
+            Timed t(c, kStRowDft, s);
+            CK(launch_rowdft_fwd_tw(pd, A, s));
+        }
+        Timed t(c, kStTranspose, s);
+        CK(launch_transpose(A, pd.N2, pd.N1, kPrimes, N, s));
+    }
+    {
+        Timed t(c, kStRowMul, s);
+        CK(launch_row_mul(pd, c->X, c->Y, square, s));
+    }
+    {
+        Timed t(c, kStTranspose, s);
+        CK(launch_transpose(c->X, pd.N1, pd.N2, kPrimes, N, s));
+    }
+    {
+        Timed t(c, kStRowDft, s);
+        CK(launch_rowdft_inv_tw(pd, c->X, s));
+    }
+    Timed t(c, kStTranspose, s);
+    CK(launch_transpose(c->X, pd.N2, pd.N1, kPrimes, N, s));
+    return DMUL_OK;
+}
+
+static void collect_timers(dmul_ctx *c) {
+    if (!c->timing || c->ev_log.empty()) return;
+    for (auto &pr : c->ev_log) {
+        auto &ev = c->ev_pool[pr.second];
+        cudaEventSynchronize(ev.second);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev.first, ev.second);
+        c->timers[pr.first].ms += ms;
+        c->timers[pr.first].launches += 1;
+    }
+    c->ev_log.clear();
+    c->ev_used = 0;
+}
+
+}  // namespace dml
+
+// ================================================================================================
+// C ABI
+// ================================================================================================
+extern "C" {
+
+const char *dmul_strerror(int st) {
+    switch (st) {
+        case DMUL_OK: return "ok";
+        case DMUL_ERR_INVALID: return "invalid argument or input limb";
+        case DMUL_ERR_TOO_LARGE: return "operands too large for the prime set / transform lengths";
+        case DMUL_ERR_NOMEM: return "out of device memory (HBM budget)";
+        case DMUL_ERR_TIMEOUT: return "a bounded device wait expired";
+        case DMUL_ERR_CUDA: return "CUDA runtime error";
+        case DMUL_ERR_CAPACITY: return "output capacity too small";
+        case DMUL_ERR_UNKNOWN_TICKET: return "unknown ticket";
+        default: return "unknown status";
+    }
+}
+
+int dmul_primes(uint32_t out[3]) {
+    std::vector<uint64_t> p = find_primes(31, 23, 3);
+    if (p.size() != 3) return DMUL_ERR_INVALID;
+    // ascending
+    out[0] = (uint32_t)p[2];
+    out[1] = (uint32_t)p[1];
+    out[2] = (uint32_t)p[0];
+    return DMUL_OK;
+}
+
+int dmul_lambda(int w, int l, int log2M) { return lambda_max_digits(w, l, log2M); }
+
+uint64_t dmul_max_min_limbs(void) { return max_min_limbs(); }
+
+int dmul_get_plan(const dmul_ctx *ctx, uint64_t L, dmul_plan_info *out) {
+    if (!out || L < 2) return DMUL_ERR_INVALID;
+    const bool six = ctx && (ctx->cfg.flags & DMUL_FLAG_SIXSTEP);
+    uint64_t N = six ? choose_N_pow2(L) : choose_N(L);
+    if (!N) return DMUL_ERR_TOO_LARGE;
+    HostPlan hp;
+    if (!(six ? make_host_plan_sixstep(N, &hp) : make_host_plan(N, &hp))) return DMUL_ERR_TOO_LARGE;
+    memset(out, 0, sizeof(*out));
+    for (int i = 0; i < kPrimes; ++i) out->primes[i] = kPrimeSet[i];
+    out->N = hp.N;
+    out->N1 = hp.N1;
+    out->N2 = hp.N2;
+    for (size_t i = 0; i < hp.col_radix.size() && i < 8; ++i) out->col_radix[i] = hp.col_radix[i];
+    for (size_t i = 0; i < hp.row_radix.size() && i < 8; ++i) out->row_radix[i] = hp.row_radix[i];
+    out->sixstep = (ctx && (ctx->cfg.flags & DMUL_FLAG_SIXSTEP)) ? 1u : 0u;
+    return DMUL_OK;
+}
+
+int dmul_init(dmul_ctx **out, const dmul_config *cfg) {
+    if (!out) return DMUL_ERR_INVALID;
+    *out = nullptr;
+    uint32_t pr[3];
+    if (dmul_primes(pr) != DMUL_OK) return DMUL_ERR_INVALID;
+    for (int i = 0; i < 3; ++i)
+        if (pr[i] != kPrimeSet[i]) return DMUL_ERR_INVALID;  // FindPrimes must give the compiled set
+    auto c = std::make_unique<dmul_ctx>();
+    if (cfg) c->cfg = *cfg;
+    c->device = c->cfg.device;
+    c->budget = c->cfg.hbm_budget_bytes ? c->cfg.hbm_budget_bytes : (16ull << 30);
+    c->timing = (c->cfg.flags & DMUL_FLAG_STAGE_TIMING) != 0;
+    for (int i = 0; i < kNumStages; ++i) c->timers.push_back(StageTimer{kStageNames[i]});
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || c->device < 0 || c->device >= ndev) {
+        cudaGetLastError();
+        return DMUL_ERR_CUDA;
+    }
+    CK(cudaSetDevice(c->device));
+    PrimeConst pc[kPrimes];
+    CrtConst crt;
+    make_prime_consts(pc);
+    make_crt_consts(&crt);
+    CK(upload_constants_main(pc, crt));
+    CK(upload_constants_sixstep(pc, crt));
+    CK(upload_constants_batch(pc, crt));
+    CK(init_kernel_attributes_main());
+    CK(init_kernel_attributes_sixstep());
+    CK(init_kernel_attributes_batch());
+    int rc = dev_alloc(c.get(), (void **)&c->status, 256);
+    if (rc) return rc;
+    CK(cudaMemset(c->status, 0, 256));
+    CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+    *out = c.release();
+    return DMUL_OK;
+}
+
+void dmul_destroy(dmul_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    c->server.reset();
+    cudaDeviceSynchronize();
+    for (auto &kv : c->plans) dev_free(c, kv.second->dtables, kv.second->bytes);
+    dev_free(c, c->X, c->res_words * 4);
+    dev_free(c, c->Y, c->res_words * 4);
+    dev_free(c, c->spill, c->spill_cap * sizeof(uint2));
+    dev_free(c, c->ctl, c->ctl_cap);
+    dev_free(c, c->status, 256);
+    destroy_batch_state(c);
+
+    if (c->hx) { cudaFree(c->hx); cudaFree(c->hy); cudaFree(c->hz); cudaFree(c->hnz); }
+    for (auto &e : c->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+int dmul_sync(dmul_ctx *c, void *stream) {
+    if (!c) return DMUL_ERR_INVALID;
+    int rc = set_device(c);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(s));
+    uint32_t st = 0;
+    CK(cudaMemcpy(&st, c->status, 4, cudaMemcpyDeviceToHost));
+    if (st) CK(cudaMemset(c->status, 0, 4));
+    if (st & kStatusTimeout) return DMUL_ERR_TIMEOUT;
+    if (st & kStatusInvalid) return DMUL_ERR_INVALID;
+    return DMUL_OK;
+}
+
+int dmul_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny, uint32_t *z,
+             size_t z_cap, uint64_t *nz, void *stream) {
+    if (!c || !x || !y) return DMUL_ERR_INVALID;
+    return enqueue_mul(c, x, nx, y, ny, z, z_cap, nz, (cudaStream_t)stream, kInvDigits, nullptr);
+}
+
+int dmul_sqr(dmul_ctx *c, const uint32_t *x, size_t nx, uint32_t *z, size_t z_cap, uint64_t *nz,
+             void *stream) {
+    if (!c || !x) return DMUL_ERR_INVALID;
+    return enqueue_mul(c, x, nx, x, nx, z, z_cap, nz, (cudaStream_t)stream, kInvDigits, nullptr);
+}
+
+int dmul_conv_residues(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny,
+                       uint32_t *r, void *stream) {
+    if (!c || !x || !y || !r) return DMUL_ERR_INVALID;
+    return enqueue_mul(c, x, nx, y, ny, nullptr, 0, nullptr, (cudaStream_t)stream, kInvResidues, r);
+}
+
+int dmul_conv_coeffs(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny,
+                     uint32_t *d, void *stream) {
+    if (!c || !x || !y || !d) return DMUL_ERR_INVALID;
+    return enqueue_mul(c, x, nx, y, ny, nullptr, 0, nullptr, (cudaStream_t)stream, kInvTriples, d);
+}
+
+int dmul_carry(dmul_ctx *c, const uint32_t *d, size_t L, uint32_t *z, size_t z_cap, uint64_t *nz,
+               void *stream) {
+    if (!c || !d || !z || L == 0) return DMUL_ERR_INVALID;
+    if (z_cap < L) return DMUL_ERR_CAPACITY;
+    if (overlaps(z, L * 4, d, L * 12)) return DMUL_ERR_INVALID;
+    int rc = set_device(c);
+    if (rc) return rc;
+    rc = ensure_scratch(c, 0, L, false);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    c->last_stream = s;
+    CK(launch_triples_to_digits(d, L, z, c->spill, c->status, s));
+    CK(cudaMemsetAsync(c->ctl, 0, carry_ctl_bytes(L), s));
+    Timed t(c, kStCarry, s);
+    CK(launch_carry(z, c->spill, L, (CarryCtl *)c->ctl, nz, c->status, s));
+    return DMUL_OK;
+}
+
+int dmul_transpose(dmul_ctx *c, uint32_t *a, size_t rows, size_t cols, void *stream) {
+    if (!c || !a) return DMUL_ERR_INVALID;
+    if (rows % 32 || cols % 32 || rows == 0) return DMUL_ERR_INVALID;
+    if (!(rows == cols || rows == 2 * cols || cols == 2 * rows)) return DMUL_ERR_INVALID;
+    int rc = set_device(c);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    c->last_stream = s;
+    Timed t(c, kStTranspose, s);
+    CK(launch_transpose(a, rows, cols, 1, rows * cols, s));
+    return DMUL_OK;
+}
+
+int dmul_mul_host(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny,
+                  uint32_t *z, size_t z_cap, size_t *nz) {
+    if (!c || !x || !y || !z) return DMUL_ERR_INVALID;
+    const bool square = (x == y && nx == ny);
+    uint64_t N;
+    int rc = check_sizes(c, nx, ny, &N);
+    if (rc) return rc;
+    const size_t L = nx + ny;
+    if (z_cap < L) return DMUL_ERR_CAPACITY;
+    rc = set_device(c);
+    if (rc) return rc;
+    if (c->h_cap < L) {
+        if (c->hx) { cudaFree(c->hx); cudaFree(c->hy); cudaFree(c->hz); cudaFree(c->hnz); c->used -= c->h_cap * 12 + 64; }
+        c->hx = c->hy = c->hz = nullptr;
+        c->h_cap = 0;
+        if (c->used + L * 12 + 64 > c->budget) return DMUL_ERR_NOMEM;
+        CK(cudaMalloc(&c->hx, L * 4));
+        CK(cudaMalloc(&c->hy, L * 4));
+        CK(cudaMalloc(&c->hz, L * 4));
+        CK(cudaMalloc(&c->hnz, 64));
+        c->used += L * 12 + 64;
+        c->h_cap = L;
+    }
+    cudaStream_t s = c->own_stream;
+    CK(cudaMemcpyAsync(c->hx, x, nx * 4, cudaMemcpyHostToDevice, s));
+    if (!square) CK(cudaMemcpyAsync(c->hy, y, ny * 4, cudaMemcpyHostToDevice, s));
+    rc = enqueue_mul(c, c->hx, nx, square ? c->hx : c->hy, ny, c->hz, L, c->hnz, s, kInvDigits, nullptr);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(z, c->hz, L * 4, cudaMemcpyDeviceToHost, s));
+    uint64_t n64 = 0;
+    CK(cudaMemcpyAsync(&n64, c->hnz, 8, cudaMemcpyDeviceToHost, s));
+    rc = dmul_sync(c, s);
+    if (nz) *nz = (size_t)n64;
+    return rc;
+}
+
+int dmul_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, void *stream) {
+    if (!c || (!jobs && count)) return DMUL_ERR_INVALID;
+    return dml::run_batch(c, jobs, count, (cudaStream_t)stream);
+}
+
+int dmul_submit(dmul_ctx *c, const dmul_job *job, uint64_t *ticket) {
+    if (!c || !job || !ticket) return DMUL_ERR_INVALID;
+    if (!c->server) c->server = std::make_unique<dml::Server>(c);
+    return c->server->submit(*job, ticket);
+}
+
+int dmul_poll(dmul_ctx *c, uint64_t ticket, int *done) {
+    if (!c || !done) return DMUL_ERR_INVALID;
+    if (!c->server) return DMUL_ERR_UNKNOWN_TICKET;
+    return c->server->poll(ticket, done);
+}
+
+int dmul_wait(dmul_ctx *c, uint64_t ticket) {
+    if (!c) return DMUL_ERR_INVALID;
+    if (!c->server) return DMUL_ERR_UNKNOWN_TICKET;
+    return c->server->wait(ticket);
+}
+
+int dmul_stage_times(dmul_ctx *c, const char **names, double *ms, uint64_t *launches, int *n) {
+    if (!c || !n) return DMUL_ERR_INVALID;
+    if (c->last_stream || c->ev_used) {
+        set_device(c);
+        collect_timers(c);
+    }
+    int k = 0;
+    for (int i = 0; i < kNumStages; ++i) {
+        if (c->timers[i].launches == 0) continue;
+        if (k < *n) {
+            if (names) names[k] = c->timers[i].name;
+            if (ms) ms[k] = c->timers[i].ms;
+            if (launches) launches[k] = c->timers[i].launches;
+        }
+        ++k;
+        c->timers[i].ms = 0;
+        c->timers[i].launches = 0;
+    }
+    *n = k;
+    return DMUL_OK;
+}
+
+int dmul_probe_imad(dmul_ctx *c, double *imad_per_s) {
+    if (!c || !imad_per_s) return DMUL_ERR_INVALID;
+    int rc = set_device(c);
+    if (rc) return rc;
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    uint32_t *sink;
+    CK(cudaMalloc(&sink, 4096 * 4));
+    cudaStream_t s = c->own_stream;
+    const int blocks = sms * 8, iters = 4096;
+    CK(launch_imad_probe(sink, blocks, iters, s));  // warm-up
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+    CK(launch_imad_probe(sink, blocks, iters, s));
+    cudaEventRecord(b, s);
+    CK(cudaEventSynchronize(b));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    const double ops = (double)blocks * 256 * iters * 16 * 8;
+    *imad_per_s = ops / (ms * 1e-3);
+    return DMUL_OK;
+}
+
+}  // extern "C"
+
+// ---- internal entry points used by the batch and serve layers ------------------------------------
+namespace dml {
+
+int ctx_enqueue_mul(dmul_ctx *c, const dmul_job &j, cudaStream_t s) {
+    return enqueue_mul(c, j.x, j.nx, j.y, j.ny, j.z, j.z_cap, j.nz, s, kInvDigits, nullptr);
+}
+
+}  // namespace dml

@@ -1,0 +1,523 @@
+// batch.cu -- the batched form (dmul_batch) and the fused small-product kernel.
+//
+// Small products (transform length N <= 24576) run whole in one cluster of three CTAs, one per
+// prime: limbs -> residues in shared memory, forward transform of x (and y), pointwise product
+// fused with the first inverse stage, inverse transform with the 2^32 N^-1 scale (Sec. 6), then
+// the cluster's CRT through distributed shared memory (Sec. 8.2.2) and the carry recurrence as
+// a block-wide scan of carry maps (Sec. 3.2) in the rank-0 CTA.  One launch, no HBM round trips.
+//
+// Larger products run the four-step pipeline (column pass, fused row pass, inverse column pass
+// with CRT, lookahead carry) with a job index in the grid: one launch per stage serves every job of
+// the same transform length.  Groups of different lengths are independent and run on several
+// streams at once.  A batch whose shape (lengths and job counts) repeats replays a captured CUDA
+// graph; only the job descriptors change between replays.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "ctx.h"
+#include "kernels.cuh"
+#include "modarith.cuh"
+#include "serve.h"
+#include "stages.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace dml {
+
+DMUL_DEFINE_UPLOAD(upload_constants_batch)
+
+// ---------------------------------------------------------------------------------------------
+// fused small product
+// ---------------------------------------------------------------------------------------------
+template <int PI>
+__device__ void small_transform(const SmallPlanDev &sp, const JobDev &J, uint32_t *sx, uint32_t *sy,
+                                uint32_t *status) {
+    const uint32_t N = sp.N;
+    const uint2 *tw = sp.tw[PI];
+    const bool sq = J.square != 0;
+    uint32_t bad = 0;
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
+        uint32_t a = i < J.nx ? J.x[i] : 0u;
+        bad |= (a >= kBase);
+        if (PI == 0) a = red2p<0>(a);
+        sx[swz(i)] = a;
+        if (!sq) {
+            uint32_t b = i < J.ny ? J.y[i] : 0u;
+            bad |= (b >= kBase);
+            if (PI == 0) b = red2p<0>(b);
+            sy[swz(i)] = b;
+        }
+    }
+    const int any_bad = __syncthreads_or((int)bad);
+    if (PI == 0 && any_bad && threadIdx.x == 0) atomicOr(status, kStatusInvalid);
+    const int ns = sp.ns;
+    for (int t = 0; t < ns - 1; ++t) {
+        DMUL_RADIX_SWITCH(sp.st[t].R, (row_mid<PI, RR, false>(sp.st[t], tw, sx, N)));
+        if (!sq) DMUL_RADIX_SWITCH(sp.st[t].R, (row_mid<PI, RR, false>(sp.st[t], tw, sy, N)));
+        __syncthreads();
+    }
+    if (sq) {
+        DMUL_RADIX_SWITCH(sp.st[ns - 1].R, (row_fused_center<PI, RR, true>(sx, sy, N)));
+    } else {
+        DMUL_RADIX_SWITCH(sp.st[ns - 1].R, (row_fused_center<PI, RR, false>(sx, sy, N)));
+    }
+    __syncthreads();
+    for (int t = ns - 2; t >= 0; --t) {
+        DMUL_RADIX_SWITCH(sp.st[t].R, (row_mid<PI, RR, true>(sp.st[t], tw, sx, N)));
+        __syncthreads();
+    }
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
+        uint32_t v = sx[swz(i)];
+        sx[swz(i)] = red1p<PI>(shoup<PI>(v, sp.scale[PI], sp.scales[PI]));
+    }
+    __syncthreads();
+}
+
+// Carry recurrence over the whole (short) product in one CTA: every thread maps a contiguous
+// segment, a block scan of the carry maps gives each segment its incoming carry.
+__device__ void small_carry(const JobDev &J, const uint2 *spb, uint32_t *status) {
+    __shared__ uint32_t s_w[32];
+    __shared__ uint64_t s_top[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const uint64_t L = J.L;
+    const uint64_t per = (L + blockDim.x - 1) / blockDim.x;
+    const uint64_t b0 = (uint64_t)tid * per;
+    const uint64_t b1 = b0 + per < L ? b0 + per : L;
+    auto digit = [&](uint64_t k) -> uint32_t {
+        uint32_t v = J.z[k];
+        if (k >= 32 && (k & 31) == 0) v += spb[(k >> 5) - 1].x;
+        if (k >= 33 && (k & 31) == 1) v += spb[(k >> 5) - 1].y;
+        return v;
+    };
+    uint32_t c0 = 0, c1 = 1, c2 = 2;
+    for (uint64_t k = b0; k < b1; ++k) {
+        uint32_t v = digit(k);
+        c0 = qdig(v + c0);
+        c1 = qdig(v + c1);
+        c2 = qdig(v + c2);
+    }
+    uint32_t f = c0 | (c1 << 2) | (c2 << 4);
+    uint32_t inc = f;
+#pragma unroll
+    for (int dd = 1; dd < 32; dd <<= 1) {
+        uint32_t o = __shfl_up_sync(0xffffffffu, inc, dd);
+        if (lane >= dd) inc = map_compose(inc, o);
+    }
+    uint32_t exc = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) exc = kIdentityMap;
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t agg = kIdentityMap;
+        for (int w = 0; w < nw; ++w) {
+            uint32_t wf = s_w[w];
+            s_w[w] = agg;
+            agg = map_compose(wf, agg);
+        }
+    }
+    __syncthreads();
+    uint32_t c = map_apply(map_compose(exc, s_w[warp]), 0);
+    uint64_t top = 0;
+    for (uint64_t k = b0; k < b1; ++k) {
+        uint32_t t = digit(k) + c;
+        uint32_t q = qdig(t);
+        uint32_t o = t - q * kBase;
+        c = q;
+        if (o) top = k + 1;
+        if (k == L - 1 && c) atomicOr(status, kStatusInvalid);
+        // the digit() of later positions reads z[k + 1...] and spills only, never z[k]: safe
+        J.z[k] = o;
+    }
+#pragma unroll
+    for (int dd = 16; dd >= 1; dd >>= 1) {
+        uint64_t o = __shfl_down_sync(0xffffffffu, top, dd);
+        top = o > top ? o : top;
+    }
+    if (lane == 0) s_top[warp] = top;
+    __syncthreads();
+    if (tid == 0) {
+        uint64_t t = 0;
+        for (int w = 0; w < nw; ++w) t = s_top[w] > t ? s_top[w] : t;
+        if (J.nz) *J.nz = t ? t : 1;
+    }
+}
+
+// jobs == null: the single job `one` (passed by value, so a lone product needs no descriptor copy)
+__global__ void __launch_bounds__(512) k_small_mul(const SmallPlanDev sp, const JobDev *__restrict__ jobs,
+                                                   const JobDev one, uint32_t *status) {
+    extern __shared__ uint32_t sm[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int pi = (int)cluster.block_rank();
+    const JobDev J = jobs ? jobs[blockIdx.y] : one;
+    uint32_t *sx = sm, *sy = sm + sp.N;
+    uint2 *spb = (uint2 *)(sm + 2 * sp.N);
+    DMUL_PRIME_SWITCH(pi, (small_transform<PI>(sp, J, sx, sy, status)));
+    cluster.sync();
+    const uint32_t *s0 = cluster.map_shared_rank(sx, 0);
+    const uint32_t *s1 = cluster.map_shared_rank(sx, 1);
+    const uint32_t *s2 = cluster.map_shared_rank(sx, 2);
+    uint2 *sp0 = cluster.map_shared_rank(spb, 0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t nch = (uint32_t)((J.L + 31) >> 5);
+    for (uint32_t c = pi + kPrimes * warp; c < nch; c += kPrimes * nw) {
+        const uint32_t k = c * 32 + lane;  // < N: L <= N and 32 | N
+        uint32_t d0, d1, d2;
+        crt_digits(s0[swz(k)], s1[swz(k)], s2[swz(k)], d0, d1, d2);
+        uint32_t sv;
+        uint2 spv;
+        chunk_digits(d0, d1, d2, sv, spv);
+        if (k < J.L) J.z[k] = sv;
+        if (lane == 31) sp0[c] = spv;
+    }
+    __threadfence();
+    cluster.sync();
+    if (pi != 0) return;
+    small_carry(J, spb, status);
+}
+
+static size_t small_smem(uint32_t N) { return (size_t)2 * N * 4 + (size_t)(N / 32) * sizeof(uint2); }
+
+static cudaError_t small_launch(const SmallPlanDev &sp, const JobDev *jobs, int njobs, const JobDev &one,
+                                uint32_t *status, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kPrimes, (unsigned)njobs, 1);
+    cfg.blockDim = dim3(sp.N >= 8192 ? 512 : 256, 1, 1);
+    cfg.dynamicSmemBytes = small_smem(sp.N);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kPrimes;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_small_mul, sp, jobs, one, status);
+}
+
+cudaError_t launch_small_mul(const SmallPlanDev &sp, const JobDev *jobs, int njobs, uint32_t *status,
+                             cudaStream_t s) {
+    JobDev none;
+    memset(&none, 0, sizeof(none));
+    return small_launch(sp, jobs, njobs, none, status, s);
+}
+
+cudaError_t launch_small_mul_one(const SmallPlanDev &sp, const JobDev &job, uint32_t *status,
+                                 cudaStream_t s) {
+    return small_launch(sp, nullptr, 1, job, status, s);
+}
+
+// ---------------------------------------------------------------------------------------------
+// batched four-step pipeline (job = blockIdx.z, or blockIdx.y for the carry)
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_col_fwd_b(const PlanDev pd, const JobDev *__restrict__ jobs,
+                                                   uint32_t *status) {
+    extern __shared__ uint32_t sm[];
+    const JobDev &J = jobs[blockIdx.z];
+    const bool second = blockIdx.y != 0;
+    if (second && J.square) return;
+    const int pi = blockIdx.x % kPrimes;
+    const uint32_t tile = blockIdx.x / kPrimes;
+    const uint32_t *src = second ? J.y : J.x;
+    const uint64_t n = second ? J.ny : J.nx;
+    uint32_t *dst = (second ? J.Y : J.X) + (uint64_t)pi * pd.N;
+    DMUL_PRIME_SWITCH(pi, (col_fwd_body<PI>(pd, sm, src, n, dst, tile, status)));
+}
+
+__global__ void __launch_bounds__(256) k_row_mul_b(const PlanDev pd, const JobDev *__restrict__ jobs) {
+    extern __shared__ uint32_t sm[];
+    const JobDev &J = jobs[blockIdx.z];
+    const uint32_t row = blockIdx.x;
+    const int pi = blockIdx.y;
+    uint32_t *xr = J.X + (uint64_t)pi * pd.N + (uint64_t)row * pd.N2;
+    if (J.square) {
+        DMUL_PRIME_SWITCH(pi, (row_mul_body<PI, true>(pd, sm, xr, nullptr)));
+    } else {
+        const uint32_t *yr = J.Y + (uint64_t)pi * pd.N + (uint64_t)row * pd.N2;
+        DMUL_PRIME_SWITCH(pi, (row_mul_body<PI, false>(pd, sm, xr, yr)));
+    }
+}
+
+__global__ void __launch_bounds__(512) k_col_inv_b(const PlanDev pd, const JobDev *__restrict__ jobs) {
+    extern __shared__ uint32_t sm[];
+    const JobDev &J = jobs[blockIdx.z];
+    col_inv_crt(pd, J.X, J.L, kInvDigits, J.z, J.spill, sm);
+}
+
+__global__ void __launch_bounds__(256) k_carry_b(const JobDev *__restrict__ jobs, uint32_t *status) {
+    const JobDev &J = jobs[blockIdx.y];
+    if (blockIdx.x >= J.ntiles) return;
+    carry_tile(J.z, J.spill, J.L, J.ctl, J.nz, status, J.ntiles);
+}
+
+cudaError_t init_kernel_attributes_batch() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_small_mul, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)small_smem(kSmallMaxN))) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_col_fwd_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kMaxN1 * 32 * 4)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_row_mul_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  2 * kMaxN2 * 4)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_col_inv_b, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxN1 * 32 * 4);
+}
+
+cudaError_t launch_col_fwd_b(const PlanDev &pd, const JobDev *jobs, int njobs, uint32_t *status,
+                             cudaStream_t s) {
+    dim3 grid(kPrimes * (pd.N2 / 32), 2, (unsigned)njobs);
+    k_col_fwd_b<<<grid, pd.N1 >= 512 ? 512 : 256, (size_t)pd.N1 * 32 * 4, s>>>(pd, jobs, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_mul_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s) {
+    dim3 grid(pd.N1, kPrimes, (unsigned)njobs);
+    k_row_mul_b<<<grid, 256, (size_t)2 * pd.N2 * 4, s>>>(pd, jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_col_inv_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kPrimes * (pd.N2 / 32), 1, (unsigned)njobs);
+    cfg.blockDim = dim3(pd.N1 >= 512 ? 512 : 256, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)pd.N1 * 32 * 4;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kPrimes;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_col_inv_b, pd, jobs);
+}
+
+cudaError_t launch_carry_b(const JobDev *jobs, int njobs, uint32_t maxtiles, uint32_t *status,
+                           cudaStream_t s) {
+    k_carry_b<<<dim3(maxtiles, (unsigned)njobs), 256, 0, s>>>(jobs, status);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------------
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+void destroy_batch_state(dmul_ctx *c) {
+    BatchState *b = c->batch.get();
+    if (!b) return;
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+    if (b->arena) dev_free(c, b->arena, b->arena_cap);
+    if (b->djobs) dev_free(c, b->djobs, b->jobs_cap * sizeof(JobDev));
+    if (b->hjobs) cudaFreeHost(b->hjobs);
+    for (int i = 0; i < kBatchStreams; ++i) {
+        if (b->streams[i]) cudaStreamDestroy(b->streams[i]);
+        if (b->join[i]) cudaEventDestroy(b->join[i]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
+    c->batch.reset();
+}
+
+static int batch_state(dmul_ctx *c, BatchState **out) {
+    if (!c->batch) {
+        c->batch = std::make_unique<BatchState>();
+        BatchState *b = c->batch.get();
+        for (int i = 0; i < kBatchStreams; ++i) {
+            if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess) return DMUL_ERR_CUDA;
+            if (cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess) return DMUL_ERR_CUDA;
+        }
+        if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return DMUL_ERR_CUDA;
+    }
+    *out = c->batch.get();
+    return DMUL_OK;
+}
+
+// Enqueue the launches of every group (on the fork/join streams).
+static int enqueue_groups(dmul_ctx *c, BatchState *b, const std::vector<GroupLaunch> &groups,
+                          cudaStream_t s, size_t njobs, size_t ctl_off, size_t ctl_bytes) {
+    if (cudaMemcpyAsync(b->djobs, b->hjobs, njobs * sizeof(JobDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return DMUL_ERR_CUDA;
+    if (ctl_bytes && cudaMemsetAsync(b->arena + ctl_off, 0, ctl_bytes, s) != cudaSuccess) return DMUL_ERR_CUDA;
+    if (cudaEventRecord(b->fork, s) != cudaSuccess) return DMUL_ERR_CUDA;
+    for (int i = 0; i < kBatchStreams; ++i)
+        if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) return DMUL_ERR_CUDA;
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const GroupLaunch &G = groups[g];
+        cudaStream_t st = b->streams[g % kBatchStreams];
+        const JobDev *jd = b->djobs + G.first;
+        if (G.small) {
+            SmallPlanEntry *se;
+            int rc = get_small_plan(c, G.N, &se);
+            if (rc) return rc;
+            if (launch_small_mul(se->sp, jd, (int)G.count, c->status, st) != cudaSuccess) return DMUL_ERR_CUDA;
+        } else {
+            PlanEntry *pe;
+            int rc = get_plan(c, G.N, &pe);
+            if (rc) return rc;
+            if (launch_col_fwd_b(pe->pd, jd, (int)G.count, c->status, st) != cudaSuccess) return DMUL_ERR_CUDA;
+            if (launch_row_mul_b(pe->pd, jd, (int)G.count, st) != cudaSuccess) return DMUL_ERR_CUDA;
+            if (launch_col_inv_b(pe->pd, jd, (int)G.count, st) != cudaSuccess) return DMUL_ERR_CUDA;
+            if (launch_carry_b(jd, (int)G.count, G.maxtiles, c->status, st) != cudaSuccess) return DMUL_ERR_CUDA;
+        }
+    }
+    for (int i = 0; i < kBatchStreams; ++i) {
+        if (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess) return DMUL_ERR_CUDA;
+        if (cudaStreamWaitEvent(s, b->join[i], 0) != cudaSuccess) return DMUL_ERR_CUDA;
+    }
+    return DMUL_OK;
+}
+
+int run_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, cudaStream_t s) {
+    if (count == 0) return DMUL_OK;
+    int rc = set_device(c);
+    if (rc) return rc;
+    // validate and classify
+    struct Item { size_t idx; bool small; uint64_t N; bool square; };
+    std::vector<Item> items(count);
+    for (size_t i = 0; i < count; ++i) {
+        const dmul_job &j = jobs[i];
+        if (!j.x || !j.y || !j.z || j.nx == 0 || j.ny == 0) return DMUL_ERR_INVALID;
+        const uint64_t L = j.nx + j.ny;
+        if (j.z_cap < L) return DMUL_ERR_CAPACITY;
+        if (overlaps(j.z, L * 4, j.x, j.nx * 4) || overlaps(j.z, L * 4, j.y, j.ny * 4)) return DMUL_ERR_INVALID;
+        if (std::min(j.nx, j.ny) > max_min_limbs()) return DMUL_ERR_TOO_LARGE;
+        if (c->cfg.max_limbs && L > c->cfg.max_limbs) return DMUL_ERR_TOO_LARGE;
+        Item it{i, false, 0, j.x == j.y && j.nx == j.ny};
+        uint64_t Ns = choose_N_small(L);
+        if (Ns && !(c->cfg.flags & DMUL_FLAG_SIXSTEP)) {
+            it.small = true;
+            it.N = Ns;
+        } else {
+            it.N = (c->cfg.flags & DMUL_FLAG_SIXSTEP) ? 0 : choose_N(L);
+            if (!it.N) return (c->cfg.flags & DMUL_FLAG_SIXSTEP) ? DMUL_ERR_INVALID : DMUL_ERR_TOO_LARGE;
+        }
+        items[i] = it;
+    }
+    // group by (kind, N): the largest transforms first
+    std::sort(items.begin(), items.end(), [](const Item &a, const Item &b) {
+        if (a.small != b.small) return !a.small;
+        if (a.N != b.N) return a.N > b.N;
+        return a.idx < b.idx;
+    });
+    std::vector<GroupLaunch> groups;
+    for (size_t i = 0; i < count; ++i) {
+        if (groups.empty() || groups.back().small != items[i].small || groups.back().N != items[i].N)
+            groups.push_back(GroupLaunch{items[i].small, items[i].N, i, 0, 0});
+        groups.back().count++;
+    }
+    // arena: per medium job X, Y, spill; then all carry control blocks contiguously
+    size_t off = 0;
+    std::vector<size_t> offX(count), offY(count), offS(count), offC(count);
+    for (size_t i = 0; i < count; ++i) {
+        const Item &it = items[i];
+        if (it.small) continue;
+        const dmul_job &j = jobs[it.idx];
+        offX[i] = off;
+        off = align256(off + (size_t)kPrimes * it.N * 4);
+        offY[i] = off;
+        if (!it.square) off = align256(off + (size_t)kPrimes * it.N * 4);
+        offS[i] = off;
+        off = align256(off + ((j.nx + j.ny + 31) / 32 + 1) * sizeof(uint2));
+    }
+    const size_t ctl_off = off;
+    for (size_t i = 0; i < count; ++i) {
+        const Item &it = items[i];
+        if (it.small) continue;
+        const dmul_job &j = jobs[it.idx];
+        offC[i] = off;
+        off = align256(off + carry_ctl_bytes(j.nx + j.ny));
+    }
+    const size_t ctl_bytes = off - ctl_off;
+    const size_t need = std::max<size_t>(off, 256);
+    BatchState *b;
+    rc = batch_state(c, &b);
+    if (rc) return rc;
+    if (need > b->arena_cap) {
+        for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+        b->graphs.clear();
+        if (cudaStreamSynchronize(s) != cudaSuccess) return DMUL_ERR_CUDA;
+        if (b->arena) dev_free(c, b->arena, b->arena_cap);
+        b->arena = nullptr;
+        b->arena_cap = 0;
+        rc = dev_alloc(c, (void **)&b->arena, need);
+        if (rc) return rc;
+        b->arena_cap = need;
+    }
+    if (count > b->jobs_cap) {
+        for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+        b->graphs.clear();
+        if (cudaStreamSynchronize(s) != cudaSuccess) return DMUL_ERR_CUDA;
+        if (b->djobs) dev_free(c, b->djobs, b->jobs_cap * sizeof(JobDev));
+        if (b->hjobs) cudaFreeHost(b->hjobs);
+        b->djobs = nullptr;
+        b->hjobs = nullptr;
+        b->jobs_cap = 0;
+        rc = dev_alloc(c, (void **)&b->djobs, count * sizeof(JobDev));
+        if (rc) return rc;
+        if (cudaMallocHost(&b->hjobs, count * sizeof(JobDev)) != cudaSuccess) return DMUL_ERR_NOMEM;
+        b->jobs_cap = count;
+    }
+    // the previous batch's descriptors may still be in flight (an earlier replay reads hjobs)
+    if (cudaStreamSynchronize(s) != cudaSuccess) return DMUL_ERR_CUDA;
+    for (size_t i = 0; i < count; ++i) {
+        const Item &it = items[i];
+        const dmul_job &j = jobs[it.idx];
+        JobDev &d = b->hjobs[i];
+        memset(&d, 0, sizeof(d));
+        d.x = j.x;
+        d.y = j.y;
+        d.z = j.z;
+        d.nz = j.nz;
+        d.nx = j.nx;
+        d.ny = j.ny;
+        d.L = j.nx + j.ny;
+        d.square = it.square ? 1u : 0u;
+        if (!it.small) {
+            d.X = (uint32_t *)(b->arena + offX[i]);
+            d.Y = it.square ? nullptr : (uint32_t *)(b->arena + offY[i]);
+            d.spill = (uint2 *)(b->arena + offS[i]);
+            d.ctl = (CarryCtl *)(b->arena + offC[i]);
+            d.ntiles = (uint32_t)((d.L + kCarryLimbs - 1) / kCarryLimbs);
+        }
+    }
+    for (auto &G : groups) {
+        uint32_t mt = 0;
+        for (size_t i = G.first; i < G.first + G.count; ++i) mt = std::max(mt, b->hjobs[i].ntiles);
+        G.maxtiles = mt;
+    }
+    // plans are built outside any capture
+    for (auto &G : groups) {
+        if (G.small) { SmallPlanEntry *se; rc = get_small_plan(c, G.N, &se); }
+        else { PlanEntry *pe; rc = get_plan(c, G.N, &pe); }
+        if (rc) return rc;
+    }
+    std::vector<std::tuple<int, uint64_t, size_t>> key;
+    for (auto &G : groups) key.emplace_back(G.small ? 1 : 0, G.N, G.count);
+    for (size_t i = 0; i < count; ++i) key.emplace_back(2, (uint64_t)b->hjobs[i].square, b->hjobs[i].ntiles);
+    c->last_stream = s;
+    Timed t(c, kStBatch, s);
+    auto it = b->graphs.find(key);
+    if (it == b->graphs.end()) {
+        cudaGraph_t graph;
+        cudaStream_t cap = b->streams[0];
+        // capture on a private stream, joined to s through events
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DMUL_ERR_CUDA;
+        rc = enqueue_groups(c, b, groups, cap, count, ctl_off, ctl_bytes);
+        cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+        if (rc) return rc;
+        if (ce != cudaSuccess) return DMUL_ERR_CUDA;
+        cudaGraphExec_t exec;
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return DMUL_ERR_CUDA;
+        it = b->graphs.emplace(key, exec).first;
+    }
+    if (cudaGraphLaunch(it->second, s) != cudaSuccess) return DMUL_ERR_CUDA;
+    return DMUL_OK;
+}
+
+}  // namespace dml

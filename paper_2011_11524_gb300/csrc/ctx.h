@@ -1,0 +1,121 @@
+// ctx.h -- the library context and the helpers the plain, batched and served forms share.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <tuple>
+#include <memory>
+#include <vector>
+
+#include "../../include/dmul.h"
+#include "kernels.cuh"
+#include "plan.h"
+
+namespace dml {
+
+struct PlanEntry {
+    HostPlan hp;
+    PlanDev pd;
+    void *dtables = nullptr;  // one allocation holding the three per-prime tables
+    size_t bytes = 0;
+};
+
+struct SmallPlanEntry {
+    SmallPlanDev sp;
+    void *dtables = nullptr;
+    size_t bytes = 0;
+};
+
+struct StageTimer {
+    const char *name;
+    double ms = 0;
+    uint64_t launches = 0;
+};
+
+class Server;
+
+constexpr int kBatchStreams = 4;
+
+struct GroupLaunch {
+    bool small;
+    uint64_t N;
+    size_t first, count;   // range in the descriptor array
+    uint32_t maxtiles;
+};
+
+struct BatchState {
+    uint8_t *arena = nullptr;
+    size_t arena_cap = 0;
+    JobDev *djobs = nullptr;
+    JobDev *hjobs = nullptr;  // pinned
+    size_t jobs_cap = 0;
+    cudaStream_t streams[kBatchStreams] = {};
+    cudaEvent_t fork = nullptr, join[kBatchStreams] = {};
+    // graph cache keyed by the batch shape
+    std::map<std::vector<std::tuple<int, uint64_t, size_t>>, cudaGraphExec_t> graphs;
+    };
+
+
+
+}  // namespace dml
+
+struct dmul_ctx {
+    int device = 0;
+    dmul_config cfg{};
+    uint64_t budget = 0;
+    uint64_t used = 0;  // library-owned device bytes
+    std::map<uint64_t, std::unique_ptr<dml::PlanEntry>> plans;
+    std::map<uint64_t, std::unique_ptr<dml::SmallPlanEntry>> small_plans;
+    // scratch of the plain form (one set, used by one call at a time)
+    uint32_t *X = nullptr, *Y = nullptr;
+    size_t res_words = 0;  // capacity of X and of Y, in words
+    uint2 *spill = nullptr;
+    size_t spill_cap = 0;
+    void *ctl = nullptr;
+    size_t ctl_cap = 0;
+    uint32_t *status = nullptr;  // device status word
+    // host-buffer path staging
+    uint32_t *hx = nullptr, *hy = nullptr, *hz = nullptr;
+    uint64_t *hnz = nullptr;
+    size_t h_cap = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t last_stream = nullptr;
+    // stage timing
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<int, size_t>> ev_log;  // (stage id, event pair index)
+    std::vector<dml::StageTimer> timers;
+    // batched form
+    std::unique_ptr<dml::BatchState> batch;
+    // serving
+    std::unique_ptr<dml::Server> server;
+};
+
+namespace dml {
+
+enum StageId { kStColFwd = 0, kStRowMul, kStColInv, kStCarry, kStTranspose, kStRowDft, kStCrt,
+               kStPack, kStSmall, kStBatch, kNumStages };
+
+int set_device(dmul_ctx *c);
+int dev_alloc(dmul_ctx *c, void **p, size_t bytes);
+void dev_free(dmul_ctx *c, void *p, size_t bytes);
+int get_plan(dmul_ctx *c, uint64_t N, PlanEntry **out);
+int get_small_plan(dmul_ctx *c, uint64_t N, SmallPlanEntry **out);
+bool overlaps(const void *a, size_t abytes, const void *b, size_t bbytes);
+uint64_t max_min_limbs();
+
+// RAII CUDA-event pair around a stage when the context records stage timings.
+struct Timed {
+    dmul_ctx *c;
+    int id;
+    cudaStream_t s;
+    size_t idx = 0;
+    Timed(dmul_ctx *c_, int id_, cudaStream_t s_);
+    ~Timed();
+};
+
+void destroy_batch_state(dmul_ctx *c);
+
+}  // namespace dml

@@ -1,0 +1,162 @@
+// kernels.cu -- the multiplication pipeline on sm_103a: forward column pass, fused row pass,
+// inverse column pass with cluster CRT, decoupled-lookahead carry scan.
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+#include "modarith.cuh"
+#include "stages.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace dml {
+
+DMUL_DEFINE_UPLOAD(upload_constants_main)
+
+__global__ void __launch_bounds__(512) k_col_fwd(const PlanDev pd, const uint32_t *__restrict__ x,
+                                                 uint64_t nx, const uint32_t *__restrict__ y,
+                                                 uint64_t ny, uint32_t *X, uint32_t *Y,
+                                                 uint32_t *status) {
+    extern __shared__ uint32_t sm[];
+    const int pi = blockIdx.x % kPrimes;
+    const uint32_t tile = blockIdx.x / kPrimes;
+    const bool second = blockIdx.y != 0;
+    const uint32_t *src = second ? y : x;
+    const uint64_t n = second ? ny : nx;
+    uint32_t *dst = (second ? Y : X) + (uint64_t)pi * pd.N;
+    DMUL_PRIME_SWITCH(pi, (col_fwd_body<PI>(pd, sm, src, n, dst, tile, status)));
+}
+
+cudaError_t launch_col_fwd(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
+                           uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status, cudaStream_t s) {
+    const size_t smem = (size_t)pd.N1 * 32 * sizeof(uint32_t);
+    const int threads = pd.N1 >= 512 ? 512 : 256;
+    dim3 grid(kPrimes * (pd.N2 / 32), y ? 2 : 1);
+    k_col_fwd<<<grid, threads, smem, s>>>(pd, x, nx, y, ny, X, Y, status);
+    return cudaGetLastError();
+}
+
+template <bool SQR>
+__global__ void __launch_bounds__(256) k_row_mul(const PlanDev pd, uint32_t *X, const uint32_t *Y) {
+    extern __shared__ uint32_t sm[];
+    const uint32_t row = blockIdx.x;
+    const int pi = blockIdx.y;
+    uint32_t *xr = X + (uint64_t)pi * pd.N + (uint64_t)row * pd.N2;
+    const uint32_t *yr = SQR ? nullptr : Y + (uint64_t)pi * pd.N + (uint64_t)row * pd.N2;
+    DMUL_PRIME_SWITCH(pi, (row_mul_body<PI, SQR>(pd, sm, xr, yr)));
+}
+
+cudaError_t launch_row_mul(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
+                           cudaStream_t s) {
+    dim3 grid(pd.N1, kPrimes);
+    const size_t smem = (size_t)(square ? 1 : 2) * pd.N2 * sizeof(uint32_t);
+    if (square) k_row_mul<true><<<grid, 256, smem, s>>>(pd, X, Y);
+    else k_row_mul<false><<<grid, 256, smem, s>>>(pd, X, Y);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(512) k_col_inv(const PlanDev pd, const uint32_t *__restrict__ X,
+                                                 uint64_t L, int mode, uint32_t *__restrict__ out,
+                                                 uint2 *__restrict__ spill) {
+    extern __shared__ uint32_t sm[];
+    col_inv_crt(pd, X, L, mode, out, spill, sm);
+}
+
+cudaError_t launch_col_inv(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
+                           uint32_t *out, uint2 *spill, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kPrimes * (pd.N2 / 32), 1, 1);
+    cfg.blockDim = dim3(pd.N1 >= 512 ? 512 : 256, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)pd.N1 * 32 * sizeof(uint32_t);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kPrimes;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_col_inv, pd, X, L, (int)mode, out, spill);
+}
+
+// digit triples -> within-chunk digit sums + spills (the CRT stage's epilogue on given triples)
+__global__ void k_triples_to_digits(const uint32_t *__restrict__ d, uint64_t L,
+                                    uint32_t *__restrict__ out, uint2 *__restrict__ spill,
+                                    uint32_t *status) {
+    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;  // blockDim % 32 == 0
+    const uint64_t k0 = k & ~31ull;
+    if (k0 >= L) return;  // warp-uniform
+    uint32_t d0 = 0, d1 = 0, d2 = 0;
+    if (k < L) { d0 = d[3 * k]; d1 = d[3 * k + 1]; d2 = d[3 * k + 2]; }
+    uint32_t sv;
+    uint2 sp;
+    chunk_digits(d0, d1, d2, sv, sp);
+    if (k < L) out[k] = sv;
+    bool over = (k >= L && sv != 0);  // a digit beyond the L limbs: the sum does not fit
+    if ((threadIdx.x & 31) == 31) {
+        spill[k0 >> 5] = sp;
+        over |= (k0 + 32 >= L) && (sp.x | sp.y);
+    }
+    if (over) atomicOr(status, kStatusInvalid);
+}
+
+cudaError_t launch_triples_to_digits(const uint32_t *d, uint64_t L, uint32_t *out, uint2 *spill,
+                                     uint32_t *status, cudaStream_t s) {
+    const uint64_t blocks = (L + 255) / 256;
+    k_triples_to_digits<<<(unsigned)blocks, 256, 0, s>>>(d, L, out, spill, status);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_carry(uint32_t *__restrict__ z, const uint2 *__restrict__ spill,
+                                               uint64_t L, CarryCtl *ctl, uint64_t *nz,
+                                               uint32_t *status, uint32_t ntiles) {
+    carry_tile(z, spill, L, ctl, nz, status, ntiles);
+}
+
+cudaError_t launch_carry(uint32_t *z, const uint2 *spill, uint64_t L, CarryCtl *ctl, uint64_t *nz,
+                         uint32_t *status, cudaStream_t s) {
+    const uint64_t ntiles = (L + kCarryLimbs - 1) / kCarryLimbs;
+    k_carry<<<(unsigned)ntiles, 256, 0, s>>>(z, spill, L, ctl, nz, status, (uint32_t)ntiles);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Integer-pipe probe: independent chains of 32-bit multiply-adds (IMAD) per thread.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_imad_probe(uint32_t *sink, int iters) {
+    uint32_t a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = threadIdx.x * 2654435761u + i * 40503u + 1u;
+    const uint32_t m = blockIdx.x | 1u;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) a[i] = a[i] * m + (uint32_t)i;  // one IMAD each
+        }
+    }
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) acc ^= a[i];
+    if (acc == 0x9e3779b9u) sink[blockIdx.x] = acc;  // keeps the chains alive
+}
+
+cudaError_t launch_imad_probe(uint32_t *sink, int blocks, int iters, cudaStream_t s) {
+    k_imad_probe<<<blocks, 256, 0, s>>>(sink, iters);
+    return cudaGetLastError();
+}
+
+cudaError_t init_kernel_attributes_main() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_col_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kMaxN1 * 32 * 4)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_row_mul<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  2 * kMaxN2 * 4)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_row_mul<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kMaxN2 * 4)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_col_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxN1 * 32 * 4);
+}
+
+}  // namespace dml

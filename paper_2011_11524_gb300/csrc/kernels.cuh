@@ -1,0 +1,98 @@
+// kernels.cuh -- launch interface of the multiplication pipeline kernels (host side).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "common.h"
+
+namespace dml {
+
+// Device-side status bits (accumulated in a context word, read by dmul_sync).
+constexpr uint32_t kStatusInvalid = 1u;   // an input limb >= 10^9, or the result overflowed
+constexpr uint32_t kStatusTimeout = 2u;   // a bounded wait expired
+
+// Control block of one carry scan (zeroed before each scan).
+struct CarryCtl {
+    uint32_t ticket;   // dynamic tile counter
+    uint32_t done;     // tiles finished
+    uint64_t top;      // highest nonzero limb index + 1
+    uint64_t flags[1]; // per-tile lookahead words (ntiles entries)
+};
+inline size_t carry_ctl_bytes(uint64_t L) {
+    uint64_t ntiles = (L + kCarryLimbs - 1) / kCarryLimbs;
+    return sizeof(CarryCtl) + ntiles * sizeof(uint64_t);
+}
+
+// One job of a batched launch (device-resident descriptor).
+struct JobDev {
+    const uint32_t *x, *y;  // operands (y == x for a squaring)
+    uint32_t *z;            // product, L limbs
+    uint64_t *nz;           // normalized length or null
+    uint64_t nx, ny, L;
+    uint32_t *X, *Y;        // residue scratch (medium jobs)
+    uint2 *spill;
+    CarryCtl *ctl;
+    uint32_t square, ntiles;
+};
+
+// Inverse column pass output modes.
+enum InvMode { kInvDigits = 0, kInvTriples = 1, kInvResidues = 2 };
+
+cudaError_t upload_constants_main(const PrimeConst pc[kPrimes], const CrtConst &crt);
+cudaError_t upload_constants_sixstep(const PrimeConst pc[kPrimes], const CrtConst &crt);
+cudaError_t upload_constants_batch(const PrimeConst pc[kPrimes], const CrtConst &crt);
+
+// x (and y) limbs -> forward column transforms + four-step twiddle -> X (and Y) residues [3][N].
+cudaError_t launch_col_fwd(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
+                           uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status, cudaStream_t s);
+
+// Row pass: forward row transforms, pointwise product (or square), inverse row transforms,
+// result in X.
+cudaError_t launch_row_mul(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
+                           cudaStream_t s);
+
+// Inverse column pass + (mode) CRT and digit split.  kInvDigits writes the within-chunk digit
+// sums to out[0..L) and the chunk spills to spill; kInvTriples writes d[3k..3k+2]; kInvResidues
+// writes r[pi*L + k].
+cudaError_t launch_col_inv(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
+                           uint32_t *out, uint2 *spill, cudaStream_t s);
+
+// Digit triples -> within-chunk digit sums + spills (the tail of the CRT stage, on its own).
+cudaError_t launch_triples_to_digits(const uint32_t *d, uint64_t L, uint32_t *out, uint2 *spill,
+                                     uint32_t *status, cudaStream_t s);
+
+// Decoupled-lookahead carry scan: z[0..L) (digit sums < 3*10^9) + spills -> base-10^9 limbs,
+// *nz (device, may be null).  ctl must be zeroed (carry_ctl_bytes(L)) before the launch.
+cudaError_t launch_carry(uint32_t *z, const uint2 *spill, uint64_t L, CarryCtl *ctl, uint64_t *nz,
+                         uint32_t *status, cudaStream_t s);
+
+// Six-step pieces (Sec. 7.2, 7.6).
+cudaError_t launch_pack(const uint32_t *x, uint64_t nx, uint64_t N, uint32_t *X, uint32_t *status,
+                        cudaStream_t s);
+cudaError_t launch_transpose(uint32_t *a, uint64_t rows, uint64_t cols, uint64_t batch,
+                             uint64_t batch_stride, cudaStream_t s);
+cudaError_t launch_rowdft_fwd_tw(const PlanDev &pd, uint32_t *A, cudaStream_t s);
+cudaError_t launch_rowdft_inv_tw(const PlanDev &pd, uint32_t *A, cudaStream_t s);
+cudaError_t launch_crt_natural(const uint32_t *X, uint64_t N, uint64_t L, InvMode mode,
+                               uint32_t *out, uint2 *spill, cudaStream_t s);
+
+// Batched forms (batch.cu).  small: one cluster of three CTAs per job does the whole product.
+cudaError_t launch_small_mul(const SmallPlanDev &sp, const JobDev *jobs, int njobs, uint32_t *status,
+                             cudaStream_t s);
+cudaError_t launch_small_mul_one(const SmallPlanDev &sp, const JobDev &job, uint32_t *status,
+                                 cudaStream_t s);
+cudaError_t launch_col_fwd_b(const PlanDev &pd, const JobDev *jobs, int njobs, uint32_t *status,
+                             cudaStream_t s);
+cudaError_t launch_row_mul_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s);
+cudaError_t launch_col_inv_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s);
+cudaError_t launch_carry_b(const JobDev *jobs, int njobs, uint32_t maxtiles, uint32_t *status,
+                           cudaStream_t s);
+
+// Sets the shared-memory / cluster attributes of every kernel once (outside any graph capture).
+cudaError_t init_kernel_attributes_main();
+cudaError_t init_kernel_attributes_sixstep();
+cudaError_t init_kernel_attributes_batch();
+
+// Integer-pipe probe.
+cudaError_t launch_imad_probe(uint32_t *sink, int blocks, int iters, cudaStream_t s);
+
+}  // namespace dml

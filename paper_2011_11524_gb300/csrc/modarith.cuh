@@ -1,0 +1,132 @@
+// modarith.cuh -- 32-bit field arithmetic mod p < 2^30 and the in-register radix-R DFTs.
+//
+// Representation: every value that travels between stages is an "unadjusted" residue in
+// [0, 2p) (Sec. 8.3); p < 2^30 makes 4p < 2^32, so sums and differences of two such values fit a
+// word without overflow checks (the p < mu/4 variant suggested in Sec. 9).
+//
+//  * Products by a known constant w (twiddles, DFT roots, CRT constants) use Shoup's method with
+//    the precomputed companion w' = floor(w 2^32 / p): q = hi(a w'), r = a w - q p lies in
+//    [0, 2p) for every 32-bit a.  Three multiplies on the IMAD pipe, no correction.
+//  * Products of two variable values (the pointwise product of the convolution theorem, Sec. 3.3)
+//    use Montgomery reduction (Sec. 4.4.3) in its subtractive form:  m = lo(ab) p^-1 mod 2^32,
+//    r = hi(ab) - hi(m p) + p lies in (0, 2p) and equals ab 2^-32 mod p; valid for ab < p 2^32,
+//    i.e. both inputs < 2p.  The factor 2^-32 it leaves behind is removed once, inside the
+//    inverse transform's final scale (the linearity trick of Sec. 6).
+//  * Additions and subtractions are branch-free (Sec. 8.1): the unsigned min(a, a - 2p) maps
+//    [0, 4p) onto [0, 2p).
+#pragma once
+#include <stdint.h>
+#include "common.h"
+
+namespace dml {
+
+// One copy of the constants per translation unit (no relocatable device code); every .cu file that
+// includes this header uploads its copy through its own upload function (kernels.cuh).
+static __constant__ PrimeConst c_prime[kPrimes];
+static __constant__ CrtConst c_crt;
+
+#define DMUL_DEFINE_UPLOAD(NAME)                                                             \
+    cudaError_t NAME(const PrimeConst pc[kPrimes], const CrtConst &crt) {                   \
+        cudaError_t e = cudaMemcpyToSymbol(c_prime, pc, sizeof(PrimeConst) * kPrimes);       \
+        if (e != cudaSuccess) return e;                                                      \
+        return cudaMemcpyToSymbol(c_crt, &crt, sizeof(CrtConst));                           \
+    }
+
+__device__ __forceinline__ uint32_t umin32(uint32_t a, uint32_t b) { return a < b ? a : b; }
+
+// [0, 4p) -> [0, 2p)
+template <int PI>
+__device__ __forceinline__ uint32_t red2p(uint32_t a) { return umin32(a, a - c_prime[PI].p2); }
+
+// [0, 2p) -> [0, p)
+template <int PI>
+__device__ __forceinline__ uint32_t red1p(uint32_t a) { return umin32(a, a - c_prime[PI].p); }
+
+// a * w mod p in [0, 2p) for any 32-bit a; w < p with companion ws.
+template <int PI>
+__device__ __forceinline__ uint32_t shoup(uint32_t a, uint32_t w, uint32_t ws) {
+    uint32_t q = __umulhi(a, ws);
+    return a * w + q * c_prime[PI].negp;
+}
+
+// a * b * 2^-32 mod p in (0, 2p) for a, b in [0, 2p).
+template <int PI>
+__device__ __forceinline__ uint32_t mont(uint32_t a, uint32_t b) {
+    uint32_t lo = a * b;
+    uint32_t hi = __umulhi(a, b);
+    uint32_t m = lo * c_prime[PI].pinv;
+    uint32_t t = __umulhi(m, c_prime[PI].p);
+    return hi - t + c_prime[PI].p;
+}
+
+// Gentleman-Sande (DIF) butterfly of Sec. 5.3 on unadjusted values: x' = x + y,
+// y' = (x - y) * xi_16^e.  e == 0 is the factor-1 butterfly of Sec. 5.6 (no multiply).
+template <int PI, int DIR, int E>
+__device__ __forceinline__ void bfly(uint32_t &x, uint32_t &y) {
+    uint32_t s = red2p<PI>(x + y);
+    uint32_t d = x - y + c_prime[PI].p2;
+    if constexpr (E == 0) {
+        d = red2p<PI>(d);
+    } else {
+        d = shoup<PI>(d, c_prime[PI].w16[DIR][E], c_prime[PI].w16s[DIR][E]);
+    }
+    x = s;
+    y = d;
+}
+
+__host__ __device__ constexpr int brev(int v, int bits) {
+    int r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((v >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
+
+// Position of output k of an R-point DFT computed by dft<>: brev(k) for R = 2^a, k for R = 3.
+template <int R>
+__device__ __forceinline__ constexpr int outpos(int k) {
+    if constexpr (R == 3) return k; else return brev(k, ilog2c(R));
+}
+
+template <int PI, int DIR, int R, int H, int S, int J>
+__device__ __forceinline__ void dft_level_j(uint32_t (&v)[R]) {
+    if constexpr (J < H) {
+        bfly<PI, DIR, J * (8 / H)>(v[S + J], v[S + J + H]);
+        dft_level_j<PI, DIR, R, H, S, J + 1>(v);
+    }
+}
+template <int PI, int DIR, int R, int H, int S>
+__device__ __forceinline__ void dft_level_s(uint32_t (&v)[R]) {
+    if constexpr (S < R) {
+        dft_level_j<PI, DIR, R, H, S, 0>(v);
+        dft_level_s<PI, DIR, R, H, S + 2 * H>(v);
+    }
+}
+template <int PI, int DIR, int R, int H>
+__device__ __forceinline__ void dft_levels(uint32_t (&v)[R]) {
+    if constexpr (H >= 1) {
+        dft_level_s<PI, DIR, R, H, 0>(v);
+        dft_levels<PI, DIR, R, H / 2>(v);
+    }
+}
+
+// In-register R-point DFT (DIR 0: root xi_R, DIR 1: xi_R^-1), no scaling.  Input in natural
+// order v[0..R); output k is left in v[outpos<R>(k)].  For R = 2^a this is the radix-2 DIF
+// network of Sec. 5.3 without its final bit reversal (Sec. 5.4); the butterfly at level of half
+// size H and offset J uses xi_{2H}^J = xi_16^(J * 8 / H).
+template <int PI, int DIR, int R>
+__device__ __forceinline__ void dft(uint32_t (&v)[R]) {
+    if constexpr (R == 3) {
+        // X0 = a+b+c, X1 = (a-c) + w(b-c), X2 = (a-b) - w(b-c), with w = xi_3^(+-1)
+        const uint32_t p2 = c_prime[PI].p2;
+        uint32_t a = v[0], b = v[1], c = v[2];
+        uint32_t t = shoup<PI>(b - c + p2, c_prime[PI].w3[DIR], c_prime[PI].w3s[DIR]);
+        uint32_t x0 = red2p<PI>(red2p<PI>(a + b) + c);
+        uint32_t x1 = red2p<PI>(red2p<PI>(a - c + p2) + t);
+        uint32_t x2 = red2p<PI>(red2p<PI>(a - b + p2) - t + p2);
+        v[0] = x0; v[1] = x1; v[2] = x2;
+    } else {
+        dft_levels<PI, DIR, R, R / 2>(v);
+    }
+}
+
+}  // namespace dml

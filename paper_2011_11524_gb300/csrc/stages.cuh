@@ -1,0 +1,577 @@
+// stages.cuh -- device-side building blocks of the pipeline, shared by the kernel translation
+// units (each instantiates its own copies; there is no relocatable device code).
+//
+// Transform structure (Sec. 7.1, four-step form): a length-N vector is an N1 x N2 row-major matrix
+// (Sec. 7, row-major convention).  The forward transform runs length-N1 DFTs down the columns,
+// multiplies element <k1, n2> by xi_N^(k1 n2), then runs length-N2 DFTs along the rows; nothing is
+// transposed and no bit reversal is performed: the forward output order is a fixed permutation,
+// and the inverse walks the exact mirror of the forward stages, so the pointwise product (which is
+// order-blind, Sec. 5.4 eq. cdot_permutation_invariance and Sec. 7.4) sees matching orders.
+//
+// Each length-n DFT is a sequence of radix-R stages (R in {2,3,4,8,16}).  Stage t splits
+// sub-transforms of length m into R interleaved pieces: for j < m/R it takes the R elements
+// j + u m/R of a sub-transform, computes their R-point DFT in registers (modarith.cuh), multiplies
+// output k by xi_m^(j k) (inter-stage twiddles, precomputed per stage in coalesced tables) and stores
+// it back to position j + k m/R.  The inverse stage undoes this exactly (twiddle xi_m^(-jk) first,
+// then the inverse R-point DFT).
+#pragma once
+#include <cooperative_groups.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+#include "modarith.cuh"
+
+namespace dml {
+
+// ---------------------------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------------------------
+#define DMUL_RADIX_SWITCH(R, CALL)                \
+    switch (R) {                                  \
+        case 2: { constexpr int RR = 2; CALL; } break;   \
+        case 3: { constexpr int RR = 3; CALL; } break;   \
+        case 4: { constexpr int RR = 4; CALL; } break;   \
+        case 8: { constexpr int RR = 8; CALL; } break;   \
+        default: { constexpr int RR = 16; CALL; } break; \
+    }
+
+#define DMUL_PRIME_SWITCH(pi, CALL)                 \
+    switch (pi) {                                   \
+        case 0: { constexpr int PI = 0; CALL; } break; \
+        case 1: { constexpr int PI = 1; CALL; } break; \
+        default: { constexpr int PI = 2; CALL; } break; \
+    }
+
+__device__ __forceinline__ uint2 ldtw(const uint2 *p) { return __ldg(p); }
+
+// Row-buffer index with an XOR swizzle of the 32-word bank rows: bank = (a mod 32) ^ f(a div 32),
+// f(r) = (r mod 16) | ((r >> 3) & 1) << 4.  Every stage pattern of every row schedule the planner
+// emits (a small radix first, then radix 16) then hits 32 distinct banks per warp access.
+__device__ __forceinline__ uint32_t swz(uint32_t a) {
+    uint32_t r = a >> 5;
+    uint32_t f = (r & 15u) | (((r >> 3) & 1u) << 4);
+    return a ^ f;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Forward column pass: limbs -> column DFTs (length N1) -> four-step twiddle -> residues.
+// CTA = one tile of 32 adjacent columns for one prime and one operand; the tile lives in shared
+// memory as N1 rows x 32 words, warp lane = column.
+// ---------------------------------------------------------------------------------------------
+template <int PI, int R>
+__device__ __forceinline__ void colf_first(const PlanDev &pd, const Stage &st, uint32_t *sm,
+                                           const uint32_t *__restrict__ src, uint64_t n,
+                                           uint32_t n2, uint32_t &bad) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t stride = st.m / R;
+    const uint2 *tw = pd.tw[PI] + st.tw;
+    for (uint32_t j = warp; j < stride; j += nw) {
+        uint32_t v[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            uint64_t idx = (uint64_t)(j + u * stride) * pd.N2 + n2;
+            uint32_t a = idx < n ? __ldg(src + idx) : 0u;
+            bad |= (a >= kBase);
+            if (PI == 0) a = red2p<PI>(a);  // 10^9 < 4 p0: [0, 10^9) -> [0, 2 p0)
+            v[u] = a;
+        }
+        dft<PI, 0, R>(v);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            uint32_t o = v[outpos<R>(k)];
+            if (k > 0 && st.m > (uint32_t)R) {
+                uint2 w = ldtw(tw + (k - 1) * stride + j);
+                o = shoup<PI>(o, w.x, w.y);
+            }
+            sm[(j + k * stride) * 32 + lane] = o;
+        }
+    }
+}
+
+template <int PI, int R, bool INV>
+__device__ __forceinline__ void col_mid(const PlanDev &pd, const Stage &st, uint32_t *sm,
+                                        bool final_reduce) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t stride = st.m / R;
+    const uint32_t groups = pd.N1 / R;
+    const uint2 *tw = pd.tw[PI] + (INV ? st.twi : st.tw);
+    const bool has_tw = st.m > (uint32_t)R;
+    for (uint32_t g = warp; g < groups; g += nw) {
+        uint32_t blk = g / stride, j = g - blk * stride;
+        uint32_t base = blk * st.m + j;
+        uint32_t v[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) v[u] = sm[(base + u * stride) * 32 + lane];
+        if (!INV) {
+            dft<PI, 0, R>(v);
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                uint32_t o = v[outpos<R>(k)];
+                if (k > 0 && has_tw) {
+                    uint2 w = ldtw(tw + (k - 1) * stride + j);
+                    o = shoup<PI>(o, w.x, w.y);
+                }
+                sm[(base + k * stride) * 32 + lane] = o;
+            }
+        } else {
+            if (has_tw) {
+#pragma unroll
+                for (int k = 1; k < R; ++k) {
+                    uint2 w = ldtw(tw + (k - 1) * stride + j);
+                    v[k] = shoup<PI>(v[k], w.x, w.y);
+                }
+            }
+            dft<PI, 1, R>(v);
+#pragma unroll
+            for (int u = 0; u < R; ++u) {
+                uint32_t o = v[outpos<R>(u)];
+                if (final_reduce) o = red1p<PI>(o);
+                sm[(base + u * stride) * 32 + lane] = o;
+            }
+        }
+    }
+}
+
+// Last forward column stage (m == R): DFT, then the four-step twiddle xi_N^(k1 n2) with
+// k1 = F(b) + (N1/R) k, applied as Q[k][n2] * A[b][n2], then the store to the residue array.
+template <int PI, int R>
+__device__ __forceinline__ void colf_last(const PlanDev &pd, const Stage &st, const uint32_t *sm,
+                                          uint32_t *__restrict__ dst, uint32_t n2) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t nb = pd.N1 / R;
+    const uint2 *A = pd.tw[PI] + pd.offA;
+    const uint2 *Q = pd.tw[PI] + pd.offQ;
+    for (uint32_t b = warp; b < nb; b += nw) {
+        uint32_t v[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) v[u] = sm[(b * R + u) * 32 + lane];
+        dft<PI, 0, R>(v);
+        uint2 a = ldtw(A + (uint64_t)b * pd.N2 + n2);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            uint32_t o = v[outpos<R>(k)];
+            if (k > 0) {
+                uint2 q = ldtw(Q + (uint64_t)k * pd.N2 + n2);
+                o = shoup<PI>(o, q.x, q.y);
+            }
+            o = shoup<PI>(o, a.x, a.y);
+            dst[(uint64_t)(b * R + k) * pd.N2 + n2] = o;
+        }
+    }
+}
+
+template <int PI>
+__device__ void col_fwd_body(const PlanDev &pd, uint32_t *sm, const uint32_t *__restrict__ src,
+                             uint64_t n, uint32_t *__restrict__ dst, uint32_t tile,
+                             uint32_t *status) {
+    const uint32_t n2 = tile * 32 + (threadIdx.x & 31);
+    uint32_t bad = 0;
+    DMUL_RADIX_SWITCH(pd.cs[0].R, (colf_first<PI, RR>(pd, pd.cs[0], sm, src, n, n2, bad)));
+    if (PI == 0 && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusInvalid);
+    __syncthreads();
+    for (int t = 1; t < pd.ncs - 1; ++t) {
+        DMUL_RADIX_SWITCH(pd.cs[t].R, (col_mid<PI, RR, false>(pd, pd.cs[t], sm, false)));
+        __syncthreads();
+    }
+    const Stage &last = pd.cs[pd.ncs - 1];
+    DMUL_RADIX_SWITCH(last.R, (colf_last<PI, RR>(pd, last, sm, dst, n2)));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Row pass (fused): forward row DFTs of X (and Y), pointwise Montgomery product (or square),
+// inverse row DFTs; the last forward stage, the product and the first inverse stage run on the
+// same registers.  CTA = one row of one prime.
+// ---------------------------------------------------------------------------------------------
+template <int PI, int R>
+__device__ __forceinline__ void rowf_first(const Stage &st, const uint2 *tw,
+                                           const uint32_t *__restrict__ g, uint32_t *sbuf) {
+    const uint32_t stride = st.m / R;
+    for (uint32_t j = threadIdx.x; j < stride; j += blockDim.x) {
+        uint32_t v[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) v[u] = g[j + u * stride];
+        dft<PI, 0, R>(v);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            uint32_t o = v[outpos<R>(k)];
+            if (k > 0) {
+                uint2 w = ldtw(tw + st.tw + (k - 1) * stride + j);
+                o = shoup<PI>(o, w.x, w.y);
+            }
+            sbuf[swz(j + k * stride)] = o;
+        }
+    }
+}
+
+template <int PI, int R, bool INV>
+__device__ __forceinline__ void row_mid(const Stage &st, const uint2 *tw, uint32_t *sbuf,
+                                        uint32_t n) {
+    const uint32_t stride = st.m / R;
+    const uint32_t groups = n / R;
+    const bool has_tw = st.m > (uint32_t)R;
+    for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
+        uint32_t blk = g / stride, j = g - blk * stride;
+        uint32_t base = blk * st.m + j;
+        uint32_t v[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) v[u] = sbuf[swz(base + u * stride)];
+        if (!INV) {
+            dft<PI, 0, R>(v);
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                uint32_t o = v[outpos<R>(k)];
+                if (k > 0 && has_tw) {
+                    uint2 w = ldtw(tw + st.tw + (k - 1) * stride + j);
+                    o = shoup<PI>(o, w.x, w.y);
+                }
+                sbuf[swz(base + k * stride)] = o;
+            }
+        } else {
+            if (has_tw) {
+#pragma unroll
+                for (int k = 1; k < R; ++k) {
+                    uint2 w = ldtw(tw + st.twi + (k - 1) * stride + j);
+                    v[k] = shoup<PI>(v[k], w.x, w.y);
+                }
+            }
+            dft<PI, 1, R>(v);
+#pragma unroll
+            for (int u = 0; u < R; ++u) sbuf[swz(base + u * stride)] = v[outpos<R>(u)];
+        }
+    }
+}
+
+// last forward stage of X and Y + pointwise product + first inverse stage (m == R)
+template <int PI, int R, bool SQR>
+__device__ __forceinline__ void row_fused_center(uint32_t *sx, const uint32_t *sy, uint32_t n) {
+    const uint32_t groups = n / R;
+    for (uint32_t b = threadIdx.x; b < groups; b += blockDim.x) {
+        uint32_t vx[R], vy[R], z[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) vx[u] = sx[swz(b * R + u)];
+        dft<PI, 0, R>(vx);
+        if (!SQR) {
+#pragma unroll
+            for (int u = 0; u < R; ++u) vy[u] = sy[swz(b * R + u)];
+            dft<PI, 0, R>(vy);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            uint32_t a = vx[outpos<R>(k)];
+            z[k] = mont<PI>(a, SQR ? a : vy[outpos<R>(k)]);
+        }
+        dft<PI, 1, R>(z);
+#pragma unroll
+        for (int u = 0; u < R; ++u) sx[swz(b * R + u)] = z[outpos<R>(u)];
+    }
+}
+
+template <int PI, int R>
+__device__ __forceinline__ void rowi_last(const Stage &st, const uint2 *tw, const uint32_t *sbuf,
+                                          uint32_t *__restrict__ g) {
+    const uint32_t stride = st.m / R;
+    for (uint32_t j = threadIdx.x; j < stride; j += blockDim.x) {
+        uint32_t v[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = sbuf[swz(j + k * stride)];
+#pragma unroll
+        for (int k = 1; k < R; ++k) {
+            uint2 w = ldtw(tw + st.twi + (k - 1) * stride + j);
+            v[k] = shoup<PI>(v[k], w.x, w.y);
+        }
+        dft<PI, 1, R>(v);
+#pragma unroll
+        for (int u = 0; u < R; ++u) g[j + u * stride] = v[outpos<R>(u)];
+    }
+}
+
+template <int PI, bool SQR>
+__device__ void row_mul_body(const PlanDev &pd, uint32_t *sm, uint32_t *__restrict__ xr,
+                             const uint32_t *__restrict__ yr) {
+    const uint32_t n = pd.N2;
+    const uint2 *tw = pd.tw[PI];
+    uint32_t *sx = sm;
+    uint32_t *sy = sm + n;
+    const int ns = pd.nrs;
+    DMUL_RADIX_SWITCH(pd.rs[0].R, (rowf_first<PI, RR>(pd.rs[0], tw, xr, sx)));
+    if (!SQR) DMUL_RADIX_SWITCH(pd.rs[0].R, (rowf_first<PI, RR>(pd.rs[0], tw, yr, sy)));
+    __syncthreads();
+    for (int t = 1; t < ns - 1; ++t) {
+        DMUL_RADIX_SWITCH(pd.rs[t].R, (row_mid<PI, RR, false>(pd.rs[t], tw, sx, n)));
+        if (!SQR) DMUL_RADIX_SWITCH(pd.rs[t].R, (row_mid<PI, RR, false>(pd.rs[t], tw, sy, n)));
+        __syncthreads();
+    }
+    DMUL_RADIX_SWITCH(pd.rs[ns - 1].R, (row_fused_center<PI, RR, SQR>(sx, sy, n)));
+    __syncthreads();
+    for (int t = ns - 2; t >= 1; --t) {
+        DMUL_RADIX_SWITCH(pd.rs[t].R, (row_mid<PI, RR, true>(pd.rs[t], tw, sx, n)));
+        __syncthreads();
+    }
+    DMUL_RADIX_SWITCH(pd.rs[0].R, (rowi_last<PI, RR>(pd.rs[0], tw, sx, xr)));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Inverse column pass.  A cluster of three CTAs (one per prime) shares a tile of 32 columns:
+// each runs the inverse four-step twiddle (scaled by 2^32 N^-1, the linearity trick of Sec. 6)
+// and the inverse column DFTs, then the three CTAs read each other's shared memory to recover
+// every coefficient by CRT (Sec. 8.2.2 generalized to three primes by Garner's method).
+// ---------------------------------------------------------------------------------------------
+template <int PI, int R>
+__device__ __forceinline__ void coli_first(const PlanDev &pd, const uint32_t *__restrict__ src,
+                                           uint32_t *sm, uint32_t n2) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t nb = pd.N1 / R;
+    const uint2 *A = pd.tw[PI] + pd.offAi;
+    const uint2 *Q = pd.tw[PI] + pd.offQi;
+    for (uint32_t b = warp; b < nb; b += nw) {
+        uint32_t v[R];
+        uint2 a = ldtw(A + (uint64_t)b * pd.N2 + n2);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            uint32_t o = src[(uint64_t)(b * R + k) * pd.N2 + n2];
+            if (k > 0) {
+                uint2 q = ldtw(Q + (uint64_t)k * pd.N2 + n2);
+                o = shoup<PI>(o, q.x, q.y);
+            }
+            v[k] = shoup<PI>(o, a.x, a.y);
+        }
+        dft<PI, 1, R>(v);
+#pragma unroll
+        for (int u = 0; u < R; ++u) sm[(b * R + u) * 32 + lane] = v[outpos<R>(u)];
+    }
+}
+
+template <int PI>
+__device__ void col_inv_body(const PlanDev &pd, const uint32_t *__restrict__ src, uint32_t *sm,
+                             uint32_t n2) {
+    const int ns = pd.ncs;
+    DMUL_RADIX_SWITCH(pd.cs[ns - 1].R, (coli_first<PI, RR>(pd, src, sm, n2)));
+    __syncthreads();
+    for (int t = ns - 2; t >= 0; --t) {
+        DMUL_RADIX_SWITCH(pd.cs[t].R, (col_mid<PI, RR, true>(pd, pd.cs[t], sm, t == 0)));
+        __syncthreads();
+    }
+    if (ns == 1) {  // a single stage: reduce in place
+        for (uint32_t i = threadIdx.x; i < pd.N1 * 32; i += blockDim.x) sm[i] = red1p<PI>(sm[i]);
+        __syncthreads();
+    }
+}
+
+// Garner CRT of (a0, a1, a2), a_i in [0, p_i), p0 < p1 < p2, then the base-10^9 digits of
+// c = v0 + p0 v1 + p0 p1 v2 < p0 p1 p2 < 10^27.
+__device__ __forceinline__ void crt_digits(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t &d0,
+                                           uint32_t &d1, uint32_t &d2) {
+    const uint32_t p1 = c_prime[1].p, p2 = c_prime[2].p;
+    // v1 = (a1 - a0) p0^-1 mod p1   (a0 < p0 < p1)
+    uint32_t v1 = red1p<1>(shoup<1>(a1 - a0 + p1, c_crt.inv01, c_crt.inv01s));
+    // v2 = (a2 - a0 - p0 v1) (p0 p1)^-1 mod p2   (a0 < p0 < p2)
+    uint32_t t = red1p<2>(shoup<2>(v1, c_crt.p0m2, c_crt.p0m2s));
+    uint32_t s = red1p<2>(a2 - a0 + p2);
+    s = red1p<2>(s - t + p2);
+    uint32_t v2 = red1p<2>(shoup<2>(s, c_crt.inv012, c_crt.inv012s));
+    // c = a0 + p0 v1 + (A0 + A1 10^9) v2
+    uint64_t S0 = (uint64_t)a0 + (uint64_t)c_prime[0].p * v1 + (uint64_t)c_crt.A0 * v2;
+    uint64_t q0 = S0 / kBase;
+    d0 = (uint32_t)(S0 - q0 * kBase);
+    uint64_t S1 = q0 + (uint64_t)c_crt.A1 * v2;
+    uint64_t q1 = S1 / kBase;
+    d1 = (uint32_t)(S1 - q1 * kBase);
+    d2 = (uint32_t)q1;
+}
+
+// Within a warp holding 32 consecutive coefficients (lane = position in the chunk): the chunk's
+// digit sums s_c = d0_c + d1_(c-1) + d2_(c-2) (< 3*10^9) and the spill (d1_31 + d2_30, d2_31) that
+// belongs to the first two positions of the next chunk.
+__device__ __forceinline__ void chunk_digits(uint32_t d0, uint32_t d1, uint32_t d2, uint32_t &sv,
+                                             uint2 &spill) {
+    const int lane = threadIdx.x & 31;
+    uint32_t d1p = __shfl_up_sync(0xffffffffu, d1, 1);
+    uint32_t d2p = __shfl_up_sync(0xffffffffu, d2, 2);
+    if (lane < 1) d1p = 0;
+    if (lane < 2) d2p = 0;
+    sv = d0 + d1p + d2p;
+    uint32_t d2_30 = __shfl_sync(0xffffffffu, d2, 30);
+    spill = make_uint2(d1 + d2_30, d2);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Carry: the recurrence of Sec. 3.2 (eq. sigmai_and_zi) as a decoupled-lookahead scan.
+// After the CRT stage every position holds a digit sum s < 3*10^9 (the spill of the previous
+// chunk added in), so the carry into any position is 0, 1 or 2 and each position acts on the
+// carry by a map {0,1,2} -> {0,1,2}, c -> floor((s + c) / 10^9).  Maps compose associatively;
+// a map is stored as three 2-bit outputs (6 bits).
+// ---------------------------------------------------------------------------------------------
+constexpr uint32_t kIdentityMap = 0u | (1u << 2) | (2u << 4);
+
+__device__ __forceinline__ uint32_t map_apply(uint32_t f, uint32_t c) { return (f >> (2 * c)) & 3u; }
+// g after f
+__device__ __forceinline__ uint32_t map_compose(uint32_t g, uint32_t f) {
+    return map_apply(g, map_apply(f, 0)) | (map_apply(g, map_apply(f, 1)) << 2) |
+           (map_apply(g, map_apply(f, 2)) << 4);
+}
+__device__ __forceinline__ uint32_t qdig(uint32_t t) { return (t >= kBase) + (t >= 2u * kBase); }
+
+__device__ __forceinline__ void st_release(uint64_t *p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+constexpr uint32_t kSpinLimit = 1u << 22;  // bounded lookahead wait
+
+
+// Inverse column pass of one tile (cluster of three CTAs, rank = prime) + CRT epilogue.
+__device__ __forceinline__ void col_inv_crt(const PlanDev &pd, const uint32_t *__restrict__ X,
+                                            uint64_t L, int mode, uint32_t *__restrict__ out,
+                                            uint2 *__restrict__ spill, uint32_t *sm) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int pi = (int)cluster.block_rank();
+    const uint32_t tile = blockIdx.x / kPrimes;
+    const uint32_t j0 = tile * 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t n2 = j0 + lane;
+    const uint32_t *src = X + (uint64_t)pi * pd.N;
+    DMUL_PRIME_SWITCH(pi, (col_inv_body<PI>(pd, src, sm, n2)));
+    if (mode == kInvResidues) {
+        for (uint32_t r = warp; r < pd.N1; r += nw) {
+            uint64_t k = (uint64_t)r * pd.N2 + n2;
+            if (k < L) out[(uint64_t)pi * L + k] = sm[r * 32 + lane];
+        }
+        return;
+    }
+    cluster.sync();
+    const uint32_t *s0 = cluster.map_shared_rank(sm, 0);
+    const uint32_t *s1 = cluster.map_shared_rank(sm, 1);
+    const uint32_t *s2 = cluster.map_shared_rank(sm, 2);
+    for (uint32_t r = pi + kPrimes * warp; r < pd.N1; r += kPrimes * nw) {
+        const uint64_t k0 = (uint64_t)r * pd.N2 + j0;  // first coefficient of this chunk
+        if (k0 >= L) continue;                          // warp-uniform
+        uint32_t d0, d1, d2;
+        crt_digits(s0[r * 32 + lane], s1[r * 32 + lane], s2[r * 32 + lane], d0, d1, d2);
+        const uint64_t k = k0 + lane;
+        if (mode == kInvTriples) {
+            if (k < L) { out[3 * k] = d0; out[3 * k + 1] = d1; out[3 * k + 2] = d2; }
+        } else {
+            uint32_t sv;
+            uint2 sp;
+            chunk_digits(d0, d1, d2, sv, sp);
+            if (k < L) out[k] = sv;
+            if (lane == 31) spill[k0 >> 5] = sp;
+        }
+    }
+    cluster.sync();
+}
+
+// One 2048-limb tile of the decoupled-lookahead carry scan (256 threads).
+__device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2 *__restrict__ spill,
+                                           uint64_t L, CarryCtl *ctl, uint64_t *nz,
+                                           uint32_t *status, uint32_t ntiles) {
+    __shared__ uint32_t s_tile, s_cin, s_warp[8];
+    __shared__ uint64_t s_top[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(&ctl->ticket, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t base = (uint64_t)tile * kCarryLimbs + (uint64_t)tid * 8;
+    uint32_t v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = (base + i < L) ? z[base + i] : 0u;
+    if ((base & 31) == 0 && base > 0 && base < L) {
+        uint2 sp = spill[(base >> 5) - 1];
+        v[0] += sp.x;
+        v[1] += sp.y;
+    }
+    // map of this thread's 8 positions
+    uint32_t c0 = 0, c1 = 1, c2 = 2;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        c0 = qdig(v[i] + c0);
+        c1 = qdig(v[i] + c1);
+        c2 = qdig(v[i] + c2);
+    }
+    uint32_t f = c0 | (c1 << 2) | (c2 << 4);
+    // inclusive warp scan (earlier lanes first)
+    uint32_t inc = f;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc = map_compose(inc, o);
+    }
+    uint32_t exc = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) exc = kIdentityMap;
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t agg = kIdentityMap;
+        for (int w = 0; w < 8; ++w) {
+            uint32_t wf = s_warp[w];
+            s_warp[w] = agg;  // exclusive prefix of warp w
+            agg = map_compose(wf, agg);
+        }
+        uint32_t cin = 0;
+        if (tile > 0) {
+            st_release(&ctl->flags[tile], 1ull | ((uint64_t)agg << 8));
+            uint32_t acc = kIdentityMap;  // maps of tiles (t, tile) composed
+            int64_t t = (int64_t)tile - 1;
+            bool ok = true;
+            while (t >= 0) {
+                uint64_t w;
+                uint32_t spins = 0;
+                while (((w = ld_acquire(&ctl->flags[t])) & 3u) == 0) {
+                    if (++spins > kSpinLimit) { ok = false; break; }
+                    __nanosleep(32);
+                }
+                if (!ok) break;
+                uint32_t val = (uint32_t)(w >> 8) & 63u;
+                if ((w & 3u) == 2u) { cin = map_apply(acc, val); break; }
+                acc = map_compose(acc, val);
+                --t;
+            }
+            if (!ok) { atomicOr(status, kStatusTimeout); cin = 0; }
+        }
+        uint32_t cout = map_apply(agg, cin);
+        st_release(&ctl->flags[tile], 2ull | ((uint64_t)cout << 8));
+        s_cin = cin;
+    }
+    __syncthreads();
+    uint32_t c = map_apply(map_compose(exc, s_warp[warp]), s_cin);
+    uint64_t top = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        uint32_t t = v[i] + c;
+        uint32_t q = qdig(t);
+        uint32_t o = t - q * kBase;
+        c = q;
+        if (base + i < L) {
+            z[base + i] = o;
+            if (o) top = base + i + 1;
+            if (base + i == L - 1 && c != 0) atomicOr(status, kStatusInvalid);  // z >= B^L
+        }
+    }
+    // highest nonzero limb
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        uint64_t o = __shfl_down_sync(0xffffffffu, top, d);
+        top = o > top ? o : top;
+    }
+    if (lane == 0) s_top[warp] = top;
+    __syncthreads();
+    if (tid == 0) {
+        uint64_t t = 0;
+        for (int w = 0; w < 8; ++w) t = s_top[w] > t ? s_top[w] : t;
+        if (t) atomicMax((unsigned long long *)&ctl->top, (unsigned long long)t);
+        __threadfence();
+        uint32_t prev = atomicAdd(&ctl->done, 1u);
+        if (prev == ntiles - 1 && nz) {
+            __threadfence();
+            uint64_t tt = atomicAdd((unsigned long long *)&ctl->top, 0ull);
+            *nz = tt ? tt : 1;
+        }
+    }
+}
+
+}  // namespace dml

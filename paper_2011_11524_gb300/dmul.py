@@ -1,0 +1,362 @@
+"""Thin Python binding of libdmul (include/dmul.h): argument marshalling only.
+
+Every function of the C ABI is exposed under its own name and takes the same arguments, with
+torch CUDA tensors (or raw integers) in place of device pointers; all of the arithmetic runs in
+the CUDA kernels of libdmul.so.  There is no fallback: if the library is missing this module
+raises on import of any entry point.
+
+``Context`` is a small convenience wrapper that allocates outputs with torch.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdmul.so")
+
+DMUL_OK = 0
+DMUL_ERR_INVALID = 1
+DMUL_ERR_TOO_LARGE = 2
+DMUL_ERR_NOMEM = 3
+DMUL_ERR_TIMEOUT = 4
+DMUL_ERR_CUDA = 5
+DMUL_ERR_CAPACITY = 6
+DMUL_ERR_UNKNOWN_TICKET = 7
+
+DMUL_FLAG_SIXSTEP = 1
+DMUL_FLAG_STAGE_TIMING = 2
+
+# every symbol include/dmul.h declares
+EXPORTS = [
+    "dmul_init", "dmul_destroy", "dmul_strerror", "dmul_sync", "dmul_mul", "dmul_sqr",
+    "dmul_mul_host", "dmul_batch", "dmul_submit", "dmul_poll", "dmul_wait", "dmul_conv_residues",
+    "dmul_conv_coeffs", "dmul_carry", "dmul_transpose", "dmul_get_plan", "dmul_primes",
+    "dmul_lambda", "dmul_max_min_limbs", "dmul_stage_times", "dmul_probe_imad",
+]
+
+
+class DmulError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {dmul_strerror(status)} ({status})" if what else dmul_strerror(status))
+
+
+class dmul_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("max_limbs", ctypes.c_uint64), ("flags", ctypes.c_uint32)]
+
+
+class dmul_job(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("nx", ctypes.c_uint64), ("y", ctypes.c_void_p),
+                ("ny", ctypes.c_uint64), ("z", ctypes.c_void_p), ("z_cap", ctypes.c_uint64),
+                ("nz", ctypes.c_void_p)]
+
+
+class dmul_plan_info(ctypes.Structure):
+    _fields_ = [("primes", ctypes.c_uint32 * 3), ("N", ctypes.c_uint64), ("N1", ctypes.c_uint32),
+                ("N2", ctypes.c_uint32), ("col_radix", ctypes.c_uint32 * 8),
+                ("row_radix", ctypes.c_uint32 * 8), ("sixstep", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libdmul.so (built by paper_2011_11524_gb300.build); raise if it is not there."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libdmul.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, sz, u64, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_int
+    sig = {
+        "dmul_init": ([ctypes.POINTER(vp), ctypes.POINTER(dmul_config)], i32),
+        "dmul_destroy": ([vp], None),
+        "dmul_strerror": ([i32], ctypes.c_char_p),
+        "dmul_sync": ([vp, vp], i32),
+        "dmul_mul": ([vp, vp, sz, vp, sz, vp, sz, vp, vp], i32),
+        "dmul_sqr": ([vp, vp, sz, vp, sz, vp, vp], i32),
+        "dmul_mul_host": ([vp, vp, sz, vp, sz, vp, sz, ctypes.POINTER(sz)], i32),
+        "dmul_batch": ([vp, ctypes.POINTER(dmul_job), sz, vp], i32),
+        "dmul_submit": ([vp, ctypes.POINTER(dmul_job), ctypes.POINTER(u64)], i32),
+        "dmul_poll": ([vp, u64, ctypes.POINTER(i32)], i32),
+        "dmul_wait": ([vp, u64], i32),
+        "dmul_conv_residues": ([vp, vp, sz, vp, sz, vp, vp], i32),
+        "dmul_conv_coeffs": ([vp, vp, sz, vp, sz, vp, vp], i32),
+        "dmul_carry": ([vp, vp, sz, vp, sz, vp, vp], i32),
+        "dmul_transpose": ([vp, vp, sz, sz, vp], i32),
+        "dmul_get_plan": ([vp, u64, ctypes.POINTER(dmul_plan_info)], i32),
+        "dmul_primes": ([ctypes.POINTER(ctypes.c_uint32)], i32),
+        "dmul_lambda": ([i32, i32, i32], i32),
+        "dmul_max_min_limbs": ([], u64),
+        "dmul_stage_times": ([vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(u64), ctypes.POINTER(i32)], i32),
+        "dmul_probe_imad": ([vp, ctypes.POINTER(ctypes.c_double)], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------------------------------------
+# pointer marshalling
+# ---------------------------------------------------------------------------------------------
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ---------------------------------------------------------------------------------------------
+# the C ABI, one Python function per entry point
+# ---------------------------------------------------------------------------------------------
+def dmul_strerror(status: int) -> str:
+    return load().dmul_strerror(status).decode()
+
+
+def dmul_init(device: int = 0, hbm_budget_bytes: int = 0, max_limbs: int = 0, flags: int = 0) -> int:
+    cfg = dmul_config(device, hbm_budget_bytes, max_limbs, flags)
+    h = ctypes.c_void_p()
+    rc = load().dmul_init(ctypes.byref(h), ctypes.byref(cfg))
+    if rc:
+        raise DmulError(rc, "dmul_init")
+    return h.value
+
+
+def dmul_destroy(ctx: int) -> None:
+    load().dmul_destroy(ctx)
+
+
+def dmul_sync(ctx: int, stream=None) -> int:
+    return load().dmul_sync(ctx, _stream(stream))
+
+
+def dmul_mul(ctx, x, nx, y, ny, z, z_cap, nz, stream=None) -> int:
+    return load().dmul_mul(ctx, _ptr(x), nx, _ptr(y), ny, _ptr(z), z_cap, _ptr(nz), _stream(stream))
+
+
+def dmul_sqr(ctx, x, nx, z, z_cap, nz, stream=None) -> int:
+    return load().dmul_sqr(ctx, _ptr(x), nx, _ptr(z), z_cap, _ptr(nz), _stream(stream))
+
+
+def dmul_mul_host(ctx, x, nx, y, ny, z, z_cap) -> tuple[int, int]:
+    """x, y, z: host buffers (numpy arrays or pinned torch CPU tensors).  Returns (status, nz)."""
+    nz = ctypes.c_size_t(0)
+    rc = load().dmul_mul_host(ctx, _host_ptr(x), nx, _host_ptr(y), ny, _host_ptr(z), z_cap,
+                              ctypes.byref(nz))
+    return rc, nz.value
+
+
+def _host_ptr(a) -> int:
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def make_jobs(jobs) -> ctypes.Array:
+    """jobs: iterable of (x, nx, y, ny, z, z_cap, nz) with tensors or raw device pointers."""
+    jobs = list(jobs)
+    arr = (dmul_job * max(1, len(jobs)))()
+    for i, (x, nx, y, ny, z, zc, nz) in enumerate(jobs):
+        arr[i] = dmul_job(_ptr(x), nx, _ptr(y), ny, _ptr(z), zc, _ptr(nz))
+    return arr
+
+
+def dmul_batch(ctx, jobs_array, count, stream=None) -> int:
+    return load().dmul_batch(ctx, jobs_array, count, _stream(stream))
+
+
+def dmul_submit(ctx, job: dmul_job) -> tuple[int, int]:
+    t = ctypes.c_uint64(0)
+    rc = load().dmul_submit(ctx, ctypes.byref(job), ctypes.byref(t))
+    return rc, t.value
+
+
+def dmul_poll(ctx, ticket) -> tuple[int, bool]:
+    d = ctypes.c_int(0)
+    rc = load().dmul_poll(ctx, ticket, ctypes.byref(d))
+    return rc, bool(d.value)
+
+
+def dmul_wait(ctx, ticket) -> int:
+    return load().dmul_wait(ctx, ticket)
+
+
+def dmul_conv_residues(ctx, x, nx, y, ny, r, stream=None) -> int:
+    return load().dmul_conv_residues(ctx, _ptr(x), nx, _ptr(y), ny, _ptr(r), _stream(stream))
+
+
+def dmul_conv_coeffs(ctx, x, nx, y, ny, d, stream=None) -> int:
+    return load().dmul_conv_coeffs(ctx, _ptr(x), nx, _ptr(y), ny, _ptr(d), _stream(stream))
+
+
+def dmul_carry(ctx, d, L, z, z_cap, nz, stream=None) -> int:
+    return load().dmul_carry(ctx, _ptr(d), L, _ptr(z), z_cap, _ptr(nz), _stream(stream))
+
+
+def dmul_transpose(ctx, a, rows, cols, stream=None) -> int:
+    return load().dmul_transpose(ctx, _ptr(a), rows, cols, _stream(stream))
+
+
+def dmul_get_plan(ctx, L: int) -> dmul_plan_info:
+    info = dmul_plan_info()
+    rc = load().dmul_get_plan(ctx, L, ctypes.byref(info))
+    if rc:
+        raise DmulError(rc, "dmul_get_plan")
+    return info
+
+
+def dmul_primes() -> list[int]:
+    a = (ctypes.c_uint32 * 3)()
+    rc = load().dmul_primes(a)
+    if rc:
+        raise DmulError(rc, "dmul_primes")
+    return list(a)
+
+
+def dmul_lambda(w: int, l: int, log2M: int) -> int:
+    return load().dmul_lambda(w, l, log2M)
+
+
+def dmul_max_min_limbs() -> int:
+    return int(load().dmul_max_min_limbs())
+
+
+def dmul_stage_times(ctx) -> dict[str, tuple[float, int]]:
+    n = ctypes.c_int(16)
+    names = (ctypes.c_char_p * 16)()
+    ms = (ctypes.c_double * 16)()
+    la = (ctypes.c_uint64 * 16)()
+    rc = load().dmul_stage_times(ctx, names, ms, la, ctypes.byref(n))
+    if rc:
+        raise DmulError(rc, "dmul_stage_times")
+    return {names[i].decode(): (ms[i], int(la[i])) for i in range(min(n.value, 16))}
+
+
+def dmul_probe_imad(ctx) -> float:
+    v = ctypes.c_double(0)
+    rc = load().dmul_probe_imad(ctx, ctypes.byref(v))
+    if rc:
+        raise DmulError(rc, "dmul_probe_imad")
+    return v.value
+
+
+# ---------------------------------------------------------------------------------------------
+# convenience wrapper (torch for device memory and streams)
+# ---------------------------------------------------------------------------------------------
+class Context:
+    """Owns a dmul context; multiplies torch uint32-as-int32 CUDA tensors of limbs."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_limbs: int = 0,
+                 flags: int = 0):
+        self.device = device
+        self.handle = dmul_init(device, hbm_budget_bytes, max_limbs, flags)
+
+    def close(self):
+        if self.handle:
+            dmul_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc:
+            raise DmulError(rc, what)
+
+    def sync(self, stream=None):
+        self._check(dmul_sync(self.handle, stream), "dmul_sync")
+
+    def mul(self, x, y, stream=None, sync=True):
+        """x, y: int32 CUDA tensors holding uint32 limbs.  Returns (z tensor, nz int)."""
+        import torch
+        L = x.numel() + y.numel()
+        z = torch.empty(L, dtype=torch.int32, device=x.device)
+        nz = torch.zeros(1, dtype=torch.int64, device=x.device)
+        if x.data_ptr() == y.data_ptr() and x.numel() == y.numel():
+            rc = dmul_sqr(self.handle, x, x.numel(), z, L, nz, stream)
+        else:
+            rc = dmul_mul(self.handle, x, x.numel(), y, y.numel(), z, L, nz, stream)
+        self._check(rc, "dmul_mul")
+        if not sync:
+            return z, nz
+        self.sync(stream)
+        return z, int(nz.item())
+
+    def sqr(self, x, stream=None):
+        return self.mul(x, x, stream)
+
+    def conv_residues(self, x, y, stream=None):
+        import torch
+        L = x.numel() + y.numel()
+        r = torch.empty(3 * L, dtype=torch.int32, device=x.device)
+        self._check(dmul_conv_residues(self.handle, x, x.numel(), y, y.numel(), r, stream),
+                    "dmul_conv_residues")
+        self.sync(stream)
+        return r
+
+    def conv_coeffs(self, x, y, stream=None):
+        import torch
+        L = x.numel() + y.numel()
+        d = torch.empty(3 * L, dtype=torch.int32, device=x.device)
+        self._check(dmul_conv_coeffs(self.handle, x, x.numel(), y, y.numel(), d, stream),
+                    "dmul_conv_coeffs")
+        self.sync(stream)
+        return d
+
+    def carry(self, d, L, stream=None):
+        import torch
+        z = torch.empty(L, dtype=torch.int32, device=d.device)
+        nz = torch.zeros(1, dtype=torch.int64, device=d.device)
+        self._check(dmul_carry(self.handle, d, L, z, L, nz, stream), "dmul_carry")
+        self.sync(stream)
+        return z, int(nz.item())
+
+    def transpose_(self, a, rows, cols, stream=None):
+        self._check(dmul_transpose(self.handle, a, rows, cols, stream), "dmul_transpose")
+        self.sync(stream)
+        return a
+
+    def stage_times(self):
+        return dmul_stage_times(self.handle)
+
+    def probe_imad(self) -> float:
+        return dmul_probe_imad(self.handle)
+
+
+def to_device(limbs, device="cuda"):
+    """numpy uint32 limbs -> int32 CUDA tensor (bit-identical)."""
+    import numpy as np
+    import torch
+    a = np.ascontiguousarray(np.asarray(limbs, dtype=np.uint32)).view(np.int32)
+    return torch.from_numpy(a.copy()).to(device)
+
+
+def to_host(t):
+    """int32 tensor of limbs -> numpy uint32."""
+    import numpy as np
+    return t.detach().cpu().numpy().view(np.uint32)

@@ -1,0 +1,132 @@
+"""Batched and served forms: every product bit-exact against the oracle, and identical to the
+same product computed alone through the plain form."""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_11524_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def d():
+    from paper_2011_11524_gb300 import build as dbuild
+    from paper_2011_11524_gb300 import dmul
+    dbuild.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return dmul
+
+
+@pytest.fixture(scope="module")
+def ctx(d):
+    c = d.Context(0)
+    yield c
+    c.close()
+
+
+def _prep(d, jobs):
+    dev = []
+    for j in jobs:
+        tx = d.to_device(j.x)
+        ty = tx if j.square else d.to_device(j.y)
+        L = len(j.x) + len(j.y)
+        z = torch.full((L,), -1, dtype=torch.int32, device="cuda")
+        nz = torch.zeros(1, dtype=torch.int64, device="cuda")
+        dev.append((tx, len(j.x), ty, len(j.y), z, L, nz))
+    return dev
+
+
+def _check(d, jobs, dev):
+    for j, (tx, nx, ty, ny, z, L, nz) in zip(jobs, dev):
+        ref = oracle.mul(j.x, j.y)
+        got = d.to_host(z)
+        assert np.array_equal(got, ref)
+        assert int(nz.item()) == len(oracle.normalize(ref))
+
+
+@pytest.mark.parametrize("lo,hi,count,seed", [(2.0, 4.5, 300, 11), (3.0, 5.3, 120, 12)])
+def test_batch_vs_oracle(d, ctx, lo, hi, count, seed):
+    """Uneven sizes (log-uniform digits), 20% squarings, small and four-step jobs in one batch."""
+    jobs = wl.c4_jobs(count, lo, hi, 0.2, seed=seed)
+    dev = _prep(d, jobs)
+    arr = d.make_jobs(dev)
+    assert d.dmul_batch(ctx.handle, arr, len(dev)) == 0
+    assert d.dmul_sync(ctx.handle) == 0
+    _check(d, jobs, dev)
+
+
+def test_batch_graph_replay_new_data(d, ctx):
+    """The same batch shape twice: the second call replays the captured graph with new operands."""
+    jobs1 = wl.c4_jobs(64, 2.5, 4.8, 0.25, seed=21)
+    # same sizes and squaring pattern, different digits
+    rng = np.random.Generator(np.random.PCG64(22))
+    jobs2 = []
+    for j in jobs1:
+        x = rng.integers(0, 10**9, size=len(j.x), dtype=np.uint64).astype(np.uint32)
+        x[-1] = max(1, int(x[-1]))
+        if j.square:
+            jobs2.append(wl.Job(x, x, True))
+        else:
+            y = rng.integers(0, 10**9, size=len(j.y), dtype=np.uint64).astype(np.uint32)
+            y[-1] = max(1, int(y[-1]))
+            jobs2.append(wl.Job(x, y, False))
+    for jobs in (jobs1, jobs2, jobs1):
+        dev = _prep(d, jobs)
+        assert d.dmul_batch(ctx.handle, d.make_jobs(dev), len(dev)) == 0
+        assert d.dmul_sync(ctx.handle) == 0
+        _check(d, jobs, dev)
+
+
+def test_batch_same_as_alone(d, ctx):
+    jobs = wl.c4_jobs(40, 3.0, 5.6, 0.2, seed=31)
+    dev = _prep(d, jobs)
+    assert d.dmul_batch(ctx.handle, d.make_jobs(dev), len(dev)) == 0
+    assert d.dmul_sync(ctx.handle) == 0
+    for j, (tx, nx, ty, ny, z, L, nz) in zip(jobs, dev):
+        alone, nza = ctx.mul(tx, ty)
+        assert torch.equal(alone, z) and nza == int(nz.item())
+
+
+def test_batch_rejects_bad_job(d, ctx):
+    jobs = wl.c4_jobs(3, 2.0, 3.0, 0.0, seed=41)
+    dev = _prep(d, jobs)
+    tx, nx, ty, ny, z, L, nz = dev[1]
+    dev[1] = (tx, nx, ty, ny, z, L - 1, nz)  # capacity too small
+    assert d.dmul_batch(ctx.handle, d.make_jobs(dev), len(dev)) == d.DMUL_ERR_CAPACITY
+
+
+def test_served_mix_same_as_alone(d):
+    """Requests submitted from several threads while others are on the GPU; every result equals the
+    product computed alone and the oracle's."""
+    jobs = wl.c4_jobs(120, 2.0, 5.0, 0.3, seed=51)
+    with d.Context(0) as srv:
+        dev = _prep(d, jobs)
+        arr = d.make_jobs(dev)
+        tickets = [None] * len(jobs)
+
+        def submit(idx):
+            for i in idx:
+                rc, t = d.dmul_submit(srv.handle, arr[i])
+                assert rc == 0
+                tickets[i] = t
+
+        th = [threading.Thread(target=submit, args=(range(k, len(jobs), 4),)) for k in range(4)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        for t in tickets:
+            assert d.dmul_wait(srv.handle, t) == 0
+            rc, done = d.dmul_poll(srv.handle, t)
+            assert rc == 0 and done
+        _check(d, jobs, dev)
+        with d.Context(0) as alone:
+            for j, (tx, nx, ty, ny, z, L, nz) in zip(jobs, dev):
+                za, nza = alone.mul(tx, ty)
+                assert torch.equal(za, z) and nza == int(nz.item())
+        assert d.dmul_wait(srv.handle, 10**9) == d.DMUL_ERR_UNKNOWN_TICKET

@@ -1,0 +1,99 @@
+"""Full-size parity: the benchmark workloads, in the launch configuration bench.py times.
+
+* 2^24 x 2^24 digits (random, and all nines; multiplication and squaring): every limb against the
+  oracle's independent slow NTT route; the all-nines products also against the closed form
+  (10^n - 1)^2 = 10^2n - 2 10^n + 1 (maximal convolution coefficients, eq. ci_bound).
+* 64M x 1M and 32M x 16M digits with 5% of the limbs 10^9 - 1: every limb against the oracle, four
+  residue fingerprints (x y mod q = (x mod q)(y mod q) mod q for 61-bit primes q), and a sample of
+  exact convolution coefficients c_k (after CRT) computed one by one by the oracle.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_11524_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+B = 10**9
+
+
+@pytest.fixture(scope="module")
+def d():
+    from paper_2011_11524_gb300 import build as dbuild
+    from paper_2011_11524_gb300 import dmul
+    dbuild.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return dmul
+
+
+@pytest.fixture(scope="module")
+def ctx(d):
+    c = d.Context(0)
+    yield c
+    c.close()
+
+
+def _moduli(k=4):
+    return list(itertools.islice((q for q in wl.fingerprint_candidates() if oracle.is_prime_mr(q)), k))
+
+
+def _mul(d, ctx, x, y, square=False):
+    tx = d.to_device(x)
+    ty = tx if square else d.to_device(y)
+    z, nz = ctx.mul(tx, ty)
+    return d.to_host(z), nz
+
+
+def _nines_square_limbs(ndig):
+    s = "9" * (ndig - 1) + "8" + "0" * (ndig - 1) + "1"
+    pad = (-len(s)) % 9
+    s = "0" * pad + s
+    a = np.frombuffer(s.encode(), dtype=np.uint8).astype(np.uint32) - 48
+    a = a.reshape(-1, 9)
+    w = np.array([10**(8 - i) for i in range(9)], dtype=np.uint64)
+    limbs = (a.astype(np.uint64) * w).sum(axis=1).astype(np.uint32)
+    return limbs[::-1].copy()
+
+
+def test_c2_random_mul_and_sqr(d, ctx):
+    x, y = wl.c2_random_pair()
+    z, nz = _mul(d, ctx, x, y)
+    ref = oracle.mul_ntt(x, y)
+    assert np.array_equal(z, ref)
+    assert nz == len(oracle.normalize(ref))
+    z, nz = _mul(d, ctx, x, x, square=True)
+    assert np.array_equal(z, oracle.mul_ntt(x, x))
+
+
+def test_c2_all_nines(d, ctx):
+    x, y = wl.c2_nines_pair()
+    expect = _nines_square_limbs(wl.C2_DIGITS)
+    for square in (False, True):
+        z, nz = _mul(d, ctx, x, y, square=square)
+        assert nz == len(expect)
+        assert np.array_equal(z[:nz], expect)
+        assert not z[nz:].any()
+    assert np.array_equal(oracle.normalize(oracle.mul_ntt(x, y)), expect)
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_c3_shapes(d, ctx, which):
+    x, y = wl.c3_pairs()[which]
+    z, nz = _mul(d, ctx, x, y)
+    for q in _moduli():
+        assert oracle.fingerprint(z, q) == oracle.fingerprint(x, q) * oracle.fingerprint(y, q) % q
+    ref = oracle.mul_ntt(x, y)
+    assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))
+    # sampled exact coefficients after CRT
+    dg = d.to_host(ctx.conv_coeffs(d.to_device(x), d.to_device(y))).reshape(-1, 3)
+    rng = np.random.Generator(np.random.PCG64(300 + which))
+    L = len(x) + len(y)
+    ks = sorted(set(int(k) for k in rng.integers(0, L, size=200)) | {0, 1, len(y) - 1, len(y), L - 2, L - 1})
+    for k in ks:
+        got = int(dg[k, 0]) + int(dg[k, 1]) * B + int(dg[k, 2]) * B * B
+        assert got == oracle.conv_at(x, y, k), k

@@ -1,0 +1,278 @@
+"""GPU parity: every result of libdmul (through its C ABI) against the CPU oracle, bit-exact.
+
+Shapes span every transform class from the smallest (N = 1024) up to 2^17, both length families
+(2^k and 3*2^k), ragged tails (lengths that are not multiples of any tile), unbalanced operands,
+leading zero limbs, zero, the all-nines worst case and squarings.  Each step of the path is also
+checked on its own through the stage entry points: convolution residues mod each prime (forward
+transforms, pointwise product, inverse transforms), exact coefficients after CRT, the carry scan
+on adversarial digit patterns, and the in-place transposes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_11524_gb300 import workloads as wl
+from tests.limbs import to_str
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+B = 10**9
+
+
+@pytest.fixture(scope="module")
+def d():
+    from paper_2011_11524_gb300 import build as dbuild
+    from paper_2011_11524_gb300 import dmul
+    dbuild.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return dmul
+
+
+@pytest.fixture(scope="module")
+def ctx(d):
+    c = d.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx6(d):
+    c = d.Context(0, flags=d.DMUL_FLAG_SIXSTEP)
+    yield c
+    c.close()
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _rand(rng, n, top_nonzero=True):
+    a = rng.integers(0, B, size=n, dtype=np.uint64).astype(np.uint32)
+    if top_nonzero and n:
+        a[-1] = max(1, int(a[-1]))
+    return a
+
+
+def _gpu_mul(d, ctx, x, y, square=False):
+    tx = d.to_device(x)
+    ty = tx if square else d.to_device(y)
+    z, nz = ctx.mul(tx, ty)
+    return d.to_host(z), nz
+
+
+SHAPES = [(1, 1), (1, 2), (2, 1), (3, 5), (31, 1), (32, 32), (33, 100), (500, 524), (500, 525),
+          (767, 768), (1000, 3000), (2047, 2050), (4097, 4096), (6000, 6289), (11112, 11112),
+          (12000, 12577), (24575, 1), (1, 24576), (30000, 20001), (49152, 49151), (65536, 65536),
+          (100000, 7), (98303, 98304)]
+
+
+@pytest.mark.parametrize("n,m", SHAPES)
+def test_mul_vs_oracle(d, ctx, n, m):
+    rng = _rng(1000 + n + 7 * m)
+    x, y = _rand(rng, n), _rand(rng, m)
+    z, nz = _gpu_mul(d, ctx, x, y)
+    ref = oracle.mul(x, y)
+    assert np.array_equal(z, ref)
+    assert nz == len(oracle.normalize(ref))
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 512, 513, 1536, 5000, 11112, 40000, 65536])
+def test_sqr_vs_oracle(d, ctx, n):
+    rng = _rng(2000 + n)
+    x = _rand(rng, n)
+    z, nz = _gpu_mul(d, ctx, x, x, square=True)
+    ref = oracle.mul(x, x)
+    assert np.array_equal(z, ref)
+    assert nz == len(oracle.normalize(ref))
+
+
+@pytest.mark.parametrize("ndig", [9, 100, 4609, 100_000, 500_000])
+def test_nines_closed_form(d, ctx, ndig):
+    """(10^n - 1)^2 = 10^2n - 2 10^n + 1, the largest convolution coefficients (eq. ci_bound)."""
+    x = wl.all_nines(ndig)
+    for square in (False, True):
+        z, nz = _gpu_mul(d, ctx, x, x.copy() if not square else x, square=square)
+        assert to_str(z[:nz]) == "9" * (ndig - 1) + "8" + "0" * (ndig - 1) + "1"
+
+
+def test_zero_and_leading_zeros(d, ctx):
+    rng = _rng(3000)
+    y = _rand(rng, 777)
+    z, nz = _gpu_mul(d, ctx, np.zeros(1, np.uint32), y)
+    assert nz == 1 and not z.any()
+    z, nz = _gpu_mul(d, ctx, np.zeros(5000, np.uint32), np.zeros(3, np.uint32))
+    assert nz == 1 and not z.any()
+    x = _rand(rng, 300)
+    xp = np.concatenate([x, np.zeros(1200, np.uint32)])  # leading zero limbs (Sec. 3.2 padding)
+    z, nz = _gpu_mul(d, ctx, xp, y)
+    ref = oracle.mul(x, y)
+    assert nz == len(oracle.normalize(ref))
+    assert np.array_equal(z[:len(ref)], ref) and not z[len(ref):].any()
+
+
+def test_commutative_and_repeatable(d, ctx):
+    rng = _rng(3100)
+    x, y = _rand(rng, 3333), _rand(rng, 9999)
+    a, _ = _gpu_mul(d, ctx, x, y)
+    b, _ = _gpu_mul(d, ctx, y, x)
+    c, _ = _gpu_mul(d, ctx, x, y)
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (100, 924), (3000, 5000), (12288, 1)])
+def test_conv_residues(d, ctx, n, m):
+    """c_k mod p_i after forward transforms, pointwise product and inverse transforms."""
+    rng = _rng(4000 + n)
+    x, y = _rand(rng, n), _rand(rng, m)
+    r = d.to_host(ctx.conv_residues(d.to_device(x), d.to_device(y))).reshape(3, n + m)
+    c = oracle.conv_schoolbook_words(x, y)
+    for i, p in enumerate(d.dmul_primes()):
+        assert np.array_equal(r[i].astype(np.uint64), oracle.residues(c, p)), p
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (2, 2), (1023, 1), (2500, 2600), (11112, 11112)])
+def test_conv_coeffs(d, ctx, n, m):
+    """exact c_k after CRT: d0 + d1 B + d2 B^2 equals the schoolbook coefficient."""
+    rng = _rng(5000 + n)
+    for kind in ("rand", "nines"):
+        if kind == "rand":
+            x, y = _rand(rng, n), _rand(rng, m)
+        else:
+            x, y = np.full(n, B - 1, np.uint32), np.full(m, B - 1, np.uint32)
+        dg = d.to_host(ctx.conv_coeffs(d.to_device(x), d.to_device(y))).reshape(-1, 3).astype(object)
+        got = dg[:, 0] + dg[:, 1] * B + dg[:, 2] * B * B
+        ref = oracle.conv_schoolbook(x, y)
+        assert list(got) == ref
+        assert (dg < B).all()
+
+
+def _triples_from_coeffs(c):
+    out = np.zeros((len(c), 3), np.uint32)
+    for k, v in enumerate(c):
+        out[k] = (v % B, (v // B) % B, v // (B * B))
+    return out
+
+
+@pytest.mark.parametrize("L", [1, 2, 31, 32, 33, 2047, 2048, 2049, 10000, 70001])
+def test_carry_adversarial(d, ctx, L):
+    """The lookahead carry scan against the sequential recurrence (eq. sigmai_and_zi) on coefficient
+    patterns that carry across chunks and tiles: long runs of 10^9-1 digits fed by a single carry,
+    near-maximal coefficients, random."""
+    rng = _rng(6000 + L)
+    for kind in ("run", "max", "rand"):
+        if kind == "run":
+            c = [B - 1] * L
+            c[0] = B - 1 + 1  # one carry ripples through the whole vector ...
+            c[-1] = 0  # ... and stops at the top
+            if L == 1:
+                c = [5]
+        elif kind == "max":
+            c = [int(v) for v in rng.integers(0, 2**62, size=L)]
+            c[-1] = 0
+            if L > 1:
+                c[-2] = int(rng.integers(0, B))
+            if L > 2:
+                c[-3] = int(rng.integers(0, B * B // 2))
+            if L == 1:
+                c = [int(rng.integers(0, B))]
+        else:
+            c = [int(v) for v in rng.integers(0, B, size=L)]
+        total = sum(v * B**k for k, v in enumerate(c))
+        assert total < B**L
+        tri = _triples_from_coeffs(c)
+        z, nz = ctx.carry(d.to_device(tri.reshape(-1)), L)
+        words = np.array([[v & (2**64 - 1), v >> 64] for v in c], dtype=np.uint64)
+        ref, fin = oracle.carry(words)
+        assert fin == 0
+        assert np.array_equal(d.to_host(z), ref)
+        assert nz == len(oracle.normalize(ref))
+
+
+def test_carry_overflow_flagged(d, ctx):
+    """A coefficient vector whose value does not fit L limbs is reported, not silently truncated."""
+    L = 100
+    tri = np.zeros((L, 3), np.uint32)
+    tri[L - 1] = (5, 1, 0)  # 5 + 10^9 at the top limb: one limb too many
+    t = d.to_device(tri.reshape(-1))
+    z = torch.empty(L, dtype=torch.int32, device="cuda")
+    nz = torch.zeros(1, dtype=torch.int64, device="cuda")
+    assert d.dmul_carry(ctx.handle, t, L, z, L, nz) == 0
+    assert d.dmul_sync(ctx.handle) == d.DMUL_ERR_INVALID
+    assert d.dmul_sync(ctx.handle) == 0
+
+
+def test_invalid_limb_flagged(d, ctx):
+    rng = _rng(7000)
+    x = _rand(rng, 5000)
+    x[1234] = B  # not a base-10^9 digit
+    tx, ty = d.to_device(x), d.to_device(_rand(rng, 100))
+    z = torch.empty(5100, dtype=torch.int32, device="cuda")
+    assert d.dmul_mul(ctx.handle, tx, 5000, ty, 100, z, 5100, None) == 0
+    assert d.dmul_sync(ctx.handle) == d.DMUL_ERR_INVALID
+    # the context stays usable
+    x[1234] = B - 1
+    zz, nz = _gpu_mul(d, ctx, x, _rand(_rng(7001), 10))
+
+
+def test_argument_errors(d, ctx):
+    t = d.to_device(np.ones(10, np.uint32))
+    z = torch.empty(30, dtype=torch.int32, device="cuda")
+    assert d.dmul_mul(ctx.handle, t, 10, t, 10, z, 19, None) == d.DMUL_ERR_CAPACITY
+    assert d.dmul_mul(ctx.handle, t, 0, t, 10, z, 30, None) == d.DMUL_ERR_INVALID
+    assert d.dmul_mul(ctx.handle, t, 10, t, 10, t, 20, None) == d.DMUL_ERR_INVALID  # z aliases x
+    big = 3 * 2**22
+    assert d.dmul_mul(ctx.handle, t, big, t, 10, z, big + 10, None) == d.DMUL_ERR_TOO_LARGE
+
+
+def test_host_buffer_entry_point(d, ctx):
+    rng = _rng(7100)
+    x, y = _rand(rng, 7777), _rand(rng, 5555)
+    z = np.zeros(len(x) + len(y), np.uint32)
+    rc, nz = d.dmul_mul_host(ctx.handle, x, len(x), y, len(y), z, len(z))
+    assert rc == 0
+    ref = oracle.mul(x, y)
+    assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))
+    z2 = np.zeros(2 * len(x), np.uint32)
+    rc, nz = d.dmul_mul_host(ctx.handle, x, len(x), x, len(x), z2, len(z2))
+    assert rc == 0 and np.array_equal(z2, oracle.mul(x, x))
+
+
+# ---- six-step form (Sec. 7.2) with the in-place transposes of Sec. 7.6 -------------------------
+@pytest.mark.parametrize("n,m", [(1, 1), (500, 524), (1000, 1049), (3000, 5000), (11112, 11112),
+                                 (40000, 25536), (65536, 65536)])
+def test_sixstep_mul(d, ctx6, n, m):
+    rng = _rng(8000 + n)
+    x, y = _rand(rng, n), _rand(rng, m)
+    z, nz = _gpu_mul(d, ctx6, x, y)
+    ref = oracle.mul(x, y)
+    assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))
+    z, nz = _gpu_mul(d, ctx6, x, x, square=True)
+    assert np.array_equal(z, oracle.mul(x, x))
+
+
+def test_sixstep_plan_shapes(d, ctx6):
+    for L, (n1, n2) in ((1024, (32, 32)), (2048, (32, 64)), (2**21, (1024, 2048)), (2**22, (2048, 2048))):
+        info = d.dmul_get_plan(ctx6.handle, L)
+        assert (info.N1, info.N2) == (n1, n2) and info.sixstep == 1
+
+
+@pytest.mark.parametrize("rows,cols", [(32, 32), (64, 64), (32, 64), (64, 32), (256, 512), (512, 256),
+                                       (1024, 1024), (1024, 2048), (2048, 1024)])
+def test_inplace_transpose(d, ctx, rows, cols):
+    rng = _rng(9000 + rows + cols)
+    a = rng.integers(0, 2**32, size=rows * cols, dtype=np.uint64).astype(np.uint32)
+    t = d.to_device(a)
+    ctx.transpose_(t, rows, cols)
+    assert np.array_equal(d.to_host(t), oracle.transpose(a, rows, cols))
+    ctx.transpose_(t, cols, rows)  # and back
+    assert np.array_equal(d.to_host(t), a)
+
+
+def test_c1_workload(d, ctx):
+    """One multiplication of two 100,000-digit operands against the schoolbook oracle."""
+    x, y = wl.c1_pair()
+    z, nz = _gpu_mul(d, ctx, x, y)
+    ref = oracle.mul_schoolbook(x, y)
+    assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))

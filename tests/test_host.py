@@ -1,0 +1,98 @@
+"""Host-side checks of libdmul (no GPU): the library loads, exports every symbol include/dmul.h
+declares, and its planner's number theory agrees with the oracle and the paper's printed tables."""
+import math
+import os
+import re
+
+import pytest
+
+import oracle
+from paper_2011_11524_gb300 import build as dbuild
+from paper_2011_11524_gb300 import dmul as d
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    dbuild.build()
+    d.load()
+
+
+def _header_symbols():
+    txt = open(os.path.join(ROOT, "include", "dmul.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(dmul_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol():
+    syms = _header_symbols()
+    assert len(syms) >= 20
+    lib = d.load()
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert sorted(d.EXPORTS) == syms
+
+
+def test_primes_match_oracle_find_primes():
+    """The GPU prime set is FindPrimes(w=31, n_min=23, l=3) (Sec. 4.5), as the oracle computes it."""
+    lib_primes = d.dmul_primes()
+    ref = sorted(oracle.find_primes(31, 23, 3))
+    assert lib_primes == ref
+    for p in ref:
+        assert p < 2**30 and oracle.is_prime_mr(p)
+        q = p - 1
+        assert q % 3 == 0 and (q & -q) >= 2**23
+
+
+def test_lambda_tables_from_paper():
+    """eq. lambda against the six tables printed in Sec. 4.2."""
+    path = os.path.join(ROOT, "tests", "golden", "lambda_tables.txt")
+    n = 0
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        lmu, lM, l, lam = (int(t) for t in line.split())
+        assert d.dmul_lambda(lmu, l, lM) == lam, (lmu, lM, l)
+        n += 1
+    assert n == 24
+
+
+def test_product_bound():
+    """(B-1)^2 min(n, m) < p0 p1 p2 exactly for min <= dmul_max_min_limbs() (eq. product_inequality)."""
+    P = math.prod(d.dmul_primes())
+    m = d.dmul_max_min_limbs()
+    assert (10**9 - 1) ** 2 * m < P <= (10**9 - 1) ** 2 * (m + 1)
+    # the configurations' worst case: two 2^24-digit operands
+    assert (10**9 - 1) ** 2 * 1864136 < P
+
+
+@pytest.mark.parametrize("L", [2, 3, 1000, 1024, 1025, 1536, 1537, 22224, 3728272, 5333334, 7222224,
+                               3 * 2**22])
+def test_plan_invariants(L):
+    info = d.dmul_get_plan(None, L)
+    N = info.N
+    assert N >= L and N >= 1024
+    k = N // 3 if N % 3 == 0 else N
+    assert k & (k - 1) == 0
+    # smallest admissible length
+    for cand in range(L, N):
+        kk = cand // 3 if cand % 3 == 0 else cand
+        assert not (kk & (kk - 1) == 0 and cand >= 1024), cand
+    assert info.N1 * info.N2 == N
+    cr = [r for r in info.col_radix if r]
+    rr = [r for r in info.row_radix if r]
+    assert math.prod(cr) == info.N1 and math.prod(rr) == info.N2
+    assert info.N2 % 32 == 0 and info.N2 <= 8192 and info.N1 <= 1536
+    for p in info.primes:
+        assert (p - 1) % N == 0
+
+
+def test_too_large_rejected():
+    with pytest.raises(d.DmulError):
+        d.dmul_get_plan(None, 3 * 2**22 + 1)
+
+
+def test_strerror():
+    for st in range(8):
+        assert isinstance(d.dmul_strerror(st), str) and d.dmul_strerror(st)

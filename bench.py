@@ -38,7 +38,7 @@ def _dist():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -53,7 +53,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -163,7 +163,8 @@ def run_ours(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    x_np, y_np = wl.c2_random_pair(DIGITS)
+    digits = args.digits
+    x_np, y_np = wl.c2_random_pair(digits)
     nx, ny = len(x_np), len(y_np)
     L = nx + ny
     ctx = d.Context(local, flags=d.DMUL_FLAG_STAGE_TIMING)
@@ -208,26 +209,32 @@ def run_ours(args, rank, world, local):
     if rc:
         raise d.DmulError(rc, "timed region")
     stages = ctx.stage_times()
-    digits_per_step = 2 * DIGITS
+    digits_per_step = 2 * digits
     value, total_ms = aggregate(sum(ms), digits_per_step, args.steps, world, dev)
     ms_per_step = total_ms / args.steps
 
     # ---- end to end through the host-buffer entry point (pinned host memory) ----
-    hx = torch.from_numpy(x_np.view(np.int32).copy()).pin_memory()
-    hy = torch.from_numpy(y_np.view(np.int32).copy()).pin_memory()
-    hz = torch.empty(L, dtype=torch.int32).pin_memory()
-    for _ in range(max(1, args.warmup // 2)):
-        rc, _ = d.dmul_mul_host(ctx.handle, hx, nx, hy, ny, hz, L)
-    e2e = []
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rc, nzh = d.dmul_mul_host(ctx.handle, hx, nx, hy, ny, hz, L)
-        e2e.append(time.perf_counter() - t0)
-        if rc:
-            raise d.DmulError(rc, "dmul_mul_host")
-    e2e_s = sum(e2e) / len(e2e)
+    e2e_out = None
+    if not args.no_e2e:
+        hx = torch.from_numpy(x_np.view(np.int32).copy()).pin_memory()
+        hy = torch.from_numpy(y_np.view(np.int32).copy()).pin_memory()
+        hz = torch.empty(L, dtype=torch.int32).pin_memory()
+        for _ in range(max(1, args.warmup // 2)):
+            rc, _ = d.dmul_mul_host(ctx.handle, hx, nx, hy, ny, hz, L)
+        e2e = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc, nzh = d.dmul_mul_host(ctx.handle, hx, nx, hy, ny, hz, L)
+            e2e.append(time.perf_counter() - t0)
+            if rc:
+                raise d.DmulError(rc, "dmul_mul_host")
+        e2e_s = sum(e2e) / len(e2e)
+        e2e_out = {"value": digits_per_step / e2e_s * world, "unit": "digits/s",
+                   "h2d_bytes_per_step": 4 * (nx + ny), "d2h_bytes_per_step": 4 * L + 8,
+                   "ms_per_step": e2e_s * 1e3}
+        ctx.stage_times()  # the host leg's stage timings are not the kernel measurement
 
     # ---- roofline of the dominant kernel ----
     info = d.dmul_get_plan(ctx.handle, L)
@@ -261,24 +268,24 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": "digits/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "digits_x": DIGITS, "digits_y": DIGITS, "limbs": [nx, ny],
+        "config": {"workload": WORKLOAD if digits == DIGITS else f"{digits} x {digits}-digit random multiplication",
+                   "digits_x": digits, "digits_y": digits, "limbs": [nx, ny],
                    "N": int(info.N), "split": [int(info.N1), int(info.N2)], "primes": 3,
                    "l2": "flushed between timed steps (512 MiB write)", "parallelism": "replicas"},
-        "e2e": {"value": digits_per_step / e2e_s * world, "unit": "digits/s",
-                "h2d_bytes_per_step": 4 * (nx + ny), "d2h_bytes_per_step": 4 * L + 8,
-                "ms_per_step": e2e_s * 1e3},
+        "e2e": e2e_out,
         "gpu_launches": int(launches) * args.steps,
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in stages.items()},
         "roofline": roof,
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(x_np, y_np, d.to_host(z), budget_s=args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(x_np, y_np, d.to_host(z), budget_s=args.cpu_seconds,
+                                           digits=digits)
     ctx.close()
     return out
 
 
-def cpu_baseline(x, y, z_gpu=None, budget_s=10.0) -> dict:
+def cpu_baseline(x, y, z_gpu=None, budget_s=10.0, digits=DIGITS) -> dict:
     """The CPU oracle (slow two-prime NTT route, as it stands) on the same 2^24-digit product,
     repeated until about budget_s seconds of CPU work.  Its product also checks, limb by limb, the
     GPU's result of the last timed step."""
@@ -292,8 +299,8 @@ def cpu_baseline(x, y, z_gpu=None, budget_s=10.0) -> dict:
         el = time.perf_counter() - t0
         if el >= budget_s or reps >= 8:
             break
-    out = {"value": 2 * DIGITS * reps / el, "unit": "digits/s", "cores": 1, "kind": "oracle",
-           "sample": f"{reps} full 2^24 x 2^24-digit products by the oracle's two-prime NTT route "
+    out = {"value": 2 * digits * reps / el, "unit": "digits/s", "cores": 1, "kind": "oracle",
+           "sample": f"{reps} full {digits} x {digits}-digit products by the oracle's two-prime NTT route "
                      f"({el:.1f} s, single thread)"}
     if z_gpu is not None:
         out["gpu_result_matches_oracle"] = bool(np.array_equal(np.asarray(z_gpu), ref))
@@ -334,11 +341,14 @@ def run_reference(args, rank, world, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--digits", type=int, default=DIGITS,
+                    help="operand size in decimal digits (profiling of smaller cases only)")
     args = ap.parse_args()
     rank, world, local = _dist()
     if args.impl == "reference":

@@ -55,6 +55,8 @@ typedef struct dmul_ctx dmul_ctx;
                                   /* the four-step form (Sec. 7.1-7.2); results are identical     */
 #define DMUL_FLAG_STAGE_TIMING 2u /* record CUDA events around each pipeline stage (see          */
                                   /* dmul_stage_times); adds a little launch overhead             */
+#define DMUL_FLAG_NO_SMALL 4u     /* never use the fused one-launch path for short products       */
+                                  /* (transform length <= 24576); they take the four-step path    */
 
 typedef struct {
     int device;                /* CUDA device ordinal                                          */

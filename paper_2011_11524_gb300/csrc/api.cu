@@ -204,7 +204,7 @@ int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, si
     rc = set_device(c);
     if (rc) return rc;
     const uint64_t Ns = choose_N_small(L);
-    if (mode == kInvDigits && Ns && !(c->cfg.flags & DMUL_FLAG_SIXSTEP)) {
+    if (mode == kInvDigits && Ns && !(c->cfg.flags & (DMUL_FLAG_SIXSTEP | DMUL_FLAG_NO_SMALL))) {
         // the whole product in one cluster launch (batch.cu): transforms, CRT and carry in SMEM
         SmallPlanEntry *se;
         rc = get_small_plan(c, Ns, &se);

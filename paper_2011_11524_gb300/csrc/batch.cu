@@ -307,30 +307,47 @@ cudaError_t launch_carry_b(const JobDev *jobs, int njobs, uint32_t maxtiles, uin
 static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 void destroy_batch_state(dmul_ctx *c) {
-    BatchState *b = c->batch.get();
-    if (!b) return;
+    if (!c->batch) return;
+    free_batch_state(c, c->batch.get());
+    c->batch.reset();
+}
+
+int init_batch_state(BatchState *b) {
+    for (int i = 0; i < kBatchStreams; ++i) {
+        if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess) return DMUL_ERR_CUDA;
+        if (cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess) return DMUL_ERR_CUDA;
+    }
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return DMUL_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) return DMUL_ERR_CUDA;
+    return DMUL_OK;
+}
+
+void free_batch_state(dmul_ctx *c, BatchState *b) {
+    if (b->done_recorded) cudaEventSynchronize(b->done);
     for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
     b->graphs.clear();
     if (b->arena) dev_free(c, b->arena, b->arena_cap);
     if (b->djobs) dev_free(c, b->djobs, b->jobs_cap * sizeof(JobDev));
     if (b->hjobs) cudaFreeHost(b->hjobs);
+    b->arena = nullptr;
+    b->djobs = nullptr;
+    b->hjobs = nullptr;
     for (int i = 0; i < kBatchStreams; ++i) {
         if (b->streams[i]) cudaStreamDestroy(b->streams[i]);
         if (b->join[i]) cudaEventDestroy(b->join[i]);
+        b->streams[i] = nullptr;
+        b->join[i] = nullptr;
     }
     if (b->fork) cudaEventDestroy(b->fork);
-    c->batch.reset();
+    if (b->done) cudaEventDestroy(b->done);
+    b->fork = b->done = nullptr;
 }
 
 static int batch_state(dmul_ctx *c, BatchState **out) {
     if (!c->batch) {
         c->batch = std::make_unique<BatchState>();
-        BatchState *b = c->batch.get();
-        for (int i = 0; i < kBatchStreams; ++i) {
-            if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess) return DMUL_ERR_CUDA;
-            if (cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess) return DMUL_ERR_CUDA;
-        }
-        if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return DMUL_ERR_CUDA;
+        int rc = init_batch_state(c->batch.get());
+        if (rc) return rc;
     }
     *out = c->batch.get();
     return DMUL_OK;
@@ -338,7 +355,8 @@ static int batch_state(dmul_ctx *c, BatchState **out) {
 
 // Enqueue the launches of every group (on the fork/join streams).
 static int enqueue_groups(dmul_ctx *c, BatchState *b, const std::vector<GroupLaunch> &groups,
-                          cudaStream_t s, size_t njobs, size_t ctl_off, size_t ctl_bytes) {
+                          cudaStream_t s, size_t njobs, size_t ctl_off, size_t ctl_bytes,
+                          uint32_t *status) {
     if (cudaMemcpyAsync(b->djobs, b->hjobs, njobs * sizeof(JobDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return DMUL_ERR_CUDA;
     if (ctl_bytes && cudaMemsetAsync(b->arena + ctl_off, 0, ctl_bytes, s) != cudaSuccess) return DMUL_ERR_CUDA;
@@ -353,15 +371,15 @@ static int enqueue_groups(dmul_ctx *c, BatchState *b, const std::vector<GroupLau
             SmallPlanEntry *se;
             int rc = get_small_plan(c, G.N, &se);
             if (rc) return rc;
-            if (launch_small_mul(se->sp, jd, (int)G.count, c->status, st) != cudaSuccess) return DMUL_ERR_CUDA;
+            if (launch_small_mul(se->sp, jd, (int)G.count, status, st) != cudaSuccess) return DMUL_ERR_CUDA;
         } else {
             PlanEntry *pe;
             int rc = get_plan(c, G.N, &pe);
             if (rc) return rc;
-            if (launch_col_fwd_b(pe->pd, jd, (int)G.count, c->status, st) != cudaSuccess) return DMUL_ERR_CUDA;
+            if (launch_col_fwd_b(pe->pd, jd, (int)G.count, status, st) != cudaSuccess) return DMUL_ERR_CUDA;
             if (launch_row_mul_b(pe->pd, jd, (int)G.count, st) != cudaSuccess) return DMUL_ERR_CUDA;
             if (launch_col_inv_b(pe->pd, jd, (int)G.count, st) != cudaSuccess) return DMUL_ERR_CUDA;
-            if (launch_carry_b(jd, (int)G.count, G.maxtiles, c->status, st) != cudaSuccess) return DMUL_ERR_CUDA;
+            if (launch_carry_b(jd, (int)G.count, G.maxtiles, status, st) != cudaSuccess) return DMUL_ERR_CUDA;
         }
     }
     for (int i = 0; i < kBatchStreams; ++i) {
@@ -372,9 +390,29 @@ static int enqueue_groups(dmul_ctx *c, BatchState *b, const std::vector<GroupLau
 }
 
 int run_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, cudaStream_t s) {
-    if (count == 0) return DMUL_OK;
+    BatchState *b;
     int rc = set_device(c);
     if (rc) return rc;
+    rc = batch_state(c, &b);
+    if (rc) return rc;
+    c->last_stream = s;
+    Timed t(c, kStBatch, s);
+    return run_batch_on(c, b, jobs, count, s, c->status, true);
+}
+
+size_t job_scratch_bytes(const dmul_ctx *c, const dmul_job &j) {
+    const uint64_t L = j.nx + j.ny;
+    if (choose_N_small(L) && !(c->cfg.flags & (DMUL_FLAG_SIXSTEP | DMUL_FLAG_NO_SMALL))) return 0;
+    const uint64_t N = choose_N(L);
+    const bool sq = j.x == j.y && j.nx == j.ny;
+    return align256((size_t)kPrimes * N * 4) * (sq ? 1 : 2) + align256(((L + 31) / 32 + 1) * sizeof(uint2)) +
+           align256(carry_ctl_bytes(L));
+}
+
+int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count, cudaStream_t s,
+                 uint32_t *status, bool use_graph) {
+    if (count == 0) return DMUL_OK;
+    int rc = DMUL_OK;
     // validate and classify
     struct Item { size_t idx; bool small; uint64_t N; bool square; };
     std::vector<Item> items(count);
@@ -388,7 +426,7 @@ int run_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, cudaStream_t s) {
         if (c->cfg.max_limbs && L > c->cfg.max_limbs) return DMUL_ERR_TOO_LARGE;
         Item it{i, false, 0, j.x == j.y && j.nx == j.ny};
         uint64_t Ns = choose_N_small(L);
-        if (Ns && !(c->cfg.flags & DMUL_FLAG_SIXSTEP)) {
+        if (Ns && !(c->cfg.flags & (DMUL_FLAG_SIXSTEP | DMUL_FLAG_NO_SMALL))) {
             it.small = true;
             it.N = Ns;
         } else {
@@ -432,14 +470,11 @@ int run_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, cudaStream_t s) {
         off = align256(off + carry_ctl_bytes(j.nx + j.ny));
     }
     const size_t ctl_bytes = off - ctl_off;
-    const size_t need = std::max<size_t>(off, 256);
-    BatchState *b;
-    rc = batch_state(c, &b);
-    if (rc) return rc;
+    const size_t need = off;  // 0 when every job takes the fused short path
     if (need > b->arena_cap) {
         for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
         b->graphs.clear();
-        if (cudaStreamSynchronize(s) != cudaSuccess) return DMUL_ERR_CUDA;
+        if (b->done_recorded && cudaEventSynchronize(b->done) != cudaSuccess) return DMUL_ERR_CUDA;
         if (b->arena) dev_free(c, b->arena, b->arena_cap);
         b->arena = nullptr;
         b->arena_cap = 0;
@@ -450,7 +485,7 @@ int run_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, cudaStream_t s) {
     if (count > b->jobs_cap) {
         for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
         b->graphs.clear();
-        if (cudaStreamSynchronize(s) != cudaSuccess) return DMUL_ERR_CUDA;
+        if (b->done_recorded && cudaEventSynchronize(b->done) != cudaSuccess) return DMUL_ERR_CUDA;
         if (b->djobs) dev_free(c, b->djobs, b->jobs_cap * sizeof(JobDev));
         if (b->hjobs) cudaFreeHost(b->hjobs);
         b->djobs = nullptr;
@@ -461,8 +496,8 @@ int run_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, cudaStream_t s) {
         if (cudaMallocHost(&b->hjobs, count * sizeof(JobDev)) != cudaSuccess) return DMUL_ERR_NOMEM;
         b->jobs_cap = count;
     }
-    // the previous batch's descriptors may still be in flight (an earlier replay reads hjobs)
-    if (cudaStreamSynchronize(s) != cudaSuccess) return DMUL_ERR_CUDA;
+    // the previous batch on this state may still read its descriptors (hjobs) and arena
+    if (b->done_recorded && cudaEventSynchronize(b->done) != cudaSuccess) return DMUL_ERR_CUDA;
     for (size_t i = 0; i < count; ++i) {
         const Item &it = items[i];
         const dmul_job &j = jobs[it.idx];
@@ -495,18 +530,40 @@ int run_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, cudaStream_t s) {
         else { PlanEntry *pe; rc = get_plan(c, G.N, &pe); }
         if (rc) return rc;
     }
+    if (!use_graph) {
+        // plain launches on one stream (the serving loop's slots: shapes vary, slots overlap)
+        if (cudaMemcpyAsync(b->djobs, b->hjobs, count * sizeof(JobDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return DMUL_ERR_CUDA;
+        if (ctl_bytes && cudaMemsetAsync(b->arena + ctl_off, 0, ctl_bytes, s) != cudaSuccess) return DMUL_ERR_CUDA;
+        for (const GroupLaunch &G : groups) {
+            const JobDev *jd = b->djobs + G.first;
+            if (G.small) {
+                SmallPlanEntry *se;
+                if ((rc = get_small_plan(c, G.N, &se))) return rc;
+                if (launch_small_mul(se->sp, jd, (int)G.count, status, s) != cudaSuccess) return DMUL_ERR_CUDA;
+            } else {
+                PlanEntry *pe;
+                if ((rc = get_plan(c, G.N, &pe))) return rc;
+                if (launch_col_fwd_b(pe->pd, jd, (int)G.count, status, s) != cudaSuccess) return DMUL_ERR_CUDA;
+                if (launch_row_mul_b(pe->pd, jd, (int)G.count, s) != cudaSuccess) return DMUL_ERR_CUDA;
+                if (launch_col_inv_b(pe->pd, jd, (int)G.count, s) != cudaSuccess) return DMUL_ERR_CUDA;
+                if (launch_carry_b(jd, (int)G.count, G.maxtiles, status, s) != cudaSuccess) return DMUL_ERR_CUDA;
+            }
+        }
+        if (cudaEventRecord(b->done, s) != cudaSuccess) return DMUL_ERR_CUDA;
+        b->done_recorded = true;
+        return DMUL_OK;
+    }
     std::vector<std::tuple<int, uint64_t, size_t>> key;
     for (auto &G : groups) key.emplace_back(G.small ? 1 : 0, G.N, G.count);
     for (size_t i = 0; i < count; ++i) key.emplace_back(2, (uint64_t)b->hjobs[i].square, b->hjobs[i].ntiles);
-    c->last_stream = s;
-    Timed t(c, kStBatch, s);
     auto it = b->graphs.find(key);
     if (it == b->graphs.end()) {
         cudaGraph_t graph;
         cudaStream_t cap = b->streams[0];
         // capture on a private stream, joined to s through events
         if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DMUL_ERR_CUDA;
-        rc = enqueue_groups(c, b, groups, cap, count, ctl_off, ctl_bytes);
+        rc = enqueue_groups(c, b, groups, cap, count, ctl_off, ctl_bytes, status);
         cudaError_t ce = cudaStreamEndCapture(cap, &graph);
         if (rc) return rc;
         if (ce != cudaSuccess) return DMUL_ERR_CUDA;
@@ -517,6 +574,8 @@ int run_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, cudaStream_t s) {
         it = b->graphs.emplace(key, exec).first;
     }
     if (cudaGraphLaunch(it->second, s) != cudaSuccess) return DMUL_ERR_CUDA;
+    if (cudaEventRecord(b->done, s) != cudaSuccess) return DMUL_ERR_CUDA;
+    b->done_recorded = true;
     return DMUL_OK;
 }
 

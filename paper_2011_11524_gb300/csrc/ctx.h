@@ -52,6 +52,8 @@ struct BatchState {
     size_t jobs_cap = 0;
     cudaStream_t streams[kBatchStreams] = {};
     cudaEvent_t fork = nullptr, join[kBatchStreams] = {};
+    cudaEvent_t done = nullptr;  // recorded after each batch launched on this state
+    bool done_recorded = false;
     // graph cache keyed by the batch shape
     std::map<std::vector<std::tuple<int, uint64_t, size_t>>, cudaGraphExec_t> graphs;
     };
@@ -117,5 +119,14 @@ struct Timed {
 };
 
 void destroy_batch_state(dmul_ctx *c);
+int init_batch_state(BatchState *b);
+void free_batch_state(dmul_ctx *c, BatchState *b);
+// One batch on a given state (arena, descriptors); device errors go to *status.  use_graph:
+// capture/replay per batch shape with groups forked over the state's streams; otherwise plain
+// launches on s.
+int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count, cudaStream_t s,
+                 uint32_t *status, bool use_graph);
+// Library scratch a job needs on the four-step path (0 for the fused short path).
+size_t job_scratch_bytes(const dmul_ctx *c, const dmul_job &j);
 
 }  // namespace dml

@@ -1,10 +1,24 @@
-// serve.cu -- the serving loop behind dmul_submit / dmul_poll / dmul_wait.
+// serve.cu -- the serving loop behind dmul_submit / dmul_poll / dmul_wait (see serve.h).
 #include "serve.h"
+
+#include <algorithm>
 
 namespace dml {
 
 Server::Server(dmul_ctx *c) : ctx_(c) {
-    cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking);
+    set_device(c);
+    // admission budget for in-flight scratch: what the context's HBM budget leaves free now
+    budget_ = c->budget > c->used ? (c->budget - c->used) : 0;
+    init_ok_ = true;
+    for (int i = 0; i < kSlots; ++i) {
+        auto s = std::make_unique<Slot>();
+        s->owner = this;
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) init_ok_ = false;
+        if (cudaMalloc(&s->status, 64) != cudaSuccess || cudaMemset(s->status, 0, 64) != cudaSuccess)
+            init_ok_ = false;
+        if (init_batch_state(&s->bs) != DMUL_OK) init_ok_ = false;
+        slots_.push_back(std::move(s));
+    }
     worker_ = std::thread([this] { loop(); });
 }
 
@@ -15,16 +29,31 @@ Server::~Server() {
     }
     cv_.notify_all();
     if (worker_.joinable()) worker_.join();
-    if (stream_) cudaStreamDestroy(stream_);
+    set_device(ctx_);
+    for (auto &s : slots_) {
+        if (s->stream) cudaStreamSynchronize(s->stream);
+        free_batch_state(ctx_, &s->bs);
+        if (s->status) cudaFree(s->status);
+        if (s->stream) cudaStreamDestroy(s->stream);
+    }
 }
 
 int Server::submit(const dmul_job &job, uint64_t *ticket) {
+    if (!init_ok_) return DMUL_ERR_CUDA;
+    if (!job.x || !job.y || !job.z || job.nx == 0 || job.ny == 0) return DMUL_ERR_INVALID;
+    const uint64_t L = job.nx + job.ny;
+    if (job.z_cap < L) return DMUL_ERR_CAPACITY;
+    if (!choose_N_small(L) && !choose_N(L)) return DMUL_ERR_TOO_LARGE;
+    const size_t bytes = job_scratch_bytes(ctx_, job);
+    if (bytes > budget_) return DMUL_ERR_NOMEM;
     std::lock_guard<std::mutex> g(mu_);
     uint64_t t = next_++;
-    tickets_[t].job = job;
+    Ticket &tk = tickets_[t];
+    tk.job = job;
+    tk.bytes = bytes;
     queue_.push_back(t);
     *ticket = t;
-    cv_.notify_one();
+    cv_.notify_all();
     return DMUL_OK;
 }
 
@@ -33,37 +62,123 @@ int Server::poll(uint64_t ticket, int *done) {
     auto it = tickets_.find(ticket);
     if (it == tickets_.end()) return DMUL_ERR_UNKNOWN_TICKET;
     *done = it->second.done ? 1 : 0;
-    return DMUL_OK;
+    return it->second.done ? it->second.status : DMUL_OK;
 }
 
 int Server::wait(uint64_t ticket) {
     std::unique_lock<std::mutex> g(mu_);
     auto it = tickets_.find(ticket);
     if (it == tickets_.end()) return DMUL_ERR_UNKNOWN_TICKET;
-    done_cv_.wait(g, [&] { return tickets_[ticket].done; });
-    return tickets_[ticket].status;
+    done_cv_.wait(g, [&] { return it->second.done; });
+    return it->second.status;
 }
 
-void Server::loop() {
-    for (;;) {
-        uint64_t t;
-        dmul_job job;
-        {
-            std::unique_lock<std::mutex> g(mu_);
-            cv_.wait(g, [&] { return stop_ || !queue_.empty(); });
-            if (stop_ && queue_.empty()) return;
-            t = queue_.front();
-            queue_.pop_front();
-            job = tickets_[t].job;
-        }
-        int rc = ctx_enqueue_mul(ctx_, job, stream_);
-        if (rc == DMUL_OK) rc = dmul_sync(ctx_, stream_);
-        {
-            std::lock_guard<std::mutex> g(mu_);
+void CUDART_CB Server::on_done(void *p) {
+    Slot *s = (Slot *)p;
+    Server *self = s->owner;
+    {
+        std::lock_guard<std::mutex> g(self->mu_);
+        s->finished = true;
+    }
+    self->cv_.notify_all();
+}
+
+// A finished slot: read its device status, complete its tickets, release its scratch.
+void Server::retire(Slot &s, std::unique_lock<std::mutex> &g) {
+    std::vector<uint64_t> done;
+    done.swap(s.tickets);
+    s.busy = false;
+    s.finished = false;
+    inflight_ -= s.bytes;
+    s.bytes = 0;
+    g.unlock();
+    uint32_t st = 0;
+    int rc = DMUL_OK;
+    if (cudaMemcpyAsync(&st, s.status, 4, cudaMemcpyDeviceToHost, s.stream) != cudaSuccess ||
+        cudaStreamSynchronize(s.stream) != cudaSuccess) {
+        rc = DMUL_ERR_CUDA;
+    } else if (st) {
+        cudaMemsetAsync(s.status, 0, 4, s.stream);
+        rc = (st & kStatusTimeout) ? DMUL_ERR_TIMEOUT : DMUL_ERR_INVALID;
+    }
+    g.lock();
+    for (uint64_t t : done) {
+        Ticket &tk = tickets_[t];
+        tk.status = rc;
+        tk.done = true;
+    }
+    done_cv_.notify_all();
+}
+
+// Admit pending requests into a free slot and launch them as one batch.
+bool Server::launch(Slot &s, std::unique_lock<std::mutex> &g) {
+    std::vector<dmul_job> jobs;
+    size_t bytes = 0;
+    while (!queue_.empty() && jobs.size() < kMaxBatch) {
+        Ticket &tk = tickets_[queue_.front()];
+        if (inflight_ + bytes + tk.bytes > budget_) break;  // wait for memory to free up
+        bytes += tk.bytes;
+        jobs.push_back(tk.job);
+        s.tickets.push_back(queue_.front());
+        queue_.pop_front();
+    }
+    if (jobs.empty()) return false;
+    s.busy = true;
+    s.bytes = bytes;
+    inflight_ += bytes;
+    g.unlock();
+    int rc = DMUL_OK;
+    void *arena = nullptr;
+    if (bytes) {
+        if (cudaMallocAsync(&arena, bytes, s.stream) != cudaSuccess) rc = DMUL_ERR_NOMEM;
+    }
+    if (rc == DMUL_OK) {
+        // the scratch of this batch is the pool allocation; the state never reallocates it
+        s.bs.arena = (uint8_t *)arena;
+        s.bs.arena_cap = bytes;
+        rc = run_batch_on(ctx_, &s.bs, jobs.data(), jobs.size(), s.stream, s.status, false);
+        s.bs.arena = nullptr;
+        s.bs.arena_cap = 0;
+    }
+    if (arena) cudaFreeAsync(arena, s.stream);
+    if (rc == DMUL_OK && cudaLaunchHostFunc(s.stream, on_done, &s) != cudaSuccess) rc = DMUL_ERR_CUDA;
+    g.lock();
+    if (rc != DMUL_OK) {
+        for (uint64_t t : s.tickets) {
             tickets_[t].status = rc;
             tickets_[t].done = true;
         }
+        s.tickets.clear();
+        s.busy = false;
+        inflight_ -= s.bytes;
+        s.bytes = 0;
         done_cv_.notify_all();
+    }
+    return true;
+}
+
+void Server::loop() {
+    set_device(ctx_);
+    std::unique_lock<std::mutex> g(mu_);
+    for (;;) {
+        cv_.wait(g, [&] {
+            if (stop_) return true;
+            for (auto &s : slots_)
+                if (s->busy && s->finished) return true;
+            if (queue_.empty()) return false;
+            for (auto &s : slots_)
+                if (!s->busy) return true;
+            return false;
+        });
+        for (auto &s : slots_)
+            if (s->busy && s->finished) retire(*s, g);
+        bool any_busy = false;
+        for (auto &s : slots_) any_busy |= s->busy;
+        if (stop_ && queue_.empty() && !any_busy) return;
+        for (auto &s : slots_) {
+            if (queue_.empty()) break;
+            if (!s->busy && !launch(*s, g)) break;  // nothing admissible until memory frees
+        }
     }
 }
 

@@ -5,11 +5,14 @@
 
 #include <condition_variable>
 #include <deque>
-#include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
+#include <unordered_map>
+#include <vector>
 
 #include "../../include/dmul.h"
+#include "ctx.h"
 
 namespace dml {
 
@@ -20,6 +23,14 @@ int ctx_enqueue_mul(dmul_ctx *c, const dmul_job &j, cudaStream_t s);
 int run_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, cudaStream_t s);
 
 // The serving loop behind dmul_submit / dmul_poll / dmul_wait (serve.cu).
+//
+// Continuous batching: a worker thread keeps up to kSlots batches in flight, each on its own
+// stream with its own scratch.  Whenever a slot is free it takes every pending request (FIFO) whose
+// scratch still fits the admission budget, launches them as one batch (grouped by transform
+// length, see batch.cu) and returns to the queue; requests that arrive while batches run join the
+// next one.  Scratch comes from a stream-ordered memory pool (cudaMallocAsync / cudaFreeAsync on
+// the slot's stream), so admitting and retiring batches never synchronizes the device.  A slot's
+// completion is signalled by a host callback on its stream.
 class Server {
   public:
     explicit Server(dmul_ctx *c);
@@ -28,21 +39,42 @@ class Server {
     int poll(uint64_t ticket, int *done);
     int wait(uint64_t ticket);
 
+    static constexpr int kSlots = 4;
+    static constexpr size_t kMaxBatch = 1024;
+
   private:
     struct Ticket {
         dmul_job job;
+        size_t bytes = 0;
         int status = DMUL_OK;
         bool done = false;
     };
+    struct Slot {
+        Server *owner = nullptr;
+        BatchState bs;
+        cudaStream_t stream = nullptr;
+        uint32_t *status = nullptr;  // device status word of this slot's batches
+        std::vector<uint64_t> tickets;
+        size_t bytes = 0;
+        void *arena = nullptr;
+        bool busy = false;
+        bool finished = false;
+    };
+    static void CUDART_CB on_done(void *slot);
     void loop();
+    void retire(Slot &s, std::unique_lock<std::mutex> &g);
+    bool launch(Slot &s, std::unique_lock<std::mutex> &g);
+
     dmul_ctx *ctx_;
     std::mutex mu_;
     std::condition_variable cv_, done_cv_;
     std::deque<uint64_t> queue_;
-    std::map<uint64_t, Ticket> tickets_;
+    std::unordered_map<uint64_t, Ticket> tickets_;
     uint64_t next_ = 1;
     bool stop_ = false;
-    cudaStream_t stream_ = nullptr;
+    bool init_ok_ = false;
+    std::vector<std::unique_ptr<Slot>> slots_;
+    size_t budget_ = 0, inflight_ = 0;
     std::thread worker_;
 };
 

@@ -173,7 +173,7 @@ def run_ours(args, rank, world, local):
     y = d.to_device(y_np, dev)
     z = torch.empty(L, dtype=torch.int32, device=dev)
     nz = torch.zeros(1, dtype=torch.int64, device=dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    flush = torch.empty(max(1, args.flush_mb) << 20, dtype=torch.uint8, device=dev)
     sptr = stream.cuda_stream
 
     def step():
@@ -271,7 +271,7 @@ def run_ours(args, rank, world, local):
         "config": {"workload": WORKLOAD if digits == DIGITS else f"{digits} x {digits}-digit random multiplication",
                    "digits_x": digits, "digits_y": digits, "limbs": [nx, ny],
                    "N": int(info.N), "split": [int(info.N1), int(info.N2)], "primes": 3,
-                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": "replicas"},
+                   "l2": f"flushed between timed steps ({args.flush_mb} MiB write)", "parallelism": "replicas"},
         "e2e": e2e_out,
         "gpu_launches": int(launches) * args.steps,
         "stages_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in stages.items()},
@@ -347,6 +347,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--flush-mb", type=int, default=512,
+                    help="L2 flush buffer written between timed steps (MiB); profiling runs use 1")
     ap.add_argument("--digits", type=int, default=DIGITS,
                     help="operand size in decimal digits (profiling of smaller cases only)")
     args = ap.parse_args()

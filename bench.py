@@ -278,11 +278,172 @@ def run_ours(args, rank, world, local):
         "roofline": roof,
         "clocks": clk,
     }
+    if rank == 0 and not args.no_forms:
+        out["other_configs"] = run_other_configs(d, torch, dev, flush, stream)
+        out["batched"] = run_batched(d, torch, dev)
+        out["served"] = run_served(d, torch, dev)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(x_np, y_np, d.to_host(z), budget_s=args.cpu_seconds,
                                            digits=digits)
     ctx.close()
     return out
+
+
+def _upload_jobs(d, torch, jobs, dev):
+    """Operands of a job list on the device (squarings share x), outputs allocated."""
+    import numpy as np
+    out = []
+    for j in jobs:
+        tx = torch.from_numpy(j.x.view(np.int32)).to(dev)
+        ty = tx if j.square else torch.from_numpy(j.y.view(np.int32)).to(dev)
+        L = len(j.x) + len(j.y)
+        out.append((tx, len(j.x), ty, len(j.y), torch.empty(L, dtype=torch.int32, device=dev), L,
+                    torch.zeros(1, dtype=torch.int64, device=dev)))
+    return out
+
+
+def time_product(d, torch, dev, ctx, x_np, y_np, reps, flush, stream, square=False):
+    """Median device time (ms) of one product through dmul_mul, L2 flushed before each run."""
+    import numpy as np
+    x = d.to_device(x_np, dev)
+    y = x if square else d.to_device(y_np, dev)
+    L = len(x_np) + len(y_np)
+    z = torch.empty(L, dtype=torch.int32, device=dev)
+    nz = torch.zeros(1, dtype=torch.int64, device=dev)
+    sp = stream.cuda_stream
+    ts = []
+    with torch.cuda.stream(stream):
+        for i in range(reps + 2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc = d.dmul_mul(ctx.handle, x, len(x_np), y, len(y_np), z, L, nz, sp)
+            e1.record(stream)
+            assert rc == 0
+            torch.cuda.synchronize()
+            if i >= 2:
+                ts.append(e0.elapsed_time(e1))
+    assert d.dmul_sync(ctx.handle, sp) == 0
+    return float(np.median(ts))
+
+
+def run_other_configs(d, torch, dev, flush, stream) -> dict:
+    """The other workload configurations, one product each (median of several runs)."""
+    from paper_2011_11524_gb300 import workloads as wl
+    out = {}
+    with d.Context(dev.index or 0) as ctx:
+        x, y = wl.c1_pair()
+        ms = time_product(d, torch, dev, ctx, x, y, 50, flush, stream)
+        out["c1_100k_x_100k"] = {"ms": ms, "digits_per_s": 200_000 / (ms * 1e-3)}
+        x, y = wl.c2_random_pair()
+        ms = time_product(d, torch, dev, ctx, x, x, 10, flush, stream, square=True)
+        out["c2_2e24_sqr"] = {"ms": ms, "digits_per_s": 2 * DIGITS / (ms * 1e-3)}
+        xn, yn = wl.c2_nines_pair()
+        ms = time_product(d, torch, dev, ctx, xn, yn, 10, flush, stream)
+        out["c2_2e24_nines_mul"] = {"ms": ms, "digits_per_s": 2 * DIGITS / (ms * 1e-3)}
+        for name, (a, b), nd in zip(("c3a_64M_x_1M", "c3b_32M_x_16M"), wl.c3_pairs(),
+                                    (65_000_000, 48_000_000)):
+            ms = time_product(d, torch, dev, ctx, a, b, 10, flush, stream)
+            out[name] = {"ms": ms, "digits_per_s": nd / (ms * 1e-3)}
+    with d.Context(dev.index or 0, flags=d.DMUL_FLAG_SIXSTEP) as ctx6:
+        x, y = wl.c2_random_pair()
+        ms = time_product(d, torch, dev, ctx6, x, y, 5, flush, stream)
+        out["c2_2e24_mul_sixstep"] = {"ms": ms, "digits_per_s": 2 * DIGITS / (ms * 1e-3),
+                                      "note": "six-step form with the in-place transposes (Sec. 7.2, 7.6)"}
+    return out
+
+
+def run_batched(d, torch, dev, reps=3, count=4096):
+    """4096 independent products, operand sizes log-uniform over 10^3..10^6 digits, 20% squarings:
+    one dmul_batch call (grouped launches, replayed CUDA graph) against the same jobs issued one
+    at a time through dmul_mul."""
+    from paper_2011_11524_gb300 import workloads as wl
+    jobs = wl.c4_jobs(count)
+    dj = _upload_jobs(d, torch, jobs, dev)
+    arr = d.make_jobs(dj)
+    digits = sum(len(j.x) + len(j.y) for j in jobs) * 9
+    ctx = d.Context(dev.index or 0)
+    stream = torch.cuda.Stream(device=dev)
+    sp = stream.cuda_stream
+    for _ in range(2):  # plans, autotuning, graph capture
+        assert d.dmul_batch(ctx.handle, arr, len(dj), sp) == 0
+    assert d.dmul_sync(ctx.handle, sp) == 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        assert d.dmul_batch(ctx.handle, arr, len(dj), sp) == 0
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    assert d.dmul_sync(ctx.handle, sp) == 0
+    # the plain form, one product at a time on the same stream
+    for (tx, nx, ty, ny, z, L, nz) in dj[:64]:
+        d.dmul_mul(ctx.handle, tx, nx, ty, ny, z, L, nz, sp)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    t0 = time.perf_counter()
+    for (tx, nx, ty, ny, z, L, nz) in dj:
+        rc = d.dmul_mul(ctx.handle, tx, nx, ty, ny, z, L, nz, sp)
+        assert rc == 0
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3)
+    assert d.dmul_sync(ctx.handle, sp) == 0
+    ctx.close()
+    return {"workload": f"{count} jobs, digits log-uniform 10^3..10^6 per operand, 20% squarings",
+            "mults_per_s": count / (best * 1e-3), "digits_per_s": digits / (best * 1e-3),
+            "ms_per_batch": best, "plain_mults_per_s": count / (plain_ms * 1e-3),
+            "plain_ms_for_same_jobs": plain_ms, "speedup_vs_plain": plain_ms / best}
+
+
+def run_served(d, torch, dev, count=2000, load=0.7, budget_gib=8):
+    """Poisson stream of requests (digits log-uniform 10^2..10^7, 30% squarings) into the serving
+    loop at `load` x its measured saturated rate; p50/p99 latency from arrival to completion."""
+    from paper_2011_11524_gb300 import workloads as wl
+    _, jobs = wl.c5_stream(1.0, count)
+    dj = _upload_jobs(d, torch, jobs, dev)
+    arr = d.make_jobs(dj)
+    budget = budget_gib << 30
+    # saturated rate: everything submitted at once
+    with d.Context(dev.index or 0, hbm_budget_bytes=budget) as srv:
+        for i in range(min(64, count)):  # plans and autotuning outside the measurement
+            d.dmul_wait(srv.handle, d.dmul_submit(srv.handle, arr[i])[1])
+        t0 = time.perf_counter()
+        tk = [d.dmul_submit(srv.handle, arr[i])[1] for i in range(count)]
+        for t in tk:
+            assert d.dmul_wait(srv.handle, t) == 0
+        sat = count / (time.perf_counter() - t0)
+        rate = load * sat
+        arrivals, _ = wl.c5_stream(rate, count)
+        # one thread: submit at each arrival time, and in between watch the oldest outstanding
+        # ticket (completion is observed in arrival order)
+        tickets = [0] * count
+        done_t = [0.0] * count
+        start = time.perf_counter() + 0.05
+        i = head = 0
+        while head < count:
+            now = time.perf_counter()
+            if i < count and now >= start + float(arrivals[i]):
+                rc, tickets[i] = d.dmul_submit(srv.handle, arr[i])
+                assert rc == 0
+                i += 1
+                continue
+            if head < i:
+                rc, done = d.dmul_poll(srv.handle, tickets[head])
+                assert rc == 0
+                if done:
+                    done_t[head] = now
+                    head += 1
+        lat = sorted((done_t[i] - (start + float(arrivals[i]))) * 1e3 for i in range(count))
+        wall = max(done_t) - start
+    digits = sum(len(j.x) + len(j.y) for j in jobs) * 9
+    return {"workload": f"{count} Poisson requests, digits log-uniform 10^2..10^7, 30% squarings",
+            "hbm_budget_gib": budget_gib, "saturated_mults_per_s": sat, "offered_rate_per_s": rate,
+            "mults_per_s": count / wall, "digits_per_s": digits / wall,
+            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
 
 
 def cpu_baseline(x, y, z_gpu=None, budget_s=10.0, digits=DIGITS) -> dict:
@@ -347,6 +508,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched (4096 jobs) and served (Poisson stream) measurements")
     ap.add_argument("--flush-mb", type=int, default=512,
                     help="L2 flush buffer written between timed steps (MiB); profiling runs use 1")
     ap.add_argument("--digits", type=int, default=DIGITS,

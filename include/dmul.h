@@ -57,6 +57,10 @@ typedef struct dmul_ctx dmul_ctx;
                                   /* dmul_stage_times); adds a little launch overhead             */
 #define DMUL_FLAG_NO_SMALL 4u     /* never use the fused one-launch path for short products       */
                                   /* (transform length <= 24576); they take the four-step path    */
+#define DMUL_FLAG_NO_AUTOTUNE 8u  /* plan every length with the default split instead of timing   */
+                                  /* the candidate splits and CTA sizes on first use              */
+#define DMUL_FLAG_ROW_TMA 16u     /* with DMUL_FLAG_NO_AUTOTUNE: use the persistent row pass fed  */
+                                  /* by bulk asynchronous copies (TMA) instead of one CTA per row */
 
 typedef struct {
     int device;                /* CUDA device ordinal                                          */

@@ -79,16 +79,9 @@ void dev_free(dmul_ctx *c, void *p, size_t bytes) {
     c->used -= bytes;
 }
 
-int get_plan(dmul_ctx *c, uint64_t N, PlanEntry **out) {
-    auto it = c->plans.find(N);
-    if (it != c->plans.end()) {
-        *out = it->second.get();
-        return DMUL_OK;
-    }
+static int build_plan_entry(dmul_ctx *c, const HostPlan &hp, std::unique_ptr<PlanEntry> *out) {
     auto pe = std::make_unique<PlanEntry>();
-    const bool six = (c->cfg.flags & DMUL_FLAG_SIXSTEP) != 0;
-    if (!(six ? make_host_plan_sixstep(N, &pe->hp) : make_host_plan(N, &pe->hp)))
-        return DMUL_ERR_TOO_LARGE;
+    pe->hp = hp;
     std::vector<uint32_t> tab[kPrimes];
     build_tables(pe->hp, &pe->pd, tab);
     size_t words = tab[0].size();
@@ -100,6 +93,143 @@ int get_plan(dmul_ctx *c, uint64_t N, PlanEntry **out) {
         CK(cudaMemcpy(dst, tab[i].data(), words * sizeof(uint32_t), cudaMemcpyHostToDevice));
         pe->pd.tw[i] = (const uint2 *)dst;
     }
+    *out = std::move(pe);
+    return DMUL_OK;
+}
+
+int ensure_scratch(dmul_ctx *c, uint64_t N, uint64_t L, bool need_y);
+
+// Autotuner: the first time a transform length is planned (never inside a capture: plans are
+// built before any capture begins), time the forward column pass, the fused row pass and the
+// inverse column pass of a full-length product for every candidate split N1 x N2 and CTA size,
+// and keep the fastest.  Results are identical for every candidate (the arithmetic is exact);
+// only the time differs.
+static int autotune_plan(dmul_ctx *c, uint64_t N, std::unique_ptr<PlanEntry> *best) {
+    std::vector<uint32_t> n1s;
+    for (uint32_t n1 : candidate_n1(N))
+        if (n1 >= 64 && N / n1 >= 256) n1s.push_back(n1);
+    HostPlan def;
+    if (!make_host_plan(N, &def)) return DMUL_ERR_TOO_LARGE;
+    if (n1s.empty()) n1s.push_back(def.N1);
+    // the timing runs reuse the plain form's scratch: earlier work on any stream must be done
+    CK(cudaDeviceSynchronize());
+    int rc = ensure_scratch(c, N, N, true);
+    if (rc) return rc;
+    uint32_t *in = nullptr, *zt = nullptr;
+    uint2 *sp = nullptr;
+    const size_t nsp = N / 32 + 1;
+    rc = dev_alloc(c, (void **)&in, N * 4);
+    if (!rc) rc = dev_alloc(c, (void **)&zt, N * 4);
+    if (!rc) rc = dev_alloc(c, (void **)&sp, nsp * sizeof(uint2));
+    if (rc) {
+        dev_free(c, in, N * 4);
+        dev_free(c, zt, N * 4);
+        return rc;
+    }
+    cudaStream_t s = c->own_stream;
+    int sms_i = 152;
+    cudaDeviceGetAttribute(&sms_i, cudaDevAttrMultiProcessorCount, c->device);
+    const uint32_t sms = (uint32_t)sms_i;
+    cudaMemsetAsync(in, 0, N * 4, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    for (uint32_t n1 : n1s) {
+        HostPlan hp;
+        if (!make_host_plan(N, &hp, n1)) continue;
+        std::unique_ptr<PlanEntry> cand;
+        rc = build_plan_entry(c, hp, &cand);
+        if (rc) break;
+        float cand_ms = 1e30f;
+        uint32_t cand_ct = 0, cand_rt = 0, cand_tma = 0, cand_grid = 0;
+        // row-pass variants: plain (one CTA per row) or persistent TMA-fed with G CTAs per prime
+        std::vector<std::pair<uint32_t, uint32_t>> rowv = {{0u, 0u}};
+        if (6ull * (N / n1) * 4 + 16 <= 227ull * 1024)
+            for (uint32_t G : {sms / 3, 2 * sms / 3, sms})
+                if (G >= 1 && G <= n1) rowv.push_back({1u, G});
+        for (uint32_t ct : {256u, 512u}) {
+            for (uint32_t rt : {128u, 256u}) {
+                for (auto rv : rowv) {
+                    cand->pd.col_threads = ct;
+                    cand->pd.row_threads = rt;
+                    cand->pd.row_tma = rv.first;
+                    cand->pd.row_grid = rv.second;
+                    float t = 1e30f;
+                    for (int it = 0; it < 3; ++it) {
+                        cudaEventRecord(e0, s);
+                        launch_col_fwd(cand->pd, in, N / 2, in + N / 2, N / 2, c->X, c->Y, c->status, s);
+                        if (rv.first) launch_row_mul_tma(cand->pd, c->X, c->Y, false, c->status, s);
+                        else launch_row_mul(cand->pd, c->X, c->Y, false, s);
+                        launch_col_inv(cand->pd, c->X, N, kInvDigits, zt, sp, s);
+                        cudaEventRecord(e1, s);
+                        cudaEventSynchronize(e1);
+                        float ms = 0;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if (it > 0) t = std::min(t, ms);  // the first run warms up
+                    }
+                    if (cudaGetLastError() != cudaSuccess) t = 1e30f;
+                    if (t < cand_ms) {
+                        cand_ms = t;
+                        cand_ct = ct;
+                        cand_rt = rt;
+                        cand_tma = rv.first;
+                        cand_grid = rv.second;
+                    }
+                }
+            }
+        }
+        if (cand_ms < best_ms) {
+            best_ms = cand_ms;
+            cand->hp.col_threads = cand_ct;
+            cand->hp.row_threads = cand_rt;
+            cand->hp.row_tma = cand_tma;
+            cand->hp.row_grid = cand_grid;
+            if (*best) dev_free(c, (*best)->dtables, (*best)->bytes);
+            *best = std::move(cand);
+        } else {
+            dev_free(c, cand->dtables, cand->bytes);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    uint32_t zero = 0;
+    cudaMemcpy(c->status, &zero, 4, cudaMemcpyHostToDevice);
+    dev_free(c, in, N * 4);
+    dev_free(c, zt, N * 4);
+    dev_free(c, sp, nsp * sizeof(uint2));
+    if (!*best) return rc ? rc : DMUL_ERR_CUDA;
+    (*best)->pd.col_threads = (*best)->hp.col_threads;
+    (*best)->pd.row_threads = (*best)->hp.row_threads;
+    (*best)->pd.row_tma = (*best)->hp.row_tma;
+    (*best)->pd.row_grid = (*best)->hp.row_grid;
+    return DMUL_OK;
+}
+
+int get_plan(dmul_ctx *c, uint64_t N, PlanEntry **out) {
+    auto it = c->plans.find(N);
+    if (it != c->plans.end()) {
+        *out = it->second.get();
+        return DMUL_OK;
+    }
+    std::unique_ptr<PlanEntry> pe;
+    const bool six = (c->cfg.flags & DMUL_FLAG_SIXSTEP) != 0;
+    int rc;
+    if (six || (c->cfg.flags & DMUL_FLAG_NO_AUTOTUNE)) {
+        HostPlan hp;
+        if (!(six ? make_host_plan_sixstep(N, &hp) : make_host_plan(N, &hp))) return DMUL_ERR_TOO_LARGE;
+        if (!six && (c->cfg.flags & DMUL_FLAG_ROW_TMA) && 6ull * hp.N2 * 4 + 16 <= 227ull * 1024) {
+            int sms = 152;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+            hp.row_tma = 1;
+            hp.row_grid = std::max<uint32_t>(1, std::min<uint32_t>(hp.N1, (uint32_t)sms / 3));
+        }
+        rc = build_plan_entry(c, hp, &pe);
+    } else {
+        rc = autotune_plan(c, N, &pe);
+    }
+    if (rc) return rc;
     *out = pe.get();
     c->plans[N] = std::move(pe);
     return DMUL_OK;
@@ -251,7 +381,8 @@ int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
             CK(launch_col_fwd(pd, x, nx, square ? nullptr : y, ny, c->X, c->Y, c->status, s));
         }
         Timed t(c, kStRowMul, s);
-        CK(launch_row_mul(pd, c->X, c->Y, square, s));
+        if (pd.row_tma) CK(launch_row_mul_tma(pd, c->X, c->Y, square, c->status, s));
+        else CK(launch_row_mul(pd, c->X, c->Y, square, s));
         return DMUL_OK;
     }
     // Six-step form (Sec. 7.2): [N1 x N2] -> transpose -> row DFTs of length N1 -> transpose
@@ -347,6 +478,10 @@ int dmul_get_plan(const dmul_ctx *ctx, uint64_t L, dmul_plan_info *out) {
     if (!N) return DMUL_ERR_TOO_LARGE;
     HostPlan hp;
     if (!(six ? make_host_plan_sixstep(N, &hp) : make_host_plan(N, &hp))) return DMUL_ERR_TOO_LARGE;
+    if (ctx) {
+        auto it = ctx->plans.find(N);
+        if (it != ctx->plans.end()) hp = it->second->hp;  // the split the autotuner chose
+    }
     memset(out, 0, sizeof(*out));
     for (int i = 0; i < kPrimes; ++i) out->primes[i] = kPrimeSet[i];
     out->N = hp.N;
@@ -524,22 +659,29 @@ int dmul_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, void *stream) {
     return dml::run_batch(c, jobs, count, (cudaStream_t)stream);
 }
 
+static dml::Server *server_of(dmul_ctx *c, bool create) {
+    std::lock_guard<std::mutex> g(c->server_mu);
+    if (!c->server && create) c->server = std::make_unique<dml::Server>(c);
+    return c->server.get();
+}
+
 int dmul_submit(dmul_ctx *c, const dmul_job *job, uint64_t *ticket) {
     if (!c || !job || !ticket) return DMUL_ERR_INVALID;
-    if (!c->server) c->server = std::make_unique<dml::Server>(c);
-    return c->server->submit(*job, ticket);
+    return server_of(c, true)->submit(*job, ticket);
 }
 
 int dmul_poll(dmul_ctx *c, uint64_t ticket, int *done) {
     if (!c || !done) return DMUL_ERR_INVALID;
-    if (!c->server) return DMUL_ERR_UNKNOWN_TICKET;
-    return c->server->poll(ticket, done);
+    dml::Server *s = server_of(c, false);
+    if (!s) return DMUL_ERR_UNKNOWN_TICKET;
+    return s->poll(ticket, done);
 }
 
 int dmul_wait(dmul_ctx *c, uint64_t ticket) {
     if (!c) return DMUL_ERR_INVALID;
-    if (!c->server) return DMUL_ERR_UNKNOWN_TICKET;
-    return c->server->wait(ticket);
+    dml::Server *s = server_of(c, false);
+    if (!s) return DMUL_ERR_UNKNOWN_TICKET;
+    return s->wait(ticket);
 }
 
 int dmul_stage_times(dmul_ctx *c, const char **names, double *ms, uint64_t *launches, int *n) {

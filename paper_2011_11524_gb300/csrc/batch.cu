@@ -36,7 +36,7 @@ DMUL_DEFINE_UPLOAD(upload_constants_batch)
 // fused small product
 // ---------------------------------------------------------------------------------------------
 template <int PI>
-__device__ void small_transform(const SmallPlanDev &sp, const JobDev &J, uint32_t *sx, uint32_t *sy,
+__device__ __forceinline__ void small_transform(const SmallPlanDev &sp, const JobDev &J, uint32_t *sx, uint32_t *sy,
                                 uint32_t *status) {
     const uint32_t N = sp.N;
     const uint2 *tw = sp.tw[PI];
@@ -81,7 +81,7 @@ __device__ void small_transform(const SmallPlanDev &sp, const JobDev &J, uint32_
 
 // Carry recurrence over the whole (short) product in one CTA: every thread maps a contiguous
 // segment, a block scan of the carry maps gives each segment its incoming carry.
-__device__ void small_carry(const JobDev &J, const uint2 *spb, uint32_t *status) {
+__device__ __forceinline__ void small_carry(const JobDev &J, const uint2 *spb, uint32_t *status) {
     __shared__ uint32_t s_w[32];
     __shared__ uint64_t s_top[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -181,6 +181,84 @@ __global__ void __launch_bounds__(512) k_small_mul(const SmallPlanDev sp, const 
     small_carry(J, spb, status);
 }
 
+// Persistent form: the cluster's rank-0 CTA draws the next job from the counter and hands it to
+// the other two through distributed shared memory; all three then run the job as k_small_mul
+// does.  The loop ends when the counter passes the job count.
+__global__ void __launch_bounds__(512) k_small_persist(const SmallPlanDev *__restrict__ plans,
+                                                       const JobDev *__restrict__ jobs, uint32_t njobs,
+                                                       uint32_t maxN, uint32_t *counter,
+                                                       uint32_t *status) {
+    extern __shared__ uint32_t sm[];
+    __shared__ uint32_t s_job;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int pi = (int)cluster.block_rank();
+    uint32_t *sx = sm, *sy = sm + maxN;
+    uint2 *spb = (uint2 *)(sm + 2 * maxN);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (;;) {
+        if (pi == 0 && threadIdx.x == 0) {
+            const uint32_t j = atomicAdd(counter, 1u);
+            for (int r = 0; r < kPrimes; ++r) *cluster.map_shared_rank(&s_job, r) = j;
+        }
+        cluster.sync();
+        const uint32_t j = s_job;
+        if (j >= njobs) break;
+        const JobDev J = jobs[j];
+        const SmallPlanDev &sp = plans[J.plan];
+        DMUL_PRIME_SWITCH(pi, (small_transform<PI>(sp, J, sx, sy, status)));
+        cluster.sync();
+        const uint32_t *s0 = cluster.map_shared_rank(sx, 0);
+        const uint32_t *s1 = cluster.map_shared_rank(sx, 1);
+        const uint32_t *s2 = cluster.map_shared_rank(sx, 2);
+        uint2 *sp0 = cluster.map_shared_rank(spb, 0);
+        const uint32_t nch = (uint32_t)((J.L + 31) >> 5);
+        for (uint32_t c = pi + kPrimes * warp; c < nch; c += kPrimes * nw) {
+            const uint32_t k = c * 32 + lane;
+            uint32_t d0, d1, d2;
+            crt_digits(s0[swz(k)], s1[swz(k)], s2[swz(k)], d0, d1, d2);
+            uint32_t sv;
+            uint2 spv;
+            chunk_digits(d0, d1, d2, sv, spv);
+            if (k < J.L) J.z[k] = sv;
+            if (lane == 31) sp0[c] = spv;
+        }
+        __threadfence();
+        cluster.sync();
+        if (pi == 0) small_carry(J, spb, status);
+        cluster.sync();  // shared memory is reused by the next job
+    }
+}
+
+cudaError_t launch_small_persistent(const SmallPlanDev *plans, uint32_t maxN, const JobDev *jobs,
+                                    uint32_t njobs, uint32_t *counter, uint32_t *status, cudaStream_t s) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(maxN >= 8192 ? 512 : 256, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)2 * maxN * 4 + (size_t)(maxN / 32) * sizeof(uint2);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kPrimes;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    cfg.gridDim = dim3(kPrimes, 1, 1);
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_small_persist, &cfg) != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        clusters = sms / kPrimes;
+    }
+    uint32_t n = std::min<uint32_t>(njobs, (uint32_t)std::max(1, clusters));
+    cfg.gridDim = dim3(kPrimes * n, 1, 1);
+    return cudaLaunchKernelEx(&cfg, k_small_persist, plans, jobs, njobs, maxN, counter, status);
+}
+
 static size_t small_smem(uint32_t N) { return (size_t)2 * N * 4 + (size_t)(N / 32) * sizeof(uint2); }
 
 static cudaError_t small_launch(const SmallPlanDev &sp, const JobDev *jobs, int njobs, const JobDev &one,
@@ -259,6 +337,8 @@ cudaError_t init_kernel_attributes_batch() {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_small_mul, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)small_smem(kSmallMaxN))) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_small_persist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)small_smem(kSmallMaxN))) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_col_fwd_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kMaxN1 * 32 * 4)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_row_mul_b, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -269,20 +349,20 @@ cudaError_t init_kernel_attributes_batch() {
 cudaError_t launch_col_fwd_b(const PlanDev &pd, const JobDev *jobs, int njobs, uint32_t *status,
                              cudaStream_t s) {
     dim3 grid(kPrimes * (pd.N2 / 32), 2, (unsigned)njobs);
-    k_col_fwd_b<<<grid, pd.N1 >= 512 ? 512 : 256, (size_t)pd.N1 * 32 * 4, s>>>(pd, jobs, status);
+    k_col_fwd_b<<<grid, pd.col_threads, (size_t)pd.N1 * 32 * 4, s>>>(pd, jobs, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_row_mul_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s) {
     dim3 grid(pd.N1, kPrimes, (unsigned)njobs);
-    k_row_mul_b<<<grid, 256, (size_t)2 * pd.N2 * 4, s>>>(pd, jobs);
+    k_row_mul_b<<<grid, pd.row_threads, (size_t)2 * pd.N2 * 4, s>>>(pd, jobs);
     return cudaGetLastError();
 }
 
 cudaError_t launch_col_inv_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kPrimes * (pd.N2 / 32), 1, (unsigned)njobs);
-    cfg.blockDim = dim3(pd.N1 >= 512 ? 512 : 256, 1, 1);
+    cfg.blockDim = dim3(pd.col_threads, 1, 1);
     cfg.dynamicSmemBytes = (size_t)pd.N1 * 32 * 4;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
@@ -340,6 +420,12 @@ void free_batch_state(dmul_ctx *c, BatchState *b) {
     }
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->done) cudaEventDestroy(b->done);
+    if (b->dcounter) dev_free(c, b->dcounter, 256);
+    if (b->dplans) dev_free(c, b->dplans, kMaxSmallPlans * sizeof(SmallPlanDev));
+    if (b->hplans) cudaFreeHost(b->hplans);
+    b->dcounter = nullptr;
+    b->dplans = nullptr;
+    b->hplans = nullptr;
     b->fork = b->done = nullptr;
 }
 
@@ -354,34 +440,57 @@ static int batch_state(dmul_ctx *c, BatchState **out) {
 }
 
 // Enqueue the launches of every group (on the fork/join streams).
-static int enqueue_groups(dmul_ctx *c, BatchState *b, const std::vector<GroupLaunch> &groups,
-                          cudaStream_t s, size_t njobs, size_t ctl_off, size_t ctl_bytes,
-                          uint32_t *status) {
+// Every short product of the batch runs in one persistent launch; each group of longer products
+// of one transform length runs as the four batched pipeline launches.  Work items are spread over
+// the given streams.
+struct SmallLaunch {
+    size_t first = 0, count = 0;
+    uint32_t maxN = 0;
+    size_t nplans = 0;
+};
+
+static int launch_work(dmul_ctx *c, BatchState *b, const std::vector<GroupLaunch> &groups,
+                       const SmallLaunch &sl, cudaStream_t *streams, int nstreams, uint32_t *status) {
+    int si = 0;
+    if (sl.count) {
+        if (launch_small_persistent(b->dplans, sl.maxN, b->djobs + sl.first, (uint32_t)sl.count, b->dcounter,
+                                    status, streams[si++ % nstreams]) != cudaSuccess)
+            return DMUL_ERR_CUDA;
+    }
+    for (const GroupLaunch &G : groups) {
+        if (G.small) continue;
+        cudaStream_t st = streams[si++ % nstreams];
+        const JobDev *jd = b->djobs + G.first;
+        PlanEntry *pe;
+        int rc = get_plan(c, G.N, &pe);
+        if (rc) return rc;
+        if (launch_col_fwd_b(pe->pd, jd, (int)G.count, status, st) != cudaSuccess) return DMUL_ERR_CUDA;
+        if (launch_row_mul_b(pe->pd, jd, (int)G.count, st) != cudaSuccess) return DMUL_ERR_CUDA;
+        if (launch_col_inv_b(pe->pd, jd, (int)G.count, st) != cudaSuccess) return DMUL_ERR_CUDA;
+        if (launch_carry_b(jd, (int)G.count, G.maxtiles, status, st) != cudaSuccess) return DMUL_ERR_CUDA;
+    }
+    return DMUL_OK;
+}
+
+// Descriptor uploads and zeroing of the control words, then the work.
+static int upload_and_launch(dmul_ctx *c, BatchState *b, const std::vector<GroupLaunch> &groups,
+                             const SmallLaunch &sl, cudaStream_t s, size_t njobs, size_t ctl_off,
+                             size_t ctl_bytes, uint32_t *status, bool fork) {
     if (cudaMemcpyAsync(b->djobs, b->hjobs, njobs * sizeof(JobDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return DMUL_ERR_CUDA;
+    if (sl.count) {
+        if (cudaMemcpyAsync(b->dplans, b->hplans, sl.nplans * sizeof(SmallPlanDev), cudaMemcpyHostToDevice, s) !=
+                cudaSuccess ||
+            cudaMemsetAsync(b->dcounter, 0, sizeof(uint32_t), s) != cudaSuccess)
+            return DMUL_ERR_CUDA;
+    }
     if (ctl_bytes && cudaMemsetAsync(b->arena + ctl_off, 0, ctl_bytes, s) != cudaSuccess) return DMUL_ERR_CUDA;
+    if (!fork) return launch_work(c, b, groups, sl, &s, 1, status);
     if (cudaEventRecord(b->fork, s) != cudaSuccess) return DMUL_ERR_CUDA;
     for (int i = 0; i < kBatchStreams; ++i)
         if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) return DMUL_ERR_CUDA;
-    for (size_t g = 0; g < groups.size(); ++g) {
-        const GroupLaunch &G = groups[g];
-        cudaStream_t st = b->streams[g % kBatchStreams];
-        const JobDev *jd = b->djobs + G.first;
-        if (G.small) {
-            SmallPlanEntry *se;
-            int rc = get_small_plan(c, G.N, &se);
-            if (rc) return rc;
-            if (launch_small_mul(se->sp, jd, (int)G.count, status, st) != cudaSuccess) return DMUL_ERR_CUDA;
-        } else {
-            PlanEntry *pe;
-            int rc = get_plan(c, G.N, &pe);
-            if (rc) return rc;
-            if (launch_col_fwd_b(pe->pd, jd, (int)G.count, status, st) != cudaSuccess) return DMUL_ERR_CUDA;
-            if (launch_row_mul_b(pe->pd, jd, (int)G.count, st) != cudaSuccess) return DMUL_ERR_CUDA;
-            if (launch_col_inv_b(pe->pd, jd, (int)G.count, st) != cudaSuccess) return DMUL_ERR_CUDA;
-            if (launch_carry_b(jd, (int)G.count, G.maxtiles, status, st) != cudaSuccess) return DMUL_ERR_CUDA;
-        }
-    }
+    int rc = launch_work(c, b, groups, sl, b->streams, kBatchStreams, status);
+    if (rc) return rc;
     for (int i = 0; i < kBatchStreams; ++i) {
         if (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess) return DMUL_ERR_CUDA;
         if (cudaStreamWaitEvent(s, b->join[i], 0) != cudaSuccess) return DMUL_ERR_CUDA;
@@ -530,26 +639,39 @@ int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count,
         else { PlanEntry *pe; rc = get_plan(c, G.N, &pe); }
         if (rc) return rc;
     }
+    // the persistent launch for the short products: their plan table and counter
+    SmallLaunch sl;
+    for (size_t i = 0; i < count; ++i) {
+        if (!items[i].small) continue;
+        if (!sl.count) sl.first = i;
+        ++sl.count;
+        sl.maxN = std::max<uint32_t>(sl.maxN, (uint32_t)items[i].N);
+    }
+    if (sl.count) {
+        if (!b->dcounter) {
+            if ((rc = dev_alloc(c, (void **)&b->dcounter, 256))) return rc;
+            if ((rc = dev_alloc(c, (void **)&b->dplans, kMaxSmallPlans * sizeof(SmallPlanDev)))) return rc;
+            if (cudaMallocHost(&b->hplans, kMaxSmallPlans * sizeof(SmallPlanDev)) != cudaSuccess) return DMUL_ERR_NOMEM;
+        }
+        std::vector<uint64_t> ns;
+        for (size_t i = sl.first; i < sl.first + sl.count; ++i) {
+            auto f = std::find(ns.begin(), ns.end(), items[i].N);
+            uint32_t id = (uint32_t)(f - ns.begin());
+            if (f == ns.end()) {
+                if (ns.size() == (size_t)kMaxSmallPlans) return DMUL_ERR_INVALID;
+                ns.push_back(items[i].N);
+                SmallPlanEntry *se;
+                if ((rc = get_small_plan(c, items[i].N, &se))) return rc;
+                b->hplans[id] = se->sp;
+            }
+            b->hjobs[i].plan = id;
+        }
+        sl.nplans = ns.size();
+    }
     if (!use_graph) {
         // plain launches on one stream (the serving loop's slots: shapes vary, slots overlap)
-        if (cudaMemcpyAsync(b->djobs, b->hjobs, count * sizeof(JobDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
-            return DMUL_ERR_CUDA;
-        if (ctl_bytes && cudaMemsetAsync(b->arena + ctl_off, 0, ctl_bytes, s) != cudaSuccess) return DMUL_ERR_CUDA;
-        for (const GroupLaunch &G : groups) {
-            const JobDev *jd = b->djobs + G.first;
-            if (G.small) {
-                SmallPlanEntry *se;
-                if ((rc = get_small_plan(c, G.N, &se))) return rc;
-                if (launch_small_mul(se->sp, jd, (int)G.count, status, s) != cudaSuccess) return DMUL_ERR_CUDA;
-            } else {
-                PlanEntry *pe;
-                if ((rc = get_plan(c, G.N, &pe))) return rc;
-                if (launch_col_fwd_b(pe->pd, jd, (int)G.count, status, s) != cudaSuccess) return DMUL_ERR_CUDA;
-                if (launch_row_mul_b(pe->pd, jd, (int)G.count, s) != cudaSuccess) return DMUL_ERR_CUDA;
-                if (launch_col_inv_b(pe->pd, jd, (int)G.count, s) != cudaSuccess) return DMUL_ERR_CUDA;
-                if (launch_carry_b(jd, (int)G.count, G.maxtiles, status, s) != cudaSuccess) return DMUL_ERR_CUDA;
-            }
-        }
+        rc = upload_and_launch(c, b, groups, sl, s, count, ctl_off, ctl_bytes, status, false);
+        if (rc) return rc;
         if (cudaEventRecord(b->done, s) != cudaSuccess) return DMUL_ERR_CUDA;
         b->done_recorded = true;
         return DMUL_OK;
@@ -563,7 +685,7 @@ int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count,
         cudaStream_t cap = b->streams[0];
         // capture on a private stream, joined to s through events
         if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DMUL_ERR_CUDA;
-        rc = enqueue_groups(c, b, groups, cap, count, ctl_off, ctl_bytes, status);
+        rc = upload_and_launch(c, b, groups, sl, cap, count, ctl_off, ctl_bytes, status, true);
         cudaError_t ce = cudaStreamEndCapture(cap, &graph);
         if (rc) return rc;
         if (ce != cudaSuccess) return DMUL_ERR_CUDA;

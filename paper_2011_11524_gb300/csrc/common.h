@@ -50,6 +50,9 @@ struct PlanDev {
     int ncs, nrs;
     Stage cs[kMaxStages];   // column stages, first to last
     Stage rs[kMaxStages];   // row stages
+    uint32_t col_threads, row_threads;  // CTA sizes of the column and row passes (autotuned)
+    uint32_t row_tma;                   // 1: persistent TMA-fed row pass with row_grid CTAs/prime
+    uint32_t row_grid;
     uint64_t offA, offQ, offAi, offQi;  // four-step twiddle tables (uint2 offsets)
     const uint2 *tw[kPrimes];           // per-prime table buffers (device)
 };

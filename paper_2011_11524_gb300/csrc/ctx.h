@@ -6,6 +6,7 @@
 #include <map>
 #include <tuple>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "../../include/dmul.h"
@@ -36,6 +37,7 @@ struct StageTimer {
 class Server;
 
 constexpr int kBatchStreams = 4;
+constexpr int kMaxSmallPlans = 32;  // distinct short transform lengths (there are 17)
 
 struct GroupLaunch {
     bool small;
@@ -53,6 +55,8 @@ struct BatchState {
     cudaStream_t streams[kBatchStreams] = {};
     cudaEvent_t fork = nullptr, join[kBatchStreams] = {};
     cudaEvent_t done = nullptr;  // recorded after each batch launched on this state
+    SmallPlanDev *dplans = nullptr, *hplans = nullptr;  // plans of the short products (device, pinned)
+    uint32_t *dcounter = nullptr;                       // job counter of the persistent launch
     bool done_recorded = false;
     // graph cache keyed by the batch shape
     std::map<std::vector<std::tuple<int, uint64_t, size_t>>, cudaGraphExec_t> graphs;
@@ -91,7 +95,8 @@ struct dmul_ctx {
     std::vector<dml::StageTimer> timers;
     // batched form
     std::unique_ptr<dml::BatchState> batch;
-    // serving
+    // serving (created on the first dmul_submit, under server_mu)
+    std::mutex server_mu;
     std::unique_ptr<dml::Server> server;
 };
 

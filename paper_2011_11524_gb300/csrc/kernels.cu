@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(512) k_col_fwd(const PlanDev pd, const uint32_
 cudaError_t launch_col_fwd(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
                            uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status, cudaStream_t s) {
     const size_t smem = (size_t)pd.N1 * 32 * sizeof(uint32_t);
-    const int threads = pd.N1 >= 512 ? 512 : 256;
+    const int threads = (int)pd.col_threads;
     dim3 grid(kPrimes * (pd.N2 / 32), y ? 2 : 1);
     k_col_fwd<<<grid, threads, smem, s>>>(pd, x, nx, y, ny, X, Y, status);
     return cudaGetLastError();
@@ -48,27 +48,46 @@ __global__ void __launch_bounds__(256) k_row_mul(const PlanDev pd, uint32_t *X, 
     DMUL_PRIME_SWITCH(pi, (row_mul_body<PI, SQR>(pd, sm, xr, yr)));
 }
 
+template <bool SQR>
+__global__ void __launch_bounds__(256) k_row_mul_tma(const PlanDev pd, uint32_t *X, const uint32_t *Y,
+                                                     uint32_t *status) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    const int pi = blockIdx.y;
+    DMUL_PRIME_SWITCH(pi, (row_mul_tma_body<PI, SQR>(pd, sm, X, Y, status)));
+}
+
+size_t row_tma_smem(const PlanDev &pd) { return (size_t)6 * pd.N2 * 4 + 16; }
+
+cudaError_t launch_row_mul_tma(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
+                               uint32_t *status, cudaStream_t s) {
+    dim3 grid(pd.row_grid ? pd.row_grid : 256, kPrimes);
+    if (square) k_row_mul_tma<true><<<grid, pd.row_threads, row_tma_smem(pd), s>>>(pd, X, Y, status);
+    else k_row_mul_tma<false><<<grid, pd.row_threads, row_tma_smem(pd), s>>>(pd, X, Y, status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_row_mul(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
                            cudaStream_t s) {
     dim3 grid(pd.N1, kPrimes);
     const size_t smem = (size_t)(square ? 1 : 2) * pd.N2 * sizeof(uint32_t);
-    if (square) k_row_mul<true><<<grid, 256, smem, s>>>(pd, X, Y);
-    else k_row_mul<false><<<grid, 256, smem, s>>>(pd, X, Y);
+    if (square) k_row_mul<true><<<grid, pd.row_threads, smem, s>>>(pd, X, Y);
+    else k_row_mul<false><<<grid, pd.row_threads, smem, s>>>(pd, X, Y);
     return cudaGetLastError();
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(512) k_col_inv(const PlanDev pd, const uint32_t *__restrict__ X,
-                                                 uint64_t L, int mode, uint32_t *__restrict__ out,
+                                                 uint64_t L, uint32_t *__restrict__ out,
                                                  uint2 *__restrict__ spill) {
     extern __shared__ uint32_t sm[];
-    col_inv_crt(pd, X, L, mode, out, spill, sm);
+    col_inv_crt(pd, X, L, MODE, out, spill, sm);
 }
 
 cudaError_t launch_col_inv(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
                            uint32_t *out, uint2 *spill, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kPrimes * (pd.N2 / 32), 1, 1);
-    cfg.blockDim = dim3(pd.N1 >= 512 ? 512 : 256, 1, 1);
+    cfg.blockDim = dim3(pd.col_threads, 1, 1);
     cfg.dynamicSmemBytes = (size_t)pd.N1 * 32 * sizeof(uint32_t);
     cfg.stream = s;
     cudaLaunchAttribute at[1];
@@ -78,7 +97,9 @@ cudaError_t launch_col_inv(const PlanDev &pd, const uint32_t *X, uint64_t L, Inv
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_col_inv, pd, X, L, (int)mode, out, spill);
+    if (mode == kInvTriples) return cudaLaunchKernelEx(&cfg, k_col_inv<kInvTriples>, pd, X, L, out, spill);
+    if (mode == kInvResidues) return cudaLaunchKernelEx(&cfg, k_col_inv<kInvResidues>, pd, X, L, out, spill);
+    return cudaLaunchKernelEx(&cfg, k_col_inv<kInvDigits>, pd, X, L, out, spill);
 }
 
 // digit triples -> within-chunk digit sums + spills (the CRT stage's epilogue on given triples)
@@ -156,7 +177,16 @@ cudaError_t init_kernel_attributes_main() {
                                   2 * kMaxN2 * 4)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_row_mul<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   kMaxN2 * 4)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_col_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxN1 * 32 * 4);
+    if ((e = cudaFuncSetAttribute(k_row_mul_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  6 * kMaxN2 * 4 + 16)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_row_mul_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  6 * kMaxN2 * 4 + 16)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_col_inv<kInvTriples>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kMaxN1 * 32 * 4)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_col_inv<kInvResidues>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  kMaxN1 * 32 * 4)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_col_inv<kInvDigits>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                kMaxN1 * 32 * 4);
 }
 
 }  // namespace dml

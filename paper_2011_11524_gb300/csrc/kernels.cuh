@@ -32,6 +32,8 @@ struct JobDev {
     uint2 *spill;
     CarryCtl *ctl;
     uint32_t square, ntiles;
+    uint32_t plan;          // index of the job's small plan (persistent small-job launch)
+    uint32_t pad;
 };
 
 // Inverse column pass output modes.
@@ -49,6 +51,11 @@ cudaError_t launch_col_fwd(const PlanDev &pd, const uint32_t *x, uint64_t nx, co
 // result in X.
 cudaError_t launch_row_mul(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
                            cudaStream_t s);
+
+// The same row pass as a persistent kernel fed by bulk asynchronous copies (TMA), pd.row_grid
+// CTAs per prime, each prefetching its next row while computing the current one.
+cudaError_t launch_row_mul_tma(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
+                               uint32_t *status, cudaStream_t s);
 
 // Inverse column pass + (mode) CRT and digit split.  kInvDigits writes the within-chunk digit
 // sums to out[0..L) and the chunk spills to spill; kInvTriples writes d[3k..3k+2]; kInvResidues
@@ -80,6 +87,10 @@ cudaError_t launch_small_mul(const SmallPlanDev &sp, const JobDev *jobs, int njo
                              cudaStream_t s);
 cudaError_t launch_small_mul_one(const SmallPlanDev &sp, const JobDev &job, uint32_t *status,
                                  cudaStream_t s);
+// One persistent launch for every short product of a batch: clusters take jobs from *counter
+// (zeroed beforehand) until none is left; plans[job.plan] is the job's small plan.
+cudaError_t launch_small_persistent(const SmallPlanDev *plans, uint32_t maxN, const JobDev *jobs,
+                                    uint32_t njobs, uint32_t *counter, uint32_t *status, cudaStream_t s);
 cudaError_t launch_col_fwd_b(const PlanDev &pd, const JobDev *jobs, int njobs, uint32_t *status,
                              cudaStream_t s);
 cudaError_t launch_row_mul_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s);

@@ -252,6 +252,20 @@ bool make_host_plan(uint64_t N, HostPlan *hp, uint32_t n1_override) {
     return (int)hp->col_radix.size() <= kMaxStages && (int)hp->row_radix.size() <= kMaxStages;
 }
 
+std::vector<uint32_t> candidate_n1(uint64_t N) {
+    std::vector<uint32_t> out;
+    for (uint32_t n1 = 2; n1 <= kMaxN1; n1 *= 2) {
+        for (uint32_t cand : {n1, 3 * n1}) {
+            HostPlan hp;
+            if (cand <= kMaxN1 && N % cand == 0 && make_host_plan(N, &hp, cand) && hp.N1 == cand &&
+                hp.N1 >= 32 && std::find(out.begin(), out.end(), cand) == out.end())
+                out.push_back(cand);
+        }
+    }
+    std::sort(out.begin(), out.end());
+    return out;
+}
+
 uint64_t choose_N_pow2(uint64_t L) {
     for (uint64_t n = kMinN; n <= (1ull << 23); n <<= 1)
         if (n >= L) return n;
@@ -346,6 +360,10 @@ void build_tables(const HostPlan &hp, PlanDev *pd, std::vector<uint32_t> tables[
     pd->N = hp.N;
     pd->N1 = hp.N1;
     pd->N2 = hp.N2;
+    pd->col_threads = hp.col_threads ? hp.col_threads : (hp.N1 >= 512 ? 512 : 256);
+    pd->row_threads = hp.row_threads ? hp.row_threads : 256;
+    pd->row_tma = hp.row_tma;
+    pd->row_grid = hp.row_grid;
     const uint64_t N = hp.N;
     const uint32_t N1 = hp.N1, N2 = hp.N2;
     const int s = (int)hp.col_radix.size();

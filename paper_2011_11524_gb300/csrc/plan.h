@@ -38,7 +38,11 @@ struct HostPlan {
     uint64_t N;
     uint32_t N1, N2;
     std::vector<uint32_t> col_radix, row_radix;
+    uint32_t col_threads = 0, row_threads = 0;  // 0: the default for the split
+    uint32_t row_tma = 0, row_grid = 0;         // persistent TMA-fed row pass and its CTAs/prime
 };
+// Candidate column lengths N1 for a transform length N (the autotuner's search space).
+std::vector<uint32_t> candidate_n1(uint64_t N);
 bool make_host_plan(uint64_t N, HostPlan *hp, uint32_t n1_override = 0);
 
 // Six-step form (Sec. 7.9): N = 2^k only, N1 = 2^floor(k/2), N2 = 2^ceil(k/2); both the N1-long

@@ -69,8 +69,9 @@ int Server::wait(uint64_t ticket) {
     std::unique_lock<std::mutex> g(mu_);
     auto it = tickets_.find(ticket);
     if (it == tickets_.end()) return DMUL_ERR_UNKNOWN_TICKET;
-    done_cv_.wait(g, [&] { return it->second.done; });
-    return it->second.status;
+    Ticket *tk = &it->second;  // element references survive rehashing; iterators do not
+    done_cv_.wait(g, [&] { return tk->done; });
+    return tk->status;
 }
 
 void CUDART_CB Server::on_done(void *p) {
@@ -161,23 +162,53 @@ void Server::loop() {
     set_device(ctx_);
     std::unique_lock<std::mutex> g(mu_);
     for (;;) {
+        // Wake only for something actionable, so that the lock is released while waiting (the
+        // completion callback needs it): a finished slot, a free slot with an admissible request,
+        // or shutdown with nothing in flight.
         cv_.wait(g, [&] {
-            if (stop_) return true;
-            for (auto &s : slots_)
+            bool any_busy = false, any_free = false;
+            for (auto &s : slots_) {
                 if (s->busy && s->finished) return true;
-            if (queue_.empty()) return false;
-            for (auto &s : slots_)
-                if (!s->busy) return true;
-            return false;
+                any_busy |= s->busy;
+                any_free |= !s->busy;
+            }
+            if (stop_) return !any_busy;
+            return !queue_.empty() && any_free && !mem_blocked_;
         });
         for (auto &s : slots_)
-            if (s->busy && s->finished) retire(*s, g);
+            if (s->busy && s->finished) {
+                retire(*s, g);
+                mem_blocked_ = false;  // memory came back: retry the head of the queue
+            }
         bool any_busy = false;
         for (auto &s : slots_) any_busy |= s->busy;
-        if (stop_ && queue_.empty() && !any_busy) return;
+        if (stop_) {
+            if (any_busy) continue;
+            for (uint64_t t : queue_) {  // never started: the context is going away
+                tickets_[t].status = DMUL_ERR_INVALID;
+                tickets_[t].done = true;
+            }
+            queue_.clear();
+            done_cv_.notify_all();
+            return;
+        }
         for (auto &s : slots_) {
-            if (queue_.empty()) break;
-            if (!s->busy && !launch(*s, g)) break;  // nothing admissible until memory frees
+            if (queue_.empty() || mem_blocked_) break;
+            if (s->busy) continue;
+            if (!launch(*s, g)) {
+                // the head request does not fit the admission budget next to the batches in
+                // flight: wait for one of them to retire
+                mem_blocked_ = any_busy;
+                if (!any_busy) {  // cannot happen (submit rejects such requests); fail it
+                    Ticket &tk = tickets_[queue_.front()];
+                    tk.status = DMUL_ERR_NOMEM;
+                    tk.done = true;
+                    queue_.pop_front();
+                    done_cv_.notify_all();
+                }
+                break;
+            }
+            any_busy = true;
         }
     }
 }

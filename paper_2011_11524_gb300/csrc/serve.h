@@ -73,6 +73,7 @@ class Server {
     uint64_t next_ = 1;
     bool stop_ = false;
     bool init_ok_ = false;
+    bool mem_blocked_ = false;  // the head request waits for in-flight scratch to be released
     std::vector<std::unique_ptr<Slot>> slots_;
     size_t budget_ = 0, inflight_ = 0;
     std::thread worker_;

@@ -88,6 +88,54 @@ __device__ __forceinline__ void colf_first(const PlanDev &pd, const Stage &st, u
     }
 }
 
+// Stage the N1 x 32 tile at word offset j0 of a row-major matrix with row length N2 into shared
+// memory with asynchronous 16-byte copies (all in flight at once); words at or beyond n read as 0
+// (the zero padding of Sec. 3.2).  src must be 16-byte aligned.
+__device__ __forceinline__ void tile_load_async(uint32_t *sm, const uint32_t *__restrict__ src,
+                                                uint64_t n, uint32_t N1, uint32_t N2, uint32_t j0) {
+    const uint32_t chunks = N1 * 8;  // 16-byte chunks: 8 per 32-word row
+    for (uint32_t idx = threadIdx.x; idx < chunks; idx += blockDim.x) {
+        const uint32_t row = idx >> 3, q = idx & 7;
+        const uint64_t g = (uint64_t)row * N2 + j0 + 4 * q;
+        const uint32_t valid = g >= n ? 0u : (n - g >= 4 ? 4u : (uint32_t)(n - g));
+        const uint32_t *s = valid ? src + g : src;  // a readable address even when nothing is read
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(sm + row * 32 + 4 * q);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(s), "r"(valid * 4)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+}
+
+// First forward column stage from a tile already in shared memory (limbs), in place.
+template <int PI, int R>
+__device__ __forceinline__ void colf_first_sm(const PlanDev &pd, const Stage &st, uint32_t *sm,
+                                              uint32_t &bad) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t stride = st.m / R;
+    const uint2 *tw = pd.tw[PI] + st.tw;
+    for (uint32_t j = warp; j < stride; j += nw) {
+        uint32_t v[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            uint32_t a = sm[(j + u * stride) * 32 + lane];
+            bad |= (a >= kBase);
+            if (PI == 0) a = red2p<PI>(a);  // 10^9 < 4 p0: [0, 10^9) -> [0, 2 p0)
+            v[u] = a;
+        }
+        dft<PI, 0, R>(v);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            uint32_t o = v[outpos<R>(k)];
+            if (k > 0 && st.m > (uint32_t)R) {
+                uint2 w = ldtw(tw + (k - 1) * stride + j);
+                o = shoup<PI>(o, w.x, w.y);
+            }
+            sm[(j + k * stride) * 32 + lane] = o;
+        }
+    }
+}
+
 template <int PI, int R, bool INV>
 __device__ __forceinline__ void col_mid(const PlanDev &pd, const Stage &st, uint32_t *sm,
                                         bool final_reduce) {
@@ -161,12 +209,17 @@ __device__ __forceinline__ void colf_last(const PlanDev &pd, const Stage &st, co
 }
 
 template <int PI>
-__device__ void col_fwd_body(const PlanDev &pd, uint32_t *sm, const uint32_t *__restrict__ src,
+__device__ __forceinline__ void col_fwd_body(const PlanDev &pd, uint32_t *sm, const uint32_t *__restrict__ src,
                              uint64_t n, uint32_t *__restrict__ dst, uint32_t tile,
                              uint32_t *status) {
     const uint32_t n2 = tile * 32 + (threadIdx.x & 31);
     uint32_t bad = 0;
-    DMUL_RADIX_SWITCH(pd.cs[0].R, (colf_first<PI, RR>(pd, pd.cs[0], sm, src, n, n2, bad)));
+    if ((((uintptr_t)src) & 15) == 0) {
+        tile_load_async(sm, src, n, pd.N1, pd.N2, tile * 32);
+        DMUL_RADIX_SWITCH(pd.cs[0].R, (colf_first_sm<PI, RR>(pd, pd.cs[0], sm, bad)));
+    } else {
+        DMUL_RADIX_SWITCH(pd.cs[0].R, (colf_first<PI, RR>(pd, pd.cs[0], sm, src, n, n2, bad)));
+    }
     if (PI == 0 && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusInvalid);
     __syncthreads();
     for (int t = 1; t < pd.ncs - 1; ++t) {
@@ -285,16 +338,17 @@ __device__ __forceinline__ void rowi_last(const Stage &st, const uint2 *tw, cons
     }
 }
 
+// The fused row pass on one row: inputs read from xin / yin (global memory, or a landing buffer
+// in shared memory), working buffers sx / sy (swizzled), result written to xout (global).
 template <int PI, bool SQR>
-__device__ void row_mul_body(const PlanDev &pd, uint32_t *sm, uint32_t *__restrict__ xr,
-                             const uint32_t *__restrict__ yr) {
+__device__ __forceinline__ void row_mul_core(const PlanDev &pd, uint32_t *sx, uint32_t *sy,
+                                             const uint32_t *xin, const uint32_t *yin,
+                                             uint32_t *__restrict__ xout) {
     const uint32_t n = pd.N2;
     const uint2 *tw = pd.tw[PI];
-    uint32_t *sx = sm;
-    uint32_t *sy = sm + n;
     const int ns = pd.nrs;
-    DMUL_RADIX_SWITCH(pd.rs[0].R, (rowf_first<PI, RR>(pd.rs[0], tw, xr, sx)));
-    if (!SQR) DMUL_RADIX_SWITCH(pd.rs[0].R, (rowf_first<PI, RR>(pd.rs[0], tw, yr, sy)));
+    DMUL_RADIX_SWITCH(pd.rs[0].R, (rowf_first<PI, RR>(pd.rs[0], tw, xin, sx)));
+    if (!SQR) DMUL_RADIX_SWITCH(pd.rs[0].R, (rowf_first<PI, RR>(pd.rs[0], tw, yin, sy)));
     __syncthreads();
     for (int t = 1; t < ns - 1; ++t) {
         DMUL_RADIX_SWITCH(pd.rs[t].R, (row_mid<PI, RR, false>(pd.rs[t], tw, sx, n)));
@@ -307,7 +361,102 @@ __device__ void row_mul_body(const PlanDev &pd, uint32_t *sm, uint32_t *__restri
         DMUL_RADIX_SWITCH(pd.rs[t].R, (row_mid<PI, RR, true>(pd.rs[t], tw, sx, n)));
         __syncthreads();
     }
-    DMUL_RADIX_SWITCH(pd.rs[0].R, (rowi_last<PI, RR>(pd.rs[0], tw, sx, xr)));
+    DMUL_RADIX_SWITCH(pd.rs[0].R, (rowi_last<PI, RR>(pd.rs[0], tw, sx, xout)));
+}
+
+template <int PI, bool SQR>
+__device__ __forceinline__ void row_mul_body(const PlanDev &pd, uint32_t *sm, uint32_t *__restrict__ xr,
+                             const uint32_t *__restrict__ yr) {
+    row_mul_core<PI, SQR>(pd, sm, sm + pd.N2, xr, yr, xr);
+}
+
+// ---- TMA (bulk async copy) helpers -----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// 1-D bulk copy global -> shared, completion counted on the mbarrier (16-byte aligned, size % 16 == 0)
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Bounded wait for the mbarrier phase with the given parity; false when the bound runs out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    for (uint32_t i = 0; i < (1u << 20); ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Persistent, TMA-fed row pass: CTA (g, prime) handles rows g, g + G, ...; while it computes one
+// row, the bulk-copy engine brings the next row's X and Y into the other landing buffer.
+// Shared memory: landing buffers [2][X, Y] (plain layout) + working buffers [X, Y] (swizzled)
+// + 2 mbarriers.  On an expired wait the CTA records a timeout, waits (bounded) for its own copy
+// in flight and returns.
+template <int PI, bool SQR>
+__device__ __forceinline__ void row_mul_tma_body(const PlanDev &pd, uint32_t *sm, uint32_t *X, const uint32_t *Y,
+                                 uint32_t *status) {
+    const uint32_t n = pd.N2;
+    uint32_t *land = sm;                      // [2][2][n]
+    uint32_t *sx = sm + 4 * n, *sy = sm + 5 * n;
+    uint64_t *bar = (uint64_t *)(sm + 6 * n);  // 8-byte aligned: 6n words, n % 32 == 0
+    const uint32_t G = gridDim.x;
+    const uint64_t base = (uint64_t)PI * pd.N;
+    const uint32_t bytes = n * 4;
+    const uint32_t per_row = (SQR ? 1u : 2u) * bytes;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t r = blockIdx.x;
+    if (threadIdx.x == 0 && r < pd.N1) {
+        mbar_expect_tx(&bar[0], per_row);
+        tma_load_1d(land, X + base + (uint64_t)r * n, bytes, &bar[0]);
+        if (!SQR) tma_load_1d(land + n, Y + base + (uint64_t)r * n, bytes, &bar[0]);
+    }
+    for (uint32_t it = 0; r < pd.N1; ++it, r += G) {
+        const uint32_t b = it & 1u;
+        const uint32_t rn = r + G;
+        if (threadIdx.x == 0 && rn < pd.N1) {
+            uint32_t *dst = land + (b ^ 1u) * 2 * n;
+            fence_proxy_async();
+            mbar_expect_tx(&bar[b ^ 1u], per_row);
+            tma_load_1d(dst, X + base + (uint64_t)rn * n, bytes, &bar[b ^ 1u]);
+            if (!SQR) tma_load_1d(dst + n, Y + base + (uint64_t)rn * n, bytes, &bar[b ^ 1u]);
+        }
+        // every thread polls; the outcome is agreed on so that the CTA leaves (or not) as a whole
+        const int ok = __syncthreads_and(mbar_wait(&bar[b], (it >> 1) & 1u) ? 1 : 0);
+        if (!ok) {
+            if (threadIdx.x == 0) {
+                atomicOr(status, kStatusTimeout);
+                if (rn < pd.N1) mbar_wait(&bar[b ^ 1u], ((it + 1) >> 1) & 1u);  // our copy in flight
+            }
+            return;
+        }
+        const uint32_t *lx = land + b * 2 * n;
+        row_mul_core<PI, SQR>(pd, sx, sy, lx, lx + n, X + base + (uint64_t)r * n);
+        __syncthreads();  // the landing buffer b and the working buffers are free again
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -341,11 +490,41 @@ __device__ __forceinline__ void coli_first(const PlanDev &pd, const uint32_t *__
     }
 }
 
+// First inverse column stage (inverse four-step twiddle, inverse DFT) on a staged tile, in place.
+template <int PI, int R>
+__device__ __forceinline__ void coli_first_sm(const PlanDev &pd, uint32_t *sm, uint32_t n2) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t nb = pd.N1 / R;
+    const uint2 *A = pd.tw[PI] + pd.offAi;
+    const uint2 *Q = pd.tw[PI] + pd.offQi;
+    for (uint32_t b = warp; b < nb; b += nw) {
+        uint32_t v[R];
+        uint2 a = ldtw(A + (uint64_t)b * pd.N2 + n2);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            uint32_t o = sm[(b * R + k) * 32 + lane];
+            if (k > 0) {
+                uint2 q = ldtw(Q + (uint64_t)k * pd.N2 + n2);
+                o = shoup<PI>(o, q.x, q.y);
+            }
+            v[k] = shoup<PI>(o, a.x, a.y);
+        }
+        dft<PI, 1, R>(v);
+#pragma unroll
+        for (int u = 0; u < R; ++u) sm[(b * R + u) * 32 + lane] = v[outpos<R>(u)];
+    }
+}
+
 template <int PI>
-__device__ void col_inv_body(const PlanDev &pd, const uint32_t *__restrict__ src, uint32_t *sm,
+__device__ __forceinline__ void col_inv_body(const PlanDev &pd, const uint32_t *__restrict__ src, uint32_t *sm,
                              uint32_t n2) {
     const int ns = pd.ncs;
-    DMUL_RADIX_SWITCH(pd.cs[ns - 1].R, (coli_first<PI, RR>(pd, src, sm, n2)));
+    if ((((uintptr_t)src) & 15) == 0) {
+        tile_load_async(sm, src, pd.N, pd.N1, pd.N2, n2 & ~31u);
+        DMUL_RADIX_SWITCH(pd.cs[ns - 1].R, (coli_first_sm<PI, RR>(pd, sm, n2)));
+    } else {
+        DMUL_RADIX_SWITCH(pd.cs[ns - 1].R, (coli_first<PI, RR>(pd, src, sm, n2)));
+    }
     __syncthreads();
     for (int t = ns - 2; t >= 0; --t) {
         DMUL_RADIX_SWITCH(pd.cs[t].R, (col_mid<PI, RR, true>(pd, pd.cs[t], sm, t == 0)));
@@ -467,6 +646,13 @@ __device__ __forceinline__ void col_inv_crt(const PlanDev &pd, const uint32_t *_
 }
 
 // One 2048-limb tile of the decoupled-lookahead carry scan (256 threads).
+//
+// A tile publishes its aggregate carry map (status 1) and, once it knows its carry-in, its
+// carry-out (status 2).  A tile whose map is constant -- its carry-out does not depend on its
+// carry-in, the usual case unless its digit sums sit at 10^9 - 1 -- publishes its carry-out at
+// once, so successors rarely wait.  The look-back runs on a whole warp: 32 predecessors per round,
+// the maps before the nearest finished predecessor composed by a warp reduction.  Every wait is
+// bounded; on expiry the tile records a timeout and proceeds with carry 0.
 __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2 *__restrict__ spill,
                                            uint64_t L, CarryCtl *ctl, uint64_t *nz,
                                            uint32_t *status, uint32_t ntiles) {
@@ -477,9 +663,15 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
     __syncthreads();
     const uint32_t tile = s_tile;
     const uint64_t base = (uint64_t)tile * kCarryLimbs + (uint64_t)tid * 8;
+    const bool vec = ((((uintptr_t)z) & 15) == 0) && (base + 8 <= L);
     uint32_t v[8];
+    if (vec) {
+        const uint4 a = *(const uint4 *)(z + base), b = *(const uint4 *)(z + base + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = (base + i < L) ? z[base + i] : 0u;
+        for (int i = 0; i < 8; ++i) v[i] = (base + i < L) ? z[base + i] : 0u;
+    }
     if ((base & 31) == 0 && base > 0 && base < L) {
         uint2 sp = spill[(base >> 5) - 1];
         v[0] += sp.x;
@@ -505,58 +697,93 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
     if (lane == 0) exc = kIdentityMap;
     if (lane == 31) s_warp[warp] = inc;
     __syncthreads();
-    if (tid == 0) {
+    if (warp == 0) {
         uint32_t agg = kIdentityMap;
-        for (int w = 0; w < 8; ++w) {
-            uint32_t wf = s_warp[w];
-            s_warp[w] = agg;  // exclusive prefix of warp w
-            agg = map_compose(wf, agg);
+        if (lane == 0) {
+            for (int w = 0; w < 8; ++w) {
+                uint32_t wf = s_warp[w];
+                s_warp[w] = agg;  // exclusive prefix of warp w
+                agg = map_compose(wf, agg);
+            }
+        }
+        agg = __shfl_sync(0xffffffffu, agg, 0);
+        const uint32_t a0 = map_apply(agg, 0);
+        const bool constant = (a0 == map_apply(agg, 1)) && (a0 == map_apply(agg, 2));
+        if (lane == 0) {
+            if (tile == 0 || constant) st_release(&ctl->flags[tile], 2ull | ((uint64_t)map_apply(agg, 0) << 8));
+            else st_release(&ctl->flags[tile], 1ull | ((uint64_t)agg << 8));
         }
         uint32_t cin = 0;
         if (tile > 0) {
-            st_release(&ctl->flags[tile], 1ull | ((uint64_t)agg << 8));
-            uint32_t acc = kIdentityMap;  // maps of tiles (t, tile) composed
-            int64_t t = (int64_t)tile - 1;
-            bool ok = true;
-            while (t >= 0) {
-                uint64_t w;
-                uint32_t spins = 0;
-                while (((w = ld_acquire(&ctl->flags[t])) & 3u) == 0) {
-                    if (++spins > kSpinLimit) { ok = false; break; }
-                    __nanosleep(32);
+            uint32_t acc = kIdentityMap;  // maps of the predecessors already passed, newest last-applied
+            int64_t top_t = (int64_t)tile - 1;
+            for (;;) {
+                const int64_t t = top_t - lane;
+                uint64_t w = 2ull;  // before tile 0: a finished tile with carry-out 0
+                bool late = false;
+                if (t >= 0) {
+                    uint32_t spins = 0;
+                    while (((w = ld_acquire(&ctl->flags[t])) & 3u) == 0) {
+                        if (++spins > kSpinLimit) { late = true; break; }
+                        __nanosleep(32);
+                    }
                 }
-                if (!ok) break;
-                uint32_t val = (uint32_t)(w >> 8) & 63u;
-                if ((w & 3u) == 2u) { cin = map_apply(acc, val); break; }
-                acc = map_compose(acc, val);
-                --t;
+                if (__any_sync(0xffffffffu, late)) {
+                    if (lane == 0) atomicOr(status, kStatusTimeout);
+                    cin = 0;
+                    break;
+                }
+                const uint32_t st = (uint32_t)w & 3u, val = (uint32_t)(w >> 8) & 63u;
+                const unsigned incl = __ballot_sync(0xffffffffu, st == 2u);
+                const int first = incl ? __ffs(incl) - 1 : 32;
+                // compose the maps of lanes [0, first): newer lanes are applied after older ones
+                uint32_t m = (lane < first) ? val : kIdentityMap;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    uint32_t o = __shfl_down_sync(0xffffffffu, m, d);
+                    if (lane + d < 32) m = map_compose(m, o);
+                }
+                const uint32_t G = __shfl_sync(0xffffffffu, m, 0);
+                if (incl) {
+                    const uint32_t cfirst = __shfl_sync(0xffffffffu, val, first);
+                    cin = map_apply(map_compose(acc, G), cfirst);
+                    break;
+                }
+                acc = map_compose(acc, G);
+                top_t -= 32;
             }
-            if (!ok) { atomicOr(status, kStatusTimeout); cin = 0; }
+            if (lane == 0 && !constant) st_release(&ctl->flags[tile], 2ull | ((uint64_t)map_apply(agg, cin) << 8));
         }
-        uint32_t cout = map_apply(agg, cin);
-        st_release(&ctl->flags[tile], 2ull | ((uint64_t)cout << 8));
-        s_cin = cin;
+        if (lane == 0) s_cin = cin;
     }
     __syncthreads();
     uint32_t c = map_apply(map_compose(exc, s_warp[warp]), s_cin);
     uint64_t top = 0;
+    uint32_t o[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         uint32_t t = v[i] + c;
         uint32_t q = qdig(t);
-        uint32_t o = t - q * kBase;
+        o[i] = t - q * kBase;
         c = q;
         if (base + i < L) {
-            z[base + i] = o;
-            if (o) top = base + i + 1;
+            if (o[i]) top = base + i + 1;
             if (base + i == L - 1 && c != 0) atomicOr(status, kStatusInvalid);  // z >= B^L
         }
+    }
+    if (vec) {
+        *(uint4 *)(z + base) = make_uint4(o[0], o[1], o[2], o[3]);
+        *(uint4 *)(z + base + 4) = make_uint4(o[4], o[5], o[6], o[7]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (base + i < L) z[base + i] = o[i];
     }
     // highest nonzero limb
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) {
-        uint64_t o = __shfl_down_sync(0xffffffffu, top, d);
-        top = o > top ? o : top;
+        uint64_t oo = __shfl_down_sync(0xffffffffu, top, d);
+        top = oo > top ? oo : top;
     }
     if (lane == 0) s_top[warp] = top;
     __syncthreads();

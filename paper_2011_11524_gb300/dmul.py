@@ -27,6 +27,8 @@ DMUL_ERR_UNKNOWN_TICKET = 7
 DMUL_FLAG_SIXSTEP = 1
 DMUL_FLAG_STAGE_TIMING = 2
 DMUL_FLAG_NO_SMALL = 4
+DMUL_FLAG_NO_AUTOTUNE = 8
+DMUL_FLAG_ROW_TMA = 16
 
 # every symbol include/dmul.h declares
 EXPORTS = [

@@ -46,6 +46,14 @@ def ctx4(d):
 
 
 @pytest.fixture(scope="module")
+def ctx_tma(d):
+    """Four-step path with the persistent TMA-fed row pass for every length."""
+    c = d.Context(0, flags=d.DMUL_FLAG_NO_SMALL | d.DMUL_FLAG_NO_AUTOTUNE | d.DMUL_FLAG_ROW_TMA)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
 def ctx6(d):
     c = d.Context(0, flags=d.DMUL_FLAG_SIXSTEP)
     yield c
@@ -96,6 +104,18 @@ def test_mul_four_step_short(d, ctx4, n, m):
         z, nz = _gpu_mul(d, ctx4, x, x if square else y, square=square)
         r = oracle.mul(x, x) if square else ref
         assert np.array_equal(z, r) and nz == len(oracle.normalize(r))
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (500, 525), (4097, 4096), (30000, 20001), (65536, 65536),
+                                 (100000, 7), (300000, 299999)])
+def test_mul_tma_row_pass(d, ctx_tma, n, m):
+    """The persistent TMA-fed row pass (bulk copies into double-buffered shared memory)."""
+    rng = _rng(1500 + n + 3 * m)
+    x, y = _rand(rng, n), _rand(rng, m)
+    for square in (False, True):
+        z, nz = _gpu_mul(d, ctx_tma, x, x if square else y, square=square)
+        ref = oracle.mul(x, x) if square else oracle.mul(x, y)
+        assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))
 
 
 @pytest.mark.parametrize("n", [1, 2, 17, 512, 513, 1536, 5000, 11112, 40000, 65536])

@@ -57,19 +57,19 @@ __device__ __forceinline__ void small_transform(const SmallPlanDev &sp, const Jo
     const int any_bad = __syncthreads_or((int)bad);
     if (PI == 0 && any_bad && threadIdx.x == 0) atomicOr(status, kStatusInvalid);
     const int ns = sp.ns;
+    const uint32_t nops = sq ? 1u : 2u;
     for (int t = 0; t < ns - 1; ++t) {
-        DMUL_RADIX_SWITCH(sp.st[t].R, (row_mid<PI, RR, false>(sp.st[t], tw, sx, N)));
-        if (!sq) DMUL_RADIX_SWITCH(sp.st[t].R, (row_mid<PI, RR, false>(sp.st[t], tw, sy, N)));
+        DMUL_RADIX_SWITCH(sp.st[t].R, (row_fwd_stage<PI, RR>(sp.st[t], tw, sx, sy, nullptr, nullptr, false, N, nops)));
         __syncthreads();
     }
     if (sq) {
-        DMUL_RADIX_SWITCH(sp.st[ns - 1].R, (row_fused_center<PI, RR, true>(sx, sy, N)));
+        DMUL_RADIX_SWITCH(sp.st[ns - 1].R, (row_center<PI, RR, true>(sx, sy, N)));
     } else {
-        DMUL_RADIX_SWITCH(sp.st[ns - 1].R, (row_fused_center<PI, RR, false>(sx, sy, N)));
+        DMUL_RADIX_SWITCH(sp.st[ns - 1].R, (row_center<PI, RR, false>(sx, sy, N)));
     }
     __syncthreads();
     for (int t = ns - 2; t >= 0; --t) {
-        DMUL_RADIX_SWITCH(sp.st[t].R, (row_mid<PI, RR, true>(sp.st[t], tw, sx, N)));
+        DMUL_RADIX_SWITCH(sp.st[t].R, (row_inv_stage<PI, RR>(sp.st[t], tw, sx, nullptr, N)));
         __syncthreads();
     }
     for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {

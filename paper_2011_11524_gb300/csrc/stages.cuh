@@ -338,8 +338,103 @@ __device__ __forceinline__ void rowi_last(const Stage &st, const uint2 *tw, cons
     }
 }
 
-// The fused row pass on one row: inputs read from xin / yin (global memory, or a landing buffer
-// in shared memory), working buffers sx / sy (swizzled), result written to xout (global).
+// Forward row stage on every operand at once (groups of operand 0 first).  Stage 0 reads its
+// inputs from `gin` (plain layout, global or shared), the others from the swizzled buffers.
+// Looping over operands and stages keeps one copy of the DFT code per radix, which the
+// instruction cache holds.
+template <int PI, int R>
+__device__ __forceinline__ void row_fwd_stage(const Stage &st, const uint2 *tw, uint32_t *sx,
+                                              uint32_t *sy, const uint32_t *gx, const uint32_t *gy,
+                                              bool from_plain, uint32_t n, uint32_t nops) {
+    const uint32_t stride = st.m / R;
+    const uint32_t per_op = n / R;
+    const bool has_tw = st.m > (uint32_t)R;
+    for (uint32_t g = threadIdx.x; g < per_op * nops; g += blockDim.x) {
+        const bool second = g >= per_op;
+        const uint32_t gg = second ? g - per_op : g;
+        uint32_t *sb = second ? sy : sx;
+        const uint32_t blk = gg / stride, j = gg - blk * stride;
+        const uint32_t base = blk * st.m + j;
+        uint32_t v[R];
+        if (from_plain) {
+            const uint32_t *src = second ? gy : gx;
+#pragma unroll
+            for (int u = 0; u < R; ++u) v[u] = src[base + u * stride];
+        } else {
+#pragma unroll
+            for (int u = 0; u < R; ++u) v[u] = sb[swz(base + u * stride)];
+        }
+        dft<PI, 0, R>(v);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            uint32_t o = v[outpos<R>(k)];
+            if (k > 0 && has_tw) {
+                uint2 w = ldtw(tw + st.tw + (k - 1) * stride + j);
+                o = shoup<PI>(o, w.x, w.y);
+            }
+            sb[swz(base + k * stride)] = o;
+        }
+    }
+}
+
+// Inverse row stage on the product buffer; the last one (stage 0) writes to `gout` (plain).
+template <int PI, int R>
+__device__ __forceinline__ void row_inv_stage(const Stage &st, const uint2 *tw, uint32_t *sb,
+                                              uint32_t *gout, uint32_t n) {
+    const uint32_t stride = st.m / R;
+    const uint32_t groups = n / R;
+    const bool has_tw = st.m > (uint32_t)R;
+    for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
+        const uint32_t blk = g / stride, j = g - blk * stride;
+        const uint32_t base = blk * st.m + j;
+        uint32_t v[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = sb[swz(base + k * stride)];
+        if (has_tw) {
+#pragma unroll
+            for (int k = 1; k < R; ++k) {
+                uint2 w = ldtw(tw + st.twi + (k - 1) * stride + j);
+                v[k] = shoup<PI>(v[k], w.x, w.y);
+            }
+        }
+        dft<PI, 1, R>(v);
+        if (gout) {
+#pragma unroll
+            for (int u = 0; u < R; ++u) gout[base + u * stride] = v[outpos<R>(u)];
+        } else {
+#pragma unroll
+            for (int u = 0; u < R; ++u) sb[swz(base + u * stride)] = v[outpos<R>(u)];
+        }
+    }
+}
+
+// Last forward stage (m == R) of every operand, pointwise product (or square), first inverse stage.
+template <int PI, int R, bool SQR>
+__device__ __forceinline__ void row_center(uint32_t *sx, const uint32_t *sy, uint32_t n) {
+    const uint32_t groups = n / R;
+    for (uint32_t b = threadIdx.x; b < groups; b += blockDim.x) {
+        uint32_t v[2][R];
+#pragma unroll
+        for (int op = 0; op < (SQR ? 1 : 2); ++op) {
+            const uint32_t *sb = op ? sy : sx;
+#pragma unroll
+            for (int u = 0; u < R; ++u) v[op][u] = sb[swz(b * R + u)];
+            dft<PI, 0, R>(v[op]);
+        }
+        uint32_t z[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const uint32_t a = v[0][outpos<R>(k)];
+            z[k] = mont<PI>(a, SQR ? a : v[1][outpos<R>(k)]);
+        }
+        dft<PI, 1, R>(z);
+#pragma unroll
+        for (int u = 0; u < R; ++u) sx[swz(b * R + u)] = z[outpos<R>(u)];
+    }
+}
+
+// The fused row pass on one row: inputs read from xin / yin (plain layout: global memory, or a
+// landing buffer in shared memory), working buffers sx / sy (swizzled), result written to xout.
 template <int PI, bool SQR>
 __device__ __forceinline__ void row_mul_core(const PlanDev &pd, uint32_t *sx, uint32_t *sy,
                                              const uint32_t *xin, const uint32_t *yin,
@@ -347,21 +442,17 @@ __device__ __forceinline__ void row_mul_core(const PlanDev &pd, uint32_t *sx, ui
     const uint32_t n = pd.N2;
     const uint2 *tw = pd.tw[PI];
     const int ns = pd.nrs;
-    DMUL_RADIX_SWITCH(pd.rs[0].R, (rowf_first<PI, RR>(pd.rs[0], tw, xin, sx)));
-    if (!SQR) DMUL_RADIX_SWITCH(pd.rs[0].R, (rowf_first<PI, RR>(pd.rs[0], tw, yin, sy)));
-    __syncthreads();
-    for (int t = 1; t < ns - 1; ++t) {
-        DMUL_RADIX_SWITCH(pd.rs[t].R, (row_mid<PI, RR, false>(pd.rs[t], tw, sx, n)));
-        if (!SQR) DMUL_RADIX_SWITCH(pd.rs[t].R, (row_mid<PI, RR, false>(pd.rs[t], tw, sy, n)));
+    const uint32_t nops = SQR ? 1u : 2u;
+    for (int t = 0; t < ns - 1; ++t) {
+        DMUL_RADIX_SWITCH(pd.rs[t].R, (row_fwd_stage<PI, RR>(pd.rs[t], tw, sx, sy, xin, yin, t == 0, n, nops)));
         __syncthreads();
     }
-    DMUL_RADIX_SWITCH(pd.rs[ns - 1].R, (row_fused_center<PI, RR, SQR>(sx, sy, n)));
+    DMUL_RADIX_SWITCH(pd.rs[ns - 1].R, (row_center<PI, RR, SQR>(sx, sy, n)));
     __syncthreads();
-    for (int t = ns - 2; t >= 1; --t) {
-        DMUL_RADIX_SWITCH(pd.rs[t].R, (row_mid<PI, RR, true>(pd.rs[t], tw, sx, n)));
-        __syncthreads();
+    for (int t = ns - 2; t >= 0; --t) {
+        DMUL_RADIX_SWITCH(pd.rs[t].R, (row_inv_stage<PI, RR>(pd.rs[t], tw, sx, t == 0 ? xout : nullptr, n)));
+        if (t > 0) __syncthreads();
     }
-    DMUL_RADIX_SWITCH(pd.rs[0].R, (rowi_last<PI, RR>(pd.rs[0], tw, sx, xout)));
 }
 
 template <int PI, bool SQR>

@@ -157,6 +157,30 @@ int dmul_conv_coeffs(dmul_ctx *ctx, const uint32_t *x, size_t nx, const uint32_t
 int dmul_carry(dmul_ctx *ctx, const uint32_t *d, size_t L, uint32_t *z, size_t z_cap,
                uint64_t *nz, void *stream);
 
+/* The carry stage of dmul_carry, for callers that cannot allocate device memory.  (The paper has
+ * no counterpart: this is a deployment variant, not a step of the method.)
+ *
+ * Who needs it: code whose process hands the whole GPU to another allocator (a caching allocator
+ * that has reserved the device), code on a latency-critical path that cannot pay for cudaMalloc's
+ * implicit device-wide synchronization, and code that cannot create a context (dmul_init
+ * allocates).  This function takes no context and allocates nothing: its scratch (chunk spills, the
+ * lookahead control block and a status word) lives in one static device array of about 1 MiB that
+ * every GPU loading the library holds until the process exits.
+ *
+ * Arguments as dmul_carry: d holds L base-10^9 digit triples (device), z receives L limbs (device,
+ * z_cap >= L, not overlapping d), nz (device pointer or NULL) the normalized length.  L may be at
+ * most DMUL_NOALLOC_MAX_LIMBS; longer inputs return DMUL_ERR_TOO_LARGE without touching the GPU.
+ * Device-side errors (the sum does not fit L limbs, an expired bounded wait) set *nz to 0, a value
+ * no valid result has; pass nz to see them.  Asynchronous on `stream`, on the current device.
+ *
+ * The first call on a device looks up the array's device address (once per device); make that
+ * first call before any stream capture.  All calls share the one array and the next call
+ * overwrites it: calls whose work overlaps on the GPU (different streams, or several host threads)
+ * race and must be serialized by the caller. */
+#define DMUL_NOALLOC_MAX_LIMBS (1ull << 22)
+int dmul_carry_noalloc(const uint32_t *d, size_t L, uint32_t *z, size_t z_cap, uint64_t *nz,
+                       void *stream);
+
 /* In-place transpose of a rows x cols row-major uint32 matrix on the device (Sec. 7.5-7.6):
  * square matrices by tile-pair swaps (TransposeSquareSubMatrix semantics); n x 2n by the paper's
  * procedure (rho on every row, then the two n x n halves transposed in place with row stride

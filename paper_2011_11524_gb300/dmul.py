@@ -36,6 +36,7 @@ EXPORTS = [
     "dmul_mul_host", "dmul_batch", "dmul_submit", "dmul_poll", "dmul_wait", "dmul_conv_residues",
     "dmul_conv_coeffs", "dmul_carry", "dmul_transpose", "dmul_get_plan", "dmul_primes",
     "dmul_lambda", "dmul_max_min_limbs", "dmul_stage_times", "dmul_probe_imad",
+    "dmul_carry_noalloc",
 ]
 
 
@@ -90,6 +91,7 @@ def load() -> ctypes.CDLL:
         "dmul_conv_coeffs": ([vp, vp, sz, vp, sz, vp, vp], i32),
         "dmul_carry": ([vp, vp, sz, vp, sz, vp, vp], i32),
         "dmul_transpose": ([vp, vp, sz, sz, vp], i32),
+        "dmul_carry_noalloc": ([vp, sz, vp, sz, vp, vp], i32),
         "dmul_get_plan": ([vp, u64, ctypes.POINTER(dmul_plan_info)], i32),
         "dmul_primes": ([ctypes.POINTER(ctypes.c_uint32)], i32),
         "dmul_lambda": ([i32, i32, i32], i32),
@@ -210,6 +212,14 @@ def dmul_conv_coeffs(ctx, x, nx, y, ny, d, stream=None) -> int:
 
 def dmul_carry(ctx, d, L, z, z_cap, nz, stream=None) -> int:
     return load().dmul_carry(ctx, _ptr(d), L, _ptr(z), z_cap, _ptr(nz), _stream(stream))
+
+
+def dmul_carry_noalloc(d, L, z, z_cap, nz, stream=None) -> int:
+    """The carry stage without a context or any device allocation (see include/dmul.h)."""
+    return load().dmul_carry_noalloc(_ptr(d), L, _ptr(z), z_cap, _ptr(nz), _stream(stream))
+
+
+DMUL_NOALLOC_MAX_LIMBS = 1 << 22
 
 
 def dmul_transpose(ctx, a, rows, cols, stream=None) -> int:

@@ -197,12 +197,14 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
+        torch.cuda.nvtx.range_push("timed")  # ncu --nvtx-include "timed/" captures only these
         for i in range(args.steps):
             flush.zero_()
             evs[i][0].record(stream)
             step()
             evs[i][1].record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         ms = [a.elapsed_time(b) for a, b in evs]
         clk = clocks.stop()
     rc = d.dmul_sync(ctx.handle, sptr)
@@ -271,6 +273,10 @@ def run_ours(args, rank, world, local):
         "config": {"workload": WORKLOAD if digits == DIGITS else f"{digits} x {digits}-digit random multiplication",
                    "digits_x": digits, "digits_y": digits, "limbs": [nx, ny],
                    "N": int(info.N), "split": [int(info.N1), int(info.N2)], "primes": 3,
+                   "col_radix": [r for r in info.col_radix if r], "row_radix": [r for r in info.row_radix if r],
+                   "col_threads": int(info.col_threads), "row_threads": int(info.row_threads),
+                   "row_pass": (f"persistent TMA-fed, {int(info.row_grid)} CTAs/prime" if info.row_tma
+                                else "one CTA per row"),
                    "l2": f"flushed between timed steps ({args.flush_mb} MiB write)", "parallelism": "replicas"},
         "e2e": e2e_out,
         "gpu_launches": int(launches) * args.steps,
@@ -439,8 +445,22 @@ def run_served(d, torch, dev, count=2000, load=0.7, budget_gib=8):
                     head += 1
         lat = sorted((done_t[i] - (start + float(arrivals[i]))) * 1e3 for i in range(count))
         wall = max(done_t) - start
+    # the same requests one at a time through the plain form, back to back
+    with d.Context(dev.index or 0) as plain:
+        stream = torch.cuda.Stream(device=dev)
+        sp = stream.cuda_stream
+        for (tx, nx, ty, ny, z, L, nz) in dj[:64]:
+            d.dmul_mul(plain.handle, tx, nx, ty, ny, z, L, nz, sp)
+        assert d.dmul_sync(plain.handle, sp) == 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for (tx, nx, ty, ny, z, L, nz) in dj:
+            assert d.dmul_mul(plain.handle, tx, nx, ty, ny, z, L, nz, sp) == 0
+        assert d.dmul_sync(plain.handle, sp) == 0
+        plain_rate = count / (time.perf_counter() - t0)
     digits = sum(len(j.x) + len(j.y) for j in jobs) * 9
     return {"workload": f"{count} Poisson requests, digits log-uniform 10^2..10^7, 30% squarings",
+            "plain_mults_per_s_same_requests": plain_rate,
             "hbm_budget_gib": budget_gib, "saturated_mults_per_s": sat, "offered_rate_per_s": rate,
             "mults_per_s": count / wall, "digits_per_s": digits / wall,
             "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}

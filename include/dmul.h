@@ -197,9 +197,14 @@ typedef struct {
     uint32_t col_radix[8];/* radix of each column stage, first to last (0 ends the list)   */
     uint32_t row_radix[8];/* radix of each row stage                                        */
     uint32_t sixstep;     /* 1 when the context uses the six-step form                      */
+    uint32_t col_threads; /* CTA size of the column passes                                  */
+    uint32_t row_threads; /* CTA size of the row pass                                       */
+    uint32_t row_tma;     /* 1: persistent row pass fed by bulk async copies (TMA)          */
+    uint32_t row_grid;    /* its CTAs per prime                                             */
 } dmul_plan_info;
 
-/* Plan the transform for a product of L limbs (L >= 2).  ctx may be NULL (default plan). */
+/* Plan the transform for a product of L limbs (L >= 2).  ctx may be NULL (default plan); with a
+ * context, the plan it has tuned for that length (after its first use) is reported. */
 int dmul_get_plan(const dmul_ctx *ctx, uint64_t L, dmul_plan_info *out);
 
 /* The library's prime set (ascending), found by FindPrimes(w = 31, n_min = 23, l = 3) of Sec. 4.5

@@ -320,6 +320,71 @@ int check_sizes(dmul_ctx *c, size_t nx, size_t ny, uint64_t *N) {
 int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
                        const uint32_t *y, size_t ny, bool square, cudaStream_t s);
 
+// A lone short product can run as one cluster (the fused kernel: one launch, three SMs) or as the
+// four-step pipeline (four launches, many CTAs).  Which is faster depends on the length; the
+// first product of each short length times both on zero operands (identical results) and keeps
+// the faster.
+int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
+    auto it = c->small_single.find(Ns);
+    if (it != c->small_single.end()) {
+        *use_small = it->second;
+        return DMUL_OK;
+    }
+    SmallPlanEntry *se;
+    PlanEntry *pe;
+    int rc = get_small_plan(c, Ns, &se);
+    if (!rc) rc = get_plan(c, N, &pe);
+    if (rc) return rc;
+    CK(cudaDeviceSynchronize());
+    const uint64_t Lt = Ns;  // a full-length product: L = N of the short plan
+    rc = ensure_scratch(c, N, Lt, true);
+    if (rc) return rc;
+    uint32_t *buf = nullptr;
+    uint64_t *nzb = nullptr;
+    if ((rc = dev_alloc(c, (void **)&buf, 2 * Lt * 4))) return rc;
+    if ((rc = dev_alloc(c, (void **)&nzb, 64))) { dev_free(c, buf, 2 * Lt * 4); return rc; }
+    cudaStream_t s = c->own_stream;
+    cudaMemsetAsync(buf, 0, 2 * Lt * 4, s);
+    JobDev jd;
+    memset(&jd, 0, sizeof(jd));
+    jd.x = buf; jd.y = buf + Lt / 2; jd.z = buf + Lt; jd.nz = nzb; jd.nx = Lt / 2; jd.ny = Lt / 2; jd.L = Lt;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float t_small = 1e30f, t_four = 1e30f;
+    for (int it2 = 0; it2 < 4; ++it2) {
+        float ms = 0;
+        cudaEventRecord(e0, s);
+        launch_small_mul_one(se->sp, jd, c->status, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (it2) t_small = std::min(t_small, ms);
+        cudaEventRecord(e0, s);
+        launch_col_fwd(pe->pd, jd.x, jd.nx, jd.y, jd.ny, c->X, c->Y, c->status, s);
+        if (pe->pd.row_tma) launch_row_mul_tma(pe->pd, c->X, c->Y, false, c->status, s);
+        else launch_row_mul(pe->pd, c->X, c->Y, false, s);
+        launch_col_inv(pe->pd, c->X, Lt, kInvDigits, jd.z, c->spill, s);
+        cudaMemsetAsync(c->ctl, 0, carry_ctl_bytes(Lt), s);
+        launch_carry(jd.z, c->spill, Lt, (CarryCtl *)c->ctl, nzb, c->status, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (it2) t_four = std::min(t_four, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    uint32_t zero = 0;
+    cudaMemcpy(c->status, &zero, 4, cudaMemcpyHostToDevice);
+    dev_free(c, buf, 2 * Lt * 4);
+    dev_free(c, nzb, 64);
+    if (cudaGetLastError() != cudaSuccess) return DMUL_ERR_CUDA;
+    *use_small = t_small <= t_four;
+    c->small_single[Ns] = *use_small;
+    return DMUL_OK;
+}
+
 int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny,
                 uint32_t *z, size_t z_cap, uint64_t *nz, cudaStream_t s, InvMode mode,
                 uint32_t *mode_out) {
@@ -334,7 +399,12 @@ int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, si
     rc = set_device(c);
     if (rc) return rc;
     const uint64_t Ns = choose_N_small(L);
-    if (mode == kInvDigits && Ns && !(c->cfg.flags & (DMUL_FLAG_SIXSTEP | DMUL_FLAG_NO_SMALL))) {
+    bool use_small = mode == kInvDigits && Ns && !(c->cfg.flags & (DMUL_FLAG_SIXSTEP | DMUL_FLAG_NO_SMALL));
+    if (use_small && !(c->cfg.flags & DMUL_FLAG_NO_AUTOTUNE)) {
+        rc = prefer_small_single(c, Ns, N, &use_small);
+        if (rc) return rc;
+    }
+    if (use_small) {
         // the whole product in one cluster launch (batch.cu): transforms, CRT and carry in SMEM
         SmallPlanEntry *se;
         rc = get_small_plan(c, Ns, &se);
@@ -490,6 +560,10 @@ int dmul_get_plan(const dmul_ctx *ctx, uint64_t L, dmul_plan_info *out) {
     for (size_t i = 0; i < hp.col_radix.size() && i < 8; ++i) out->col_radix[i] = hp.col_radix[i];
     for (size_t i = 0; i < hp.row_radix.size() && i < 8; ++i) out->row_radix[i] = hp.row_radix[i];
     out->sixstep = (ctx && (ctx->cfg.flags & DMUL_FLAG_SIXSTEP)) ? 1u : 0u;
+    out->col_threads = hp.col_threads ? hp.col_threads : (hp.N1 >= 512 ? 512 : 256);
+    out->row_threads = hp.row_threads ? hp.row_threads : 256;
+    out->row_tma = hp.row_tma;
+    out->row_grid = hp.row_grid;
     return DMUL_OK;
 }
 

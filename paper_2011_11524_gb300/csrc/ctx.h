@@ -73,6 +73,7 @@ struct dmul_ctx {
     uint64_t used = 0;  // library-owned device bytes
     std::map<uint64_t, std::unique_ptr<dml::PlanEntry>> plans;
     std::map<uint64_t, std::unique_ptr<dml::SmallPlanEntry>> small_plans;
+    std::map<uint64_t, bool> small_single;  // per short length: fused kernel faster than four-step
     // scratch of the plain form (one set, used by one call at a time)
     uint32_t *X = nullptr, *Y = nullptr;
     size_t res_words = 0;  // capacity of X and of Y, in words

@@ -60,7 +60,9 @@ class dmul_job(ctypes.Structure):
 class dmul_plan_info(ctypes.Structure):
     _fields_ = [("primes", ctypes.c_uint32 * 3), ("N", ctypes.c_uint64), ("N1", ctypes.c_uint32),
                 ("N2", ctypes.c_uint32), ("col_radix", ctypes.c_uint32 * 8),
-                ("row_radix", ctypes.c_uint32 * 8), ("sixstep", ctypes.c_uint32)]
+                ("row_radix", ctypes.c_uint32 * 8), ("sixstep", ctypes.c_uint32),
+                ("col_threads", ctypes.c_uint32), ("row_threads", ctypes.c_uint32),
+                ("row_tma", ctypes.c_uint32), ("row_grid", ctypes.c_uint32)]
 
 
 _lib = None

@@ -159,8 +159,7 @@ static int autotune_plan(dmul_ctx *c, uint64_t N, std::unique_ptr<PlanEntry> *be
                     for (int it = 0; it < 3; ++it) {
                         cudaEventRecord(e0, s);
                         launch_col_fwd(cand->pd, in, N / 2, in + N / 2, N / 2, c->X, c->Y, c->status, s);
-                        if (rv.first) launch_row_mul_tma(cand->pd, c->X, c->Y, false, c->status, s);
-                        else launch_row_mul(cand->pd, c->X, c->Y, false, s);
+                        launch_row_any(cand->pd, c->X, c->Y, false, c->status, s);
                         launch_col_inv(cand->pd, c->X, N, kInvDigits, zt, sp, s);
                         cudaEventRecord(e1, s);
                         cudaEventSynchronize(e1);
@@ -362,8 +361,7 @@ int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
         if (it2) t_small = std::min(t_small, ms);
         cudaEventRecord(e0, s);
         launch_col_fwd(pe->pd, jd.x, jd.nx, jd.y, jd.ny, c->X, c->Y, c->status, s);
-        if (pe->pd.row_tma) launch_row_mul_tma(pe->pd, c->X, c->Y, false, c->status, s);
-        else launch_row_mul(pe->pd, c->X, c->Y, false, s);
+        launch_row_any(pe->pd, c->X, c->Y, false, c->status, s);
         launch_col_inv(pe->pd, c->X, Lt, kInvDigits, jd.z, c->spill, s);
         cudaMemsetAsync(c->ctl, 0, carry_ctl_bytes(Lt), s);
         launch_carry(jd.z, c->spill, Lt, (CarryCtl *)c->ctl, nzb, c->status, s);
@@ -451,8 +449,7 @@ int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
             CK(launch_col_fwd(pd, x, nx, square ? nullptr : y, ny, c->X, c->Y, c->status, s));
         }
         Timed t(c, kStRowMul, s);
-        if (pd.row_tma) CK(launch_row_mul_tma(pd, c->X, c->Y, square, c->status, s));
-        else CK(launch_row_mul(pd, c->X, c->Y, square, s));
+        CK(launch_row_any(pd, c->X, c->Y, square, c->status, s));
         return DMUL_OK;
     }
     // Six-step form (Sec. 7.2): [N1 x N2] -> transpose -> row DFTs of length N1 -> transpose
@@ -593,9 +590,11 @@ int dmul_init(dmul_ctx **out, const dmul_config *cfg) {
     CK(upload_constants_main(pc, crt));
     CK(upload_constants_sixstep(pc, crt));
     CK(upload_constants_batch(pc, crt));
+    CK(upload_constants_rowpass(pc, crt));
     CK(init_kernel_attributes_main());
     CK(init_kernel_attributes_sixstep());
     CK(init_kernel_attributes_batch());
+    CK(init_kernel_attributes_rowpass());
     int rc = dev_alloc(c.get(), (void **)&c->status, 256);
     if (rc) return rc;
     CK(cudaMemset(c->status, 0, 256));

@@ -66,6 +66,13 @@ cudaError_t launch_row_mul_tma(const PlanDev &pd, uint32_t *X, const uint32_t *Y
     return cudaGetLastError();
 }
 
+cudaError_t launch_row_any(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
+                           uint32_t *status, cudaStream_t s) {
+    if (row_pass_specialized(pd)) return launch_row_pass_ct(pd, X, Y, square, status, s);
+    if (pd.row_tma) return launch_row_mul_tma(pd, X, Y, square, status, s);
+    return launch_row_mul(pd, X, Y, square, s);
+}
+
 cudaError_t launch_row_mul(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
                            cudaStream_t s) {
     dim3 grid(pd.N1, kPrimes);

@@ -57,6 +57,18 @@ cudaError_t launch_row_mul(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bo
 cudaError_t launch_row_mul_tma(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
                                uint32_t *status, cudaStream_t s);
 
+// Specialized row passes for N2 in {1024, 2048, 4096, 8192} with the planner's schedule
+// (rowpass.cu), plain or TMA-fed per pd.row_tma.
+bool row_pass_specialized(const PlanDev &pd);
+cudaError_t launch_row_pass_ct(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
+                               uint32_t *status, cudaStream_t s);
+cudaError_t init_kernel_attributes_rowpass();
+cudaError_t upload_constants_rowpass(const PrimeConst pc[kPrimes], const CrtConst &crt);
+
+// The row pass the plan asks for: specialized when available, else the generic plain or TMA form.
+cudaError_t launch_row_any(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
+                           uint32_t *status, cudaStream_t s);
+
 // Inverse column pass + (mode) CRT and digit split.  kInvDigits writes the within-chunk digit
 // sums to out[0..L) and the chunk spills to spill; kInvTriples writes d[3k..3k+2]; kInvResidues
 // writes r[pi*L + k].

@@ -1,0 +1,266 @@
+// rowpass.cu -- the fused row pass specialized for the common row lengths N2 = 1024 .. 8192.
+//
+// Same arithmetic and data layout as the generic row pass (stages.cuh: forward row DFTs of X and
+// Y, pointwise Montgomery product, inverse row DFTs, Sec. 5.4 / 6 / 7.1), but the row length is
+// a template parameter, so every stage's radix, span and stride are compile-time constants: group
+// indices become shifts and masks, and most swizzled shared-memory addresses fold into immediate
+// offsets.  The radix schedule is the planner's (a small radix first, then radix 16); the
+// dispatcher checks that the plan has exactly that schedule and otherwise uses the generic pass.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+#include "modarith.cuh"
+#include "stages.cuh"
+
+namespace dml {
+
+DMUL_DEFINE_UPLOAD(upload_constants_rowpass)
+
+// Compile-time radix schedule of a power-of-two length N (the planner's pow2_schedule).
+template <uint32_t N>
+struct Pow2Sched {
+    static constexpr int A = ilog2c((int)N);
+    static constexpr int NS = (A % 4 ? 1 : 0) + A / 4;
+    static constexpr uint32_t radix(int t) { return (A % 4 && t == 0) ? (1u << (A % 4)) : 16u; }
+    static constexpr uint32_t span(int t) {  // m of stage t
+        uint32_t m = N;
+        for (int i = 0; i < t; ++i) m /= radix(i);
+        return m;
+    }
+};
+
+template <int PI, uint32_t R, uint32_t M, uint32_t N>
+__device__ __forceinline__ void fwd_stage_ct(const Stage &st, const uint2 *tw, uint32_t *sx,
+                                             uint32_t *sy, const uint32_t *gx, const uint32_t *gy,
+                                             bool from_plain, uint32_t nops) {
+    constexpr uint32_t stride = M / R;
+    constexpr uint32_t per_op = N / R;
+    constexpr bool has_tw = M > R;
+    for (uint32_t g = threadIdx.x; g < per_op * nops; g += blockDim.x) {
+        const bool second = g >= per_op;
+        const uint32_t gg = second ? g - per_op : g;
+        uint32_t *sb = second ? sy : sx;
+        const uint32_t blk = gg / stride, j = gg % stride;
+        const uint32_t base = blk * M + j;
+        uint32_t v[R];
+        if (from_plain) {
+            const uint32_t *src = second ? gy : gx;
+#pragma unroll
+            for (uint32_t u = 0; u < R; ++u) v[u] = src[base + u * stride];
+        } else {
+#pragma unroll
+            for (uint32_t u = 0; u < R; ++u) v[u] = sb[swz(base + u * stride)];
+        }
+        dft<PI, 0, (int)R>(v);
+#pragma unroll
+        for (uint32_t k = 0; k < R; ++k) {
+            uint32_t o = v[outpos<(int)R>((int)k)];
+            if (k > 0 && has_tw) {
+                const uint2 w = ldtw(tw + st.tw + (k - 1) * stride + j);
+                o = shoup<PI>(o, w.x, w.y);
+            }
+            sb[swz(base + k * stride)] = o;
+        }
+    }
+}
+
+template <int PI, uint32_t R, uint32_t M, uint32_t N>
+__device__ __forceinline__ void inv_stage_ct(const Stage &st, const uint2 *tw, uint32_t *sb,
+                                             uint32_t *gout) {
+    constexpr uint32_t stride = M / R;
+    constexpr uint32_t groups = N / R;
+    constexpr bool has_tw = M > R;
+    for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
+        const uint32_t blk = g / stride, j = g % stride;
+        const uint32_t base = blk * M + j;
+        uint32_t v[R];
+#pragma unroll
+        for (uint32_t k = 0; k < R; ++k) v[k] = sb[swz(base + k * stride)];
+        if (has_tw) {
+#pragma unroll
+            for (uint32_t k = 1; k < R; ++k) {
+                const uint2 w = ldtw(tw + st.twi + (k - 1) * stride + j);
+                v[k] = shoup<PI>(v[k], w.x, w.y);
+            }
+        }
+        dft<PI, 1, (int)R>(v);
+        if (gout) {
+#pragma unroll
+            for (uint32_t u = 0; u < R; ++u) gout[base + u * stride] = v[outpos<(int)R>((int)u)];
+        } else {
+#pragma unroll
+            for (uint32_t u = 0; u < R; ++u) sb[swz(base + u * stride)] = v[outpos<(int)R>((int)u)];
+        }
+    }
+}
+
+// forward stages 0 .. NS-2, then the center, then inverse stages NS-2 .. 0
+template <int PI, uint32_t N, int T>
+__device__ __forceinline__ void fwd_stages_ct(const PlanDev &pd, const uint2 *tw, uint32_t *sx,
+                                              uint32_t *sy, const uint32_t *gx, const uint32_t *gy,
+                                              uint32_t nops) {
+    using S = Pow2Sched<N>;
+    if constexpr (T < S::NS - 1) {
+        fwd_stage_ct<PI, S::radix(T), S::span(T), N>(pd.rs[T], tw, sx, sy, gx, gy, T == 0, nops);
+        __syncthreads();
+        fwd_stages_ct<PI, N, T + 1>(pd, tw, sx, sy, gx, gy, nops);
+    }
+}
+
+template <int PI, uint32_t N, int T>
+__device__ __forceinline__ void inv_stages_ct(const PlanDev &pd, const uint2 *tw, uint32_t *sx,
+                                              uint32_t *xout) {
+    using S = Pow2Sched<N>;
+    if constexpr (T >= 0) {
+        inv_stage_ct<PI, S::radix(T), S::span(T), N>(pd.rs[T], tw, sx, T == 0 ? xout : nullptr);
+        if (T > 0) __syncthreads();
+        inv_stages_ct<PI, N, T - 1>(pd, tw, sx, xout);
+    }
+}
+
+template <int PI, uint32_t N, bool SQR>
+__device__ __forceinline__ void row_core_ct(const PlanDev &pd, uint32_t *sx, uint32_t *sy,
+                                            const uint32_t *xin, const uint32_t *yin,
+                                            uint32_t *__restrict__ xout) {
+    using S = Pow2Sched<N>;
+    const uint2 *tw = pd.tw[PI];
+    fwd_stages_ct<PI, N, 0>(pd, tw, sx, sy, xin, yin, SQR ? 1u : 2u);
+    row_center<PI, (int)S::radix(S::NS - 1), SQR>(sx, sy, N);
+    __syncthreads();
+    inv_stages_ct<PI, N, S::NS - 2>(pd, tw, sx, xout);
+}
+
+template <uint32_t N, bool SQR>
+__global__ void __launch_bounds__(256) k_row_ct(const PlanDev pd, uint32_t *X, const uint32_t *Y) {
+    extern __shared__ uint32_t sm[];
+    const uint32_t row = blockIdx.x;
+    const int pi = blockIdx.y;
+    uint32_t *xr = X + (uint64_t)pi * pd.N + (uint64_t)row * N;
+    const uint32_t *yr = SQR ? nullptr : Y + (uint64_t)pi * pd.N + (uint64_t)row * N;
+    DMUL_PRIME_SWITCH(pi, (row_core_ct<PI, N, SQR>(pd, sm, sm + N, xr, yr, xr)));
+}
+
+// persistent TMA-fed form (see row_mul_tma_body in stages.cuh for the protocol)
+template <int PI, uint32_t N, bool SQR>
+__device__ __forceinline__ void row_tma_ct_body(const PlanDev &pd, uint32_t *sm, uint32_t *X,
+                                                const uint32_t *Y, uint32_t *status) {
+    uint32_t *land = sm;
+    uint32_t *sx = sm + 4 * N, *sy = sm + 5 * N;
+    uint64_t *bar = (uint64_t *)(sm + 6 * N);
+    const uint32_t G = gridDim.x;
+    const uint64_t base = (uint64_t)PI * pd.N;
+    constexpr uint32_t bytes = N * 4;
+    constexpr uint32_t per_row = (SQR ? 1u : 2u) * bytes;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    uint32_t r = blockIdx.x;
+    if (threadIdx.x == 0 && r < pd.N1) {
+        mbar_expect_tx(&bar[0], per_row);
+        tma_load_1d(land, X + base + (uint64_t)r * N, bytes, &bar[0]);
+        if (!SQR) tma_load_1d(land + N, Y + base + (uint64_t)r * N, bytes, &bar[0]);
+    }
+    for (uint32_t it = 0; r < pd.N1; ++it, r += G) {
+        const uint32_t b = it & 1u;
+        const uint32_t rn = r + G;
+        if (threadIdx.x == 0 && rn < pd.N1) {
+            uint32_t *dst = land + (b ^ 1u) * 2 * N;
+            fence_proxy_async();
+            mbar_expect_tx(&bar[b ^ 1u], per_row);
+            tma_load_1d(dst, X + base + (uint64_t)rn * N, bytes, &bar[b ^ 1u]);
+            if (!SQR) tma_load_1d(dst + N, Y + base + (uint64_t)rn * N, bytes, &bar[b ^ 1u]);
+        }
+        const int ok = __syncthreads_and(mbar_wait(&bar[b], (it >> 1) & 1u) ? 1 : 0);
+        if (!ok) {
+            if (threadIdx.x == 0) {
+                atomicOr(status, kStatusTimeout);
+                if (rn < pd.N1) mbar_wait(&bar[b ^ 1u], ((it + 1) >> 1) & 1u);
+            }
+            return;
+        }
+        const uint32_t *lx = land + b * 2 * N;
+        row_core_ct<PI, N, SQR>(pd, sx, sy, lx, lx + N, X + base + (uint64_t)r * N);
+        __syncthreads();
+    }
+}
+
+template <uint32_t N, bool SQR>
+__global__ void __launch_bounds__(256) k_row_tma_ct(const PlanDev pd, uint32_t *X, const uint32_t *Y,
+                                                    uint32_t *status) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    const int pi = blockIdx.y;
+    DMUL_PRIME_SWITCH(pi, (row_tma_ct_body<PI, N, SQR>(pd, sm, X, Y, status)));
+}
+
+template <uint32_t N>
+static bool schedule_matches(const PlanDev &pd) {
+    using S = Pow2Sched<N>;
+    if (pd.N2 != N || pd.nrs != S::NS) return false;
+    for (int t = 0; t < S::NS; ++t)
+        if (pd.rs[t].R != S::radix(t) || pd.rs[t].m != S::span(t)) return false;
+    return true;
+}
+
+template <uint32_t N>
+static cudaError_t launch_ct(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
+                             uint32_t *status, cudaStream_t s) {
+    if (pd.row_tma) {
+        dim3 grid(pd.row_grid ? pd.row_grid : 256, kPrimes);
+        const size_t smem = (size_t)6 * N * 4 + 16;
+        if (square) k_row_tma_ct<N, true><<<grid, pd.row_threads, smem, s>>>(pd, X, Y, status);
+        else k_row_tma_ct<N, false><<<grid, pd.row_threads, smem, s>>>(pd, X, Y, status);
+    } else {
+        dim3 grid(pd.N1, kPrimes);
+        const size_t smem = (size_t)(square ? 1 : 2) * N * 4;
+        if (square) k_row_ct<N, true><<<grid, pd.row_threads, smem, s>>>(pd, X, Y);
+        else k_row_ct<N, false><<<grid, pd.row_threads, smem, s>>>(pd, X, Y);
+    }
+    return cudaGetLastError();
+}
+
+bool row_pass_specialized(const PlanDev &pd) {
+    switch (pd.N2) {
+        case 1024: return schedule_matches<1024>(pd);
+        case 2048: return schedule_matches<2048>(pd);
+        case 4096: return schedule_matches<4096>(pd);
+        case 8192: return schedule_matches<8192>(pd);
+        default: return false;
+    }
+}
+
+cudaError_t launch_row_pass_ct(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
+                               uint32_t *status, cudaStream_t s) {
+    switch (pd.N2) {
+        case 1024: return launch_ct<1024>(pd, X, Y, square, status, s);
+        case 2048: return launch_ct<2048>(pd, X, Y, square, status, s);
+        case 4096: return launch_ct<4096>(pd, X, Y, square, status, s);
+        default: return launch_ct<8192>(pd, X, Y, square, status, s);
+    }
+}
+
+template <uint32_t N>
+static cudaError_t attrs_ct() {
+    cudaError_t e;
+    const int plain = 2 * N * 4, tma = 6 * N * 4 + 16;
+    if ((e = cudaFuncSetAttribute(k_row_ct<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, plain)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_row_ct<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, plain)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_row_tma_ct<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tma)))
+        return e;
+    return cudaFuncSetAttribute(k_row_tma_ct<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tma);
+}
+
+cudaError_t init_kernel_attributes_rowpass() {
+    cudaError_t e;
+    if ((e = attrs_ct<1024>())) return e;
+    if ((e = attrs_ct<2048>())) return e;
+    if ((e = attrs_ct<4096>())) return e;
+    return attrs_ct<8192>();
+}
+
+}  // namespace dml

@@ -591,10 +591,12 @@ int dmul_init(dmul_ctx **out, const dmul_config *cfg) {
     CK(upload_constants_sixstep(pc, crt));
     CK(upload_constants_batch(pc, crt));
     CK(upload_constants_rowpass(pc, crt));
+    CK(upload_constants_colpass(pc, crt));
     CK(init_kernel_attributes_main());
     CK(init_kernel_attributes_sixstep());
     CK(init_kernel_attributes_batch());
     CK(init_kernel_attributes_rowpass());
+    CK(init_kernel_attributes_colpass());
     int rc = dev_alloc(c.get(), (void **)&c->status, 256);
     if (rc) return rc;
     CK(cudaMemset(c->status, 0, 256));

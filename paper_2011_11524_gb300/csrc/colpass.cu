@@ -1,0 +1,347 @@
+// colpass.cu -- the forward and inverse column passes specialized for N1 in {512, 768, 1024, 1536}.
+//
+// Same arithmetic, layout and order as the generic column passes (stages.cuh: column DFTs of
+// length N1 with the four-step twiddle, Sec. 7.1 / 7.8; the inverse with the 2^32 N^-1 scale of
+// Sec. 6 and the cluster CRT of Sec. 8.2.2), with N1 a template parameter so that each stage's
+// radix, span and stride are compile-time constants (group indices become shifts, shared-memory
+// addresses immediate offsets).  The dispatcher uses them only when the plan's column schedule is
+// the planner's (radix 3 first for 3*2^a, then a small power of two, then radix 16).
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+#include "modarith.cuh"
+#include "stages.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace dml {
+
+DMUL_DEFINE_UPLOAD(upload_constants_colpass)
+
+template <uint32_t N1>
+struct ColSched {
+    static constexpr bool THREE = (N1 % 3) == 0;
+    static constexpr uint32_t P = THREE ? N1 / 3 : N1;
+    static constexpr int A = ilog2c((int)P);
+    static constexpr int NS = (THREE ? 1 : 0) + (A % 4 ? 1 : 0) + A / 4;
+    static constexpr uint32_t radix(int t) {
+        if (THREE) {
+            if (t == 0) return 3;
+            t -= 1;
+        }
+        return (A % 4 && t == 0) ? (1u << (A % 4)) : 16u;
+    }
+    static constexpr uint32_t span(int t) {
+        uint32_t m = N1;
+        for (int i = 0; i < t; ++i) m /= radix(i);
+        return m;
+    }
+};
+
+// stage 0 of the forward pass on the staged limb tile (in place)
+template <int PI, uint32_t R, uint32_t N1>
+__device__ __forceinline__ void colf0_ct(const Stage &st, const uint2 *tw, uint32_t *sm, uint32_t &bad) {
+    constexpr uint32_t stride = N1 / R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (uint32_t j = warp; j < stride; j += nw) {
+        uint32_t v[R];
+#pragma unroll
+        for (uint32_t u = 0; u < R; ++u) {
+            uint32_t a = sm[(j + u * stride) * 32 + lane];
+            bad |= (a >= kBase);
+            if (PI == 0) a = red2p<PI>(a);  // 10^9 < 4 p0: [0, 10^9) -> [0, 2 p0)
+            v[u] = a;
+        }
+        dft<PI, 0, (int)R>(v);
+#pragma unroll
+        for (uint32_t k = 0; k < R; ++k) {
+            uint32_t o = v[outpos<(int)R>((int)k)];
+            if (k > 0) {
+                const uint2 w = ldtw(tw + st.tw + (k - 1) * stride + j);
+                o = shoup<PI>(o, w.x, w.y);
+            }
+            sm[(j + k * stride) * 32 + lane] = o;
+        }
+    }
+}
+
+// a middle stage (forward: DFT then twiddle; inverse: untwiddle then DFT), in place
+template <int PI, uint32_t R, uint32_t M, uint32_t N1, bool INV>
+__device__ __forceinline__ void colmid_ct(const Stage &st, const uint2 *tw, uint32_t *sm,
+                                          bool final_reduce) {
+    constexpr uint32_t stride = M / R;
+    constexpr uint32_t groups = N1 / R;
+    constexpr bool has_tw = M > R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (uint32_t g = warp; g < groups; g += nw) {
+        const uint32_t blk = g / stride, j = g % stride;
+        const uint32_t base = blk * M + j;
+        uint32_t v[R];
+#pragma unroll
+        for (uint32_t u = 0; u < R; ++u) v[u] = sm[(base + u * stride) * 32 + lane];
+        if (!INV) {
+            dft<PI, 0, (int)R>(v);
+#pragma unroll
+            for (uint32_t k = 0; k < R; ++k) {
+                uint32_t o = v[outpos<(int)R>((int)k)];
+                if (k > 0 && has_tw) {
+                    const uint2 w = ldtw(tw + st.tw + (k - 1) * stride + j);
+                    o = shoup<PI>(o, w.x, w.y);
+                }
+                sm[(base + k * stride) * 32 + lane] = o;
+            }
+        } else {
+            if (has_tw) {
+#pragma unroll
+                for (uint32_t k = 1; k < R; ++k) {
+                    const uint2 w = ldtw(tw + st.twi + (k - 1) * stride + j);
+                    v[k] = shoup<PI>(v[k], w.x, w.y);
+                }
+            }
+            dft<PI, 1, (int)R>(v);
+#pragma unroll
+            for (uint32_t u = 0; u < R; ++u) {
+                uint32_t o = v[outpos<(int)R>((int)u)];
+                if (final_reduce) o = red1p<PI>(o);
+                sm[(base + u * stride) * 32 + lane] = o;
+            }
+        }
+    }
+}
+
+// Q[k][n2] for k = 1..R-1: the lane's column n2 is fixed for the whole tile, so the R-1 factors
+// are loaded once and kept in registers across the N1/R groups.
+template <int PI, uint32_t R>
+__device__ __forceinline__ void load_q(const uint2 *Q, uint32_t N2, uint32_t n2, uint2 (&q)[R]) {
+#pragma unroll
+    for (uint32_t k = 1; k < R; ++k) q[k] = ldtw(Q + (uint64_t)k * N2 + n2);
+}
+
+// last forward stage (m == R) + four-step twiddle Q[k][n2] * A[b][n2] + store of the residues
+template <int PI, uint32_t R, uint32_t N1>
+__device__ __forceinline__ void colf_last_ct(const PlanDev &pd, const uint32_t *sm,
+                                             uint32_t *__restrict__ dst, uint32_t n2) {
+    constexpr uint32_t nb = N1 / R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint2 *A = pd.tw[PI] + pd.offA;
+    uint2 q[R];
+    load_q<PI, R>(pd.tw[PI] + pd.offQ, pd.N2, n2, q);
+    for (uint32_t b = warp; b < nb; b += nw) {
+        uint32_t v[R];
+#pragma unroll
+        for (uint32_t u = 0; u < R; ++u) v[u] = sm[(b * R + u) * 32 + lane];
+        const uint2 a = ldtw(A + (uint64_t)b * pd.N2 + n2);
+        dft<PI, 0, (int)R>(v);
+#pragma unroll
+        for (uint32_t k = 0; k < R; ++k) {
+            uint32_t o = v[outpos<(int)R>((int)k)];
+            if (k > 0) o = shoup<PI>(o, q[k].x, q[k].y);
+            o = shoup<PI>(o, a.x, a.y);
+            dst[(uint64_t)(b * R + k) * pd.N2 + n2] = o;
+        }
+    }
+}
+
+// first inverse stage on the staged residue tile: inverse four-step twiddle, inverse DFT
+template <int PI, uint32_t R, uint32_t N1>
+__device__ __forceinline__ void coli_first_ct(const PlanDev &pd, uint32_t *sm, uint32_t n2) {
+    constexpr uint32_t nb = N1 / R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint2 *A = pd.tw[PI] + pd.offAi;
+    uint2 q[R];
+    load_q<PI, R>(pd.tw[PI] + pd.offQi, pd.N2, n2, q);
+    for (uint32_t b = warp; b < nb; b += nw) {
+        uint32_t v[R];
+        const uint2 a = ldtw(A + (uint64_t)b * pd.N2 + n2);
+#pragma unroll
+        for (uint32_t k = 0; k < R; ++k) {
+            uint32_t o = sm[(b * R + k) * 32 + lane];
+            if (k > 0) o = shoup<PI>(o, q[k].x, q[k].y);
+            v[k] = shoup<PI>(o, a.x, a.y);
+        }
+        dft<PI, 1, (int)R>(v);
+#pragma unroll
+        for (uint32_t u = 0; u < R; ++u) sm[(b * R + u) * 32 + lane] = v[outpos<(int)R>((int)u)];
+    }
+}
+
+// forward middle stages t = T .. NS-2
+template <int PI, uint32_t N1, int T>
+__device__ __forceinline__ void colf_mids_ct(const PlanDev &pd, uint32_t *sm) {
+    using S = ColSched<N1>;
+    if constexpr (T < S::NS - 1) {
+        colmid_ct<PI, S::radix(T), S::span(T), N1, false>(pd.cs[T], pd.tw[PI], sm, false);
+        __syncthreads();
+        colf_mids_ct<PI, N1, T + 1>(pd, sm);
+    }
+}
+
+// inverse middle stages t = T .. 0 (the last one reduces to [0, p))
+template <int PI, uint32_t N1, int T>
+__device__ __forceinline__ void coli_mids_ct(const PlanDev &pd, uint32_t *sm) {
+    using S = ColSched<N1>;
+    if constexpr (T >= 0) {
+        colmid_ct<PI, S::radix(T), S::span(T), N1, true>(pd.cs[T], pd.tw[PI], sm, T == 0);
+        __syncthreads();
+        coli_mids_ct<PI, N1, T - 1>(pd, sm);
+    }
+}
+
+template <int PI, uint32_t N1>
+__device__ __forceinline__ void col_fwd_ct_body(const PlanDev &pd, uint32_t *sm,
+                                                const uint32_t *__restrict__ src, uint64_t n,
+                                                uint32_t *__restrict__ dst, uint32_t tile,
+                                                uint32_t *status) {
+    using S = ColSched<N1>;
+    const uint32_t n2 = tile * 32 + (threadIdx.x & 31);
+    uint32_t bad = 0;
+    tile_load_async(sm, src, n, N1, pd.N2, tile * 32);
+    colf0_ct<PI, S::radix(0), N1>(pd.cs[0], pd.tw[PI], sm, bad);
+    if (PI == 0 && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusInvalid);
+    __syncthreads();
+    colf_mids_ct<PI, N1, 1>(pd, sm);
+    colf_last_ct<PI, S::radix(S::NS - 1), N1>(pd, sm, dst, n2);
+}
+
+template <int PI, uint32_t N1>
+__device__ __forceinline__ void col_inv_ct_body(const PlanDev &pd, const uint32_t *__restrict__ src,
+                                                uint32_t *sm, uint32_t n2) {
+    using S = ColSched<N1>;
+    tile_load_async(sm, src, pd.N, N1, pd.N2, n2 & ~31u);
+    coli_first_ct<PI, S::radix(S::NS - 1), N1>(pd, sm, n2);
+    __syncthreads();
+    coli_mids_ct<PI, N1, S::NS - 2>(pd, sm);
+}
+
+// grid (3 * N2/32, operands): blockIdx.x = 3 * tile + prime; x and y 16-byte aligned
+template <uint32_t N1>
+__global__ void __launch_bounds__(512) k_col_fwd_ct(const PlanDev pd, const uint32_t *__restrict__ x,
+                                                    uint64_t nx, const uint32_t *__restrict__ y,
+                                                    uint64_t ny, uint32_t *X, uint32_t *Y,
+                                                    uint32_t *status) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    const int pi = blockIdx.x % kPrimes;
+    const uint32_t tile = blockIdx.x / kPrimes;
+    const bool second = blockIdx.y != 0;
+    const uint32_t *src = second ? y : x;
+    const uint64_t n = second ? ny : nx;
+    uint32_t *dst = (second ? Y : X) + (uint64_t)pi * pd.N;
+    DMUL_PRIME_SWITCH(pi, (col_fwd_ct_body<PI, N1>(pd, sm, src, n, dst, tile, status)));
+}
+
+// cluster of three CTAs (rank = prime) per 32-column tile, then the CRT epilogue
+template <uint32_t N1, int MODE>
+__global__ void __launch_bounds__(512) k_col_inv_ct(const PlanDev pd, const uint32_t *__restrict__ X,
+                                                    uint64_t L, uint32_t *__restrict__ out,
+                                                    uint2 *__restrict__ spill) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    const int pi = (int)cg::this_cluster().block_rank();
+    const uint32_t n2 = (blockIdx.x / kPrimes) * 32 + (threadIdx.x & 31);
+    const uint32_t *src = X + (uint64_t)pi * pd.N;
+    DMUL_PRIME_SWITCH(pi, (col_inv_ct_body<PI, N1>(pd, src, sm, n2)));
+    col_crt_epilogue(pd, L, MODE, out, spill, sm);
+}
+
+template <uint32_t N1>
+static bool col_schedule_matches(const PlanDev &pd) {
+    using S = ColSched<N1>;
+    if (pd.N1 != N1 || pd.ncs != S::NS) return false;
+    for (int t = 0; t < S::NS; ++t)
+        if (pd.cs[t].R != S::radix(t) || pd.cs[t].m != S::span(t)) return false;
+    return true;
+}
+
+bool col_pass_specialized(const PlanDev &pd) {
+    switch (pd.N1) {
+        case 512: return col_schedule_matches<512>(pd);
+        case 768: return col_schedule_matches<768>(pd);
+        case 1024: return col_schedule_matches<1024>(pd);
+        case 1536: return col_schedule_matches<1536>(pd);
+        default: return false;
+    }
+}
+
+template <uint32_t N1>
+static cudaError_t launch_fwd_ct(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
+                                 uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status,
+                                 cudaStream_t s) {
+    const size_t smem = (size_t)N1 * 32 * sizeof(uint32_t);
+    dim3 grid(kPrimes * (pd.N2 / 32), y ? 2 : 1);
+    k_col_fwd_ct<N1><<<grid, pd.col_threads, smem, s>>>(pd, x, nx, y, ny, X, Y, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_col_fwd_ct(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
+                              uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status,
+                              cudaStream_t s) {
+    switch (pd.N1) {
+        case 512: return launch_fwd_ct<512>(pd, x, nx, y, ny, X, Y, status, s);
+        case 768: return launch_fwd_ct<768>(pd, x, nx, y, ny, X, Y, status, s);
+        case 1024: return launch_fwd_ct<1024>(pd, x, nx, y, ny, X, Y, status, s);
+        default: return launch_fwd_ct<1536>(pd, x, nx, y, ny, X, Y, status, s);
+    }
+}
+
+template <uint32_t N1, int MODE>
+static cudaError_t launch_inv_ct_mode(const PlanDev &pd, const uint32_t *X, uint64_t L,
+                                      uint32_t *out, uint2 *spill, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kPrimes * (pd.N2 / 32), 1, 1);
+    cfg.blockDim = dim3(pd.col_threads, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)N1 * 32 * sizeof(uint32_t);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kPrimes;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_col_inv_ct<N1, MODE>, pd, X, L, out, spill);
+}
+
+template <uint32_t N1>
+static cudaError_t launch_inv_ct(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
+                                 uint32_t *out, uint2 *spill, cudaStream_t s) {
+    if (mode == kInvTriples) return launch_inv_ct_mode<N1, kInvTriples>(pd, X, L, out, spill, s);
+    if (mode == kInvResidues) return launch_inv_ct_mode<N1, kInvResidues>(pd, X, L, out, spill, s);
+    return launch_inv_ct_mode<N1, kInvDigits>(pd, X, L, out, spill, s);
+}
+
+cudaError_t launch_col_inv_ct(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
+                              uint32_t *out, uint2 *spill, cudaStream_t s) {
+    switch (pd.N1) {
+        case 512: return launch_inv_ct<512>(pd, X, L, mode, out, spill, s);
+        case 768: return launch_inv_ct<768>(pd, X, L, mode, out, spill, s);
+        case 1024: return launch_inv_ct<1024>(pd, X, L, mode, out, spill, s);
+        default: return launch_inv_ct<1536>(pd, X, L, mode, out, spill, s);
+    }
+}
+
+template <uint32_t N1>
+static cudaError_t attrs_col_ct() {
+    cudaError_t e;
+    const int smem = (int)(N1 * 32 * 4);
+    if ((e = cudaFuncSetAttribute(k_col_fwd_ct<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_col_inv_ct<N1, kInvTriples>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_col_inv_ct<N1, kInvResidues>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+        return e;
+    return cudaFuncSetAttribute(k_col_inv_ct<N1, kInvDigits>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem);
+}
+
+cudaError_t init_kernel_attributes_colpass() {
+    cudaError_t e;
+    if ((e = attrs_col_ct<512>())) return e;
+    if ((e = attrs_col_ct<768>())) return e;
+    if ((e = attrs_col_ct<1024>())) return e;
+    return attrs_col_ct<1536>();
+}
+
+}  // namespace dml

@@ -65,6 +65,18 @@ cudaError_t launch_row_pass_ct(const PlanDev &pd, uint32_t *X, const uint32_t *Y
 cudaError_t init_kernel_attributes_rowpass();
 cudaError_t upload_constants_rowpass(const PrimeConst pc[kPrimes], const CrtConst &crt);
 
+// Specialized column passes for N1 in {512, 768, 1024, 1536} with the planner's schedule
+// (colpass.cu); launch_col_fwd / launch_col_inv dispatch to them when the schedule matches (and,
+// forward, when both operands are 16-byte aligned).
+bool col_pass_specialized(const PlanDev &pd);
+cudaError_t launch_col_fwd_ct(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
+                              uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status,
+                              cudaStream_t s);
+cudaError_t launch_col_inv_ct(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
+                              uint32_t *out, uint2 *spill, cudaStream_t s);
+cudaError_t init_kernel_attributes_colpass();
+cudaError_t upload_constants_colpass(const PrimeConst pc[kPrimes], const CrtConst &crt);
+
 // The row pass the plan asks for: specialized when available, else the generic plain or TMA form.
 cudaError_t launch_row_any(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
                            uint32_t *status, cudaStream_t s);

@@ -694,18 +694,18 @@ constexpr uint32_t kSpinLimit = 1u << 22;  // bounded lookahead wait
 
 
 // Inverse column pass of one tile (cluster of three CTAs, rank = prime) + CRT epilogue.
-__device__ __forceinline__ void col_inv_crt(const PlanDev &pd, const uint32_t *__restrict__ X,
-                                            uint64_t L, int mode, uint32_t *__restrict__ out,
-                                            uint2 *__restrict__ spill, uint32_t *sm) {
+// After the inverse column pass of a tile (cluster of three CTAs, rank = prime, residues of the
+// tile in [0, p) in each CTA's shared memory): write residues, or CRT each coefficient through
+// distributed shared memory and write its digits.
+__device__ __forceinline__ void col_crt_epilogue(const PlanDev &pd, uint64_t L, int mode,
+                                                 uint32_t *__restrict__ out, uint2 *__restrict__ spill,
+                                                 uint32_t *sm) {
     namespace cg = cooperative_groups;
     cg::cluster_group cluster = cg::this_cluster();
     const int pi = (int)cluster.block_rank();
-    const uint32_t tile = blockIdx.x / kPrimes;
-    const uint32_t j0 = tile * 32;
+    const uint32_t j0 = (blockIdx.x / kPrimes) * 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t n2 = j0 + lane;
-    const uint32_t *src = X + (uint64_t)pi * pd.N;
-    DMUL_PRIME_SWITCH(pi, (col_inv_body<PI>(pd, src, sm, n2)));
     if (mode == kInvResidues) {
         for (uint32_t r = warp; r < pd.N1; r += nw) {
             uint64_t k = (uint64_t)r * pd.N2 + n2;
@@ -734,6 +734,18 @@ __device__ __forceinline__ void col_inv_crt(const PlanDev &pd, const uint32_t *_
         }
     }
     cluster.sync();
+}
+
+// Inverse column pass of one tile (cluster of three CTAs, rank = prime) + CRT epilogue.
+__device__ __forceinline__ void col_inv_crt(const PlanDev &pd, const uint32_t *__restrict__ X,
+                                            uint64_t L, int mode, uint32_t *__restrict__ out,
+                                            uint2 *__restrict__ spill, uint32_t *sm) {
+    namespace cg = cooperative_groups;
+    const int pi = (int)cg::this_cluster().block_rank();
+    const uint32_t n2 = (blockIdx.x / kPrimes) * 32 + (threadIdx.x & 31);
+    const uint32_t *src = X + (uint64_t)pi * pd.N;
+    DMUL_PRIME_SWITCH(pi, (col_inv_body<PI>(pd, src, sm, n2)));
+    col_crt_epilogue(pd, L, mode, out, spill, sm);
 }
 
 // One 2048-limb tile of the decoupled-lookahead carry scan (256 threads).

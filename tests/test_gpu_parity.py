@@ -314,3 +314,44 @@ def test_c1_workload(d, ctx):
     z, nz = _gpu_mul(d, ctx, x, y)
     ref = oracle.mul_schoolbook(x, y)
     assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))
+
+
+# ---- compile-time specialized column passes (N1 in {512, 768, 1024, 1536}) --------------------
+@pytest.fixture(scope="module")
+def ctx_def(d):
+    """Four-step path with the planner's default split and the one-CTA-per-row pass."""
+    c = d.Context(0, flags=d.DMUL_FLAG_NO_SMALL | d.DMUL_FLAG_NO_AUTOTUNE)
+    yield c
+    c.close()
+
+
+# (n, m) whose transform length gets the default split N1 x N2 with the given N1
+SPECIALIZED_COLS = [((150001, 150000), 768, 512),     # N = 3 * 2^17
+                    ((262143, 200000), 512, 1024),    # N = 2^19
+                    ((300000, 299999), 1536, 512),    # N = 3 * 2^18
+                    ((524287, 400003), 1024, 1024)]   # N = 2^20
+
+
+@pytest.mark.parametrize("shape,n1,n2", SPECIALIZED_COLS)
+def test_specialized_column_pass(d, ctx_def, shape, n1, n2):
+    n, m = shape
+    info = d.dmul_get_plan(ctx_def.handle, n + m)
+    assert (info.N1, info.N2) == (n1, n2)
+    rng = _rng(11000 + n1)
+    x, y = _rand(rng, n), _rand(rng, m)
+    for square in (False, True):
+        z, nz = _gpu_mul(d, ctx_def, x, x if square else y, square=square)
+        ref = oracle.mul(x, x) if square else oracle.mul(x, y)
+        assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))
+    # the inverse pass's other epilogues: residues and exact coefficients at sampled positions
+    L = n + m
+    ks = [0, 1, 31, 32, n - 1, n, m, L // 2, L - 3, L - 2, L - 1] + list(rng.integers(0, L - 1, 24))
+    tx, ty = d.to_device(x), d.to_device(y)
+    r = d.to_host(ctx_def.conv_residues(tx, ty)).reshape(3, L).astype(np.uint64)
+    dg = d.to_host(ctx_def.conv_coeffs(tx, ty)).reshape(-1, 3).astype(object)
+    primes = d.dmul_primes()
+    for k in ks:
+        k = int(k)
+        c = oracle.conv_at(x, y, k)
+        assert dg[k, 0] + dg[k, 1] * B + dg[k, 2] * B * B == c, k
+        assert [int(r[i, k]) for i in range(3)] == [c % p for p in primes], k

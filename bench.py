@@ -275,6 +275,7 @@ def run_ours(args, rank, world, local):
                    "N": int(info.N), "split": [int(info.N1), int(info.N2)], "primes": 3,
                    "col_radix": [r for r in info.col_radix if r], "row_radix": [r for r in info.row_radix if r],
                    "col_threads": int(info.col_threads), "row_threads": int(info.row_threads),
+                   "col_tile": [int(info.N1), 16 if info.col_half else 32],
                    "row_pass": (f"persistent TMA-fed, {int(info.row_grid)} CTAs/prime" if info.row_tma
                                 else "one CTA per row"),
                    "l2": f"flushed between timed steps ({args.flush_mb} MiB write)", "parallelism": "replicas"},

@@ -59,6 +59,8 @@ typedef struct dmul_ctx dmul_ctx;
                                   /* (transform length <= 24576); they take the four-step path    */
 #define DMUL_FLAG_NO_AUTOTUNE 8u  /* plan every length with the default split instead of timing   */
                                   /* the candidate splits and CTA sizes on first use              */
+#define DMUL_FLAG_COL_HALF 32u   /* with DMUL_FLAG_NO_AUTOTUNE: run the column passes on N1 x 16 */
+                                  /* half tiles (N1 in {512, 768, 1024, 1536}) instead of N1 x 32 */
 #define DMUL_FLAG_ROW_TMA 16u     /* with DMUL_FLAG_NO_AUTOTUNE: use the persistent row pass fed  */
                                   /* by bulk asynchronous copies (TMA) instead of one CTA per row */
 
@@ -201,6 +203,7 @@ typedef struct {
     uint32_t row_threads; /* CTA size of the row pass                                       */
     uint32_t row_tma;     /* 1: persistent row pass fed by bulk async copies (TMA)          */
     uint32_t row_grid;    /* its CTAs per prime                                             */
+    uint32_t col_half;    /* 1: column passes on N1 x 16 half tiles (two or more CTAs per SM) */
 } dmul_plan_info;
 
 /* Plan the transform for a product of L limbs (L >= 2).  ctx may be NULL (default plan); with a

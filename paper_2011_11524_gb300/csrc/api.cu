@@ -142,15 +142,23 @@ static int autotune_plan(dmul_ctx *c, uint64_t N, std::unique_ptr<PlanEntry> *be
         rc = build_plan_entry(c, hp, &cand);
         if (rc) break;
         float cand_ms = 1e30f;
-        uint32_t cand_ct = 0, cand_rt = 0, cand_tma = 0, cand_grid = 0;
+        uint32_t cand_ct = 0, cand_rt = 0, cand_tma = 0, cand_grid = 0, cand_half = 0;
+        // column-pass variants: full-width tiles (256 or 512 threads) or half tiles (128 or 256)
+        std::vector<std::pair<uint32_t, uint32_t>> colv = {{0u, 256u}, {0u, 512u}};
+        if (col_half_supported(hp)) {
+            colv.push_back({1u, 128u});
+            colv.push_back({1u, 256u});
+        }
         // row-pass variants: plain (one CTA per row) or persistent TMA-fed with G CTAs per prime
         std::vector<std::pair<uint32_t, uint32_t>> rowv = {{0u, 0u}};
         if (6ull * (N / n1) * 4 + 16 <= 227ull * 1024)
             for (uint32_t G : {sms / 3, 2 * sms / 3, sms})
                 if (G >= 1 && G <= n1) rowv.push_back({1u, G});
-        for (uint32_t ct : {256u, 512u}) {
+        for (auto cv : colv) {
+            const uint32_t ct = cv.second;
             for (uint32_t rt : {128u, 256u}) {
                 for (auto rv : rowv) {
+                    cand->pd.col_half = cv.first;
                     cand->pd.col_threads = ct;
                     cand->pd.row_threads = rt;
                     cand->pd.row_tma = rv.first;
@@ -174,6 +182,7 @@ static int autotune_plan(dmul_ctx *c, uint64_t N, std::unique_ptr<PlanEntry> *be
                         cand_rt = rt;
                         cand_tma = rv.first;
                         cand_grid = rv.second;
+                        cand_half = cv.first;
                     }
                 }
             }
@@ -184,6 +193,7 @@ static int autotune_plan(dmul_ctx *c, uint64_t N, std::unique_ptr<PlanEntry> *be
             cand->hp.row_threads = cand_rt;
             cand->hp.row_tma = cand_tma;
             cand->hp.row_grid = cand_grid;
+            cand->hp.col_half = cand_half;
             if (*best) dev_free(c, (*best)->dtables, (*best)->bytes);
             *best = std::move(cand);
         } else {
@@ -203,7 +213,27 @@ static int autotune_plan(dmul_ctx *c, uint64_t N, std::unique_ptr<PlanEntry> *be
     (*best)->pd.row_threads = (*best)->hp.row_threads;
     (*best)->pd.row_tma = (*best)->hp.row_tma;
     (*best)->pd.row_grid = (*best)->hp.row_grid;
+    (*best)->pd.col_half = (*best)->hp.col_half;
     return DMUL_OK;
+}
+
+// The plan a context uses without autotuning: the default split, with the row / column pass
+// variants its flags force (DMUL_FLAG_ROW_TMA, DMUL_FLAG_COL_HALF).
+static bool fixed_host_plan(const dmul_ctx *c, uint64_t N, HostPlan *hp) {
+    const bool six = (c->cfg.flags & DMUL_FLAG_SIXSTEP) != 0;
+    if (!(six ? make_host_plan_sixstep(N, hp) : make_host_plan(N, hp))) return false;
+    if (six) return true;
+    if ((c->cfg.flags & DMUL_FLAG_ROW_TMA) && 6ull * hp->N2 * 4 + 16 <= 227ull * 1024) {
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        hp->row_tma = 1;
+        hp->row_grid = std::max<uint32_t>(1, std::min<uint32_t>(hp->N1, (uint32_t)sms / 3));
+    }
+    if ((c->cfg.flags & DMUL_FLAG_COL_HALF) && col_half_supported(*hp)) {
+        hp->col_half = 1;
+        hp->col_threads = 256;
+    }
+    return true;
 }
 
 int get_plan(dmul_ctx *c, uint64_t N, PlanEntry **out) {
@@ -217,13 +247,7 @@ int get_plan(dmul_ctx *c, uint64_t N, PlanEntry **out) {
     int rc;
     if (six || (c->cfg.flags & DMUL_FLAG_NO_AUTOTUNE)) {
         HostPlan hp;
-        if (!(six ? make_host_plan_sixstep(N, &hp) : make_host_plan(N, &hp))) return DMUL_ERR_TOO_LARGE;
-        if (!six && (c->cfg.flags & DMUL_FLAG_ROW_TMA) && 6ull * hp.N2 * 4 + 16 <= 227ull * 1024) {
-            int sms = 152;
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-            hp.row_tma = 1;
-            hp.row_grid = std::max<uint32_t>(1, std::min<uint32_t>(hp.N1, (uint32_t)sms / 3));
-        }
+        if (!fixed_host_plan(c, N, &hp)) return DMUL_ERR_TOO_LARGE;
         rc = build_plan_entry(c, hp, &pe);
     } else {
         rc = autotune_plan(c, N, &pe);
@@ -548,6 +572,7 @@ int dmul_get_plan(const dmul_ctx *ctx, uint64_t L, dmul_plan_info *out) {
     if (ctx) {
         auto it = ctx->plans.find(N);
         if (it != ctx->plans.end()) hp = it->second->hp;  // the split the autotuner chose
+        else if (six || (ctx->cfg.flags & DMUL_FLAG_NO_AUTOTUNE)) fixed_host_plan(ctx, N, &hp);
     }
     memset(out, 0, sizeof(*out));
     for (int i = 0; i < kPrimes; ++i) out->primes[i] = kPrimeSet[i];
@@ -561,6 +586,7 @@ int dmul_get_plan(const dmul_ctx *ctx, uint64_t L, dmul_plan_info *out) {
     out->row_threads = hp.row_threads ? hp.row_threads : 256;
     out->row_tma = hp.row_tma;
     out->row_grid = hp.row_grid;
+    out->col_half = hp.col_half;
     return DMUL_OK;
 }
 
@@ -597,6 +623,7 @@ int dmul_init(dmul_ctx **out, const dmul_config *cfg) {
     CK(init_kernel_attributes_batch());
     CK(init_kernel_attributes_rowpass());
     CK(init_kernel_attributes_colpass());
+    CK(init_kernel_attributes_colhalf());
     int rc = dev_alloc(c.get(), (void **)&c->status, 256);
     if (rc) return rc;
     CK(cudaMemset(c->status, 0, 256));

@@ -345,3 +345,377 @@ cudaError_t init_kernel_attributes_colpass() {
 }
 
 }  // namespace dml
+
+// =============================================================================================
+// Half-width tiles: N1 rows x 16 columns (64 KB at N1 = 1024), so that two or three CTAs share an
+// SM and one CTA's tile load overlaps another's arithmetic.  A warp works on two groups at once,
+// one per half-warp (lane = 16 h + c, c = column).  Row r of the tile sits at slot
+// phys(r) = r ^ ((r >> 4) & 1) (16 words per slot): the two half-warps then always touch slots of
+// different parity -- rows j, j + 1 (j even) in the strided stages, rows 16 b + u, 16 (b + 1) + u
+// in the last forward / first inverse stage -- i.e. different 16-bank halves.
+// =============================================================================================
+namespace dml {
+
+__device__ __forceinline__ uint32_t hphys(uint32_t r) { return r ^ ((r >> 4) & 1u); }
+
+// Stage the N1 x 16 tile at column j0 (16-byte aligned source; words >= n read as 0).
+__device__ __forceinline__ void htile_load_async(uint32_t *sm, const uint32_t *__restrict__ src,
+                                                 uint64_t n, uint32_t N1, uint32_t N2, uint32_t j0) {
+    const uint32_t chunks = N1 * 4;  // 16-byte chunks: 4 per 16-word row
+    for (uint32_t idx = threadIdx.x; idx < chunks; idx += blockDim.x) {
+        const uint32_t row = idx >> 2, q = idx & 3;
+        const uint64_t g = (uint64_t)row * N2 + j0 + 4 * q;
+        const uint32_t valid = g >= n ? 0u : (n - g >= 4 ? 4u : (uint32_t)(n - g));
+        const uint32_t *s = valid ? src + g : src;
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(sm + hphys(row) * 16 + 4 * q);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(s), "r"(valid * 4)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+}
+
+// Word offset of row (base + u * S) for a group whose first row is `base`, for the row strides
+// the schedules produce: S a multiple of 32 (phys is linear in u), S = 16 (base has bit 4 clear:
+// odd u flips bit 0 of the row), S = 1 with base = 16 b (odd b flips bit 0 of u).  odd_off is the
+// per-thread correction added for odd u (S = 16) or to every u (S = 1: see hoff1).
+template <uint32_t S>
+__device__ __forceinline__ uint32_t hbase(uint32_t base, uint32_t c) {
+    if constexpr (S % 32 == 0) return hphys(base) * 16 + c;
+    else return base * 16 + c;
+}
+template <uint32_t S>
+__device__ __forceinline__ int hodd(uint32_t base) {
+    if constexpr (S == 16) return (base & 1u) ? -16 : 16;  // row ^ 1
+    else if constexpr (S == 1) return ((base >> 4) & 1u) ? 16 : 0;  // u -> u ^ 1 when b is odd
+    else return 0;
+}
+template <uint32_t S, uint32_t U>
+__device__ __forceinline__ uint32_t hoff(uint32_t b0, int odd) {
+    static_assert(S % 32 == 0 || S == 16 || S == 1, "row stride without a half-tile layout");
+    if constexpr (S % 32 == 0) return b0 + U * S * 16;
+    else if constexpr (S == 16) return b0 + U * 256 + ((U & 1) ? odd : 0);
+    else return (U & 1) ? b0 + U * 16 - odd : b0 + U * 16 + odd;  // (u ^ (b & 1)) * 16, odd = 16 (b & 1)
+}
+
+template <int PI, uint32_t R, uint32_t S, uint32_t U = 0>
+__device__ __forceinline__ void hload(const uint32_t *sm, uint32_t b0, int odd, uint32_t (&v)[R]) {
+    if constexpr (U < R) {
+        v[U] = sm[hoff<S, U>(b0, odd)];
+        hload<PI, R, S, U + 1>(sm, b0, odd, v);
+    }
+}
+// store v[outpos(k)] to row k of the group
+template <int PI, uint32_t R, uint32_t S, uint32_t K = 0>
+__device__ __forceinline__ void hstore_out(uint32_t *sm, uint32_t b0, int odd, const uint32_t (&v)[R]) {
+    if constexpr (K < R) {
+        sm[hoff<S, K>(b0, odd)] = v[outpos<(int)R>((int)K)];
+        hstore_out<PI, R, S, K + 1>(sm, b0, odd, v);
+    }
+}
+
+// stage 0 of the forward pass (limbs in, in place)
+template <int PI, uint32_t R, uint32_t N1>
+__device__ __forceinline__ void hcolf0(const Stage &st, const uint2 *tw, uint32_t *sm, uint32_t &bad) {
+    constexpr uint32_t stride = N1 / R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t c = lane & 15, h = lane >> 4;
+    for (uint32_t j = 2 * warp + h; j < stride; j += 2 * nw) {
+        const uint32_t b0 = hbase<stride>(j, c);
+        const int odd = hodd<stride>(j);
+        uint32_t v[R];
+        hload<PI, R, stride>(sm, b0, odd, v);
+#pragma unroll
+        for (uint32_t u = 0; u < R; ++u) {
+            bad |= (v[u] >= kBase);
+            if (PI == 0) v[u] = red2p<PI>(v[u]);  // 10^9 < 4 p0: [0, 10^9) -> [0, 2 p0)
+        }
+        dft<PI, 0, (int)R>(v);
+#pragma unroll
+        for (uint32_t k = 1; k < R; ++k) {
+            const uint2 w = ldtw(tw + st.tw + (k - 1) * stride + j);
+            v[outpos<(int)R>((int)k)] = shoup<PI>(v[outpos<(int)R>((int)k)], w.x, w.y);
+        }
+        hstore_out<PI, R, stride>(sm, b0, odd, v);
+    }
+}
+
+// a middle stage (forward: DFT then twiddle; inverse: untwiddle then DFT), in place
+template <int PI, uint32_t R, uint32_t M, uint32_t N1, bool INV>
+__device__ __forceinline__ void hcolmid(const Stage &st, const uint2 *tw, uint32_t *sm, bool final_reduce) {
+    constexpr uint32_t stride = M / R;
+    constexpr uint32_t groups = N1 / R;
+    constexpr bool has_tw = M > R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t c = lane & 15, h = lane >> 4;
+    for (uint32_t g = 2 * warp + h; g < groups; g += 2 * nw) {
+        const uint32_t blk = g / stride, j = g % stride;
+        const uint32_t base = blk * M + j;
+        const uint32_t b0 = hbase<stride>(base, c);
+        const int odd = hodd<stride>(base);
+        uint32_t v[R];
+        hload<PI, R, stride>(sm, b0, odd, v);
+        if (!INV) {
+            dft<PI, 0, (int)R>(v);
+            if (has_tw) {
+#pragma unroll
+                for (uint32_t k = 1; k < R; ++k) {
+                    const uint2 w = ldtw(tw + st.tw + (k - 1) * stride + j);
+                    v[outpos<(int)R>((int)k)] = shoup<PI>(v[outpos<(int)R>((int)k)], w.x, w.y);
+                }
+            }
+        } else {
+            if (has_tw) {
+#pragma unroll
+                for (uint32_t k = 1; k < R; ++k) {
+                    const uint2 w = ldtw(tw + st.twi + (k - 1) * stride + j);
+                    v[k] = shoup<PI>(v[k], w.x, w.y);
+                }
+            }
+            dft<PI, 1, (int)R>(v);
+            if (final_reduce) {
+#pragma unroll
+                for (uint32_t u = 0; u < R; ++u) v[u] = red1p<PI>(v[u]);
+            }
+        }
+        hstore_out<PI, R, stride>(sm, b0, odd, v);
+    }
+}
+
+// last forward stage (rows 16 b + u, R = 16) + four-step twiddle + store of the residues
+template <int PI, uint32_t R, uint32_t N1>
+__device__ __forceinline__ void hcolf_last(const PlanDev &pd, const uint32_t *sm,
+                                           uint32_t *__restrict__ dst, uint32_t n2) {
+    static_assert(R == 16, "half tiles need a last stage of radix 16");
+    constexpr uint32_t nb = N1 / R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t c = lane & 15, h = lane >> 4;
+    const uint2 *A = pd.tw[PI] + pd.offA;
+    uint2 q[R];
+    load_q<PI, R>(pd.tw[PI] + pd.offQ, pd.N2, n2, q);
+    for (uint32_t b = 2 * warp + h; b < nb; b += 2 * nw) {
+        uint32_t v[R];
+        hload<PI, R, 1>(sm, hbase<1>(b * R, c), hodd<1>(b * R), v);
+        const uint2 a = ldtw(A + (uint64_t)b * pd.N2 + n2);
+        dft<PI, 0, (int)R>(v);
+#pragma unroll
+        for (uint32_t k = 0; k < R; ++k) {
+            uint32_t o = v[outpos<(int)R>((int)k)];
+            if (k > 0) o = shoup<PI>(o, q[k].x, q[k].y);
+            o = shoup<PI>(o, a.x, a.y);
+            dst[(uint64_t)(b * R + k) * pd.N2 + n2] = o;
+        }
+    }
+}
+
+// first inverse stage on the staged half tile: inverse four-step twiddle, inverse DFT
+template <int PI, uint32_t R, uint32_t N1>
+__device__ __forceinline__ void hcoli_first(const PlanDev &pd, uint32_t *sm, uint32_t n2) {
+    static_assert(R == 16, "half tiles need a last stage of radix 16");
+    constexpr uint32_t nb = N1 / R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t c = lane & 15, h = lane >> 4;
+    const uint2 *A = pd.tw[PI] + pd.offAi;
+    uint2 q[R];
+    load_q<PI, R>(pd.tw[PI] + pd.offQi, pd.N2, n2, q);
+    for (uint32_t b = 2 * warp + h; b < nb; b += 2 * nw) {
+        const uint32_t b0 = hbase<1>(b * R, c);
+        const int odd = hodd<1>(b * R);
+        uint32_t v[R];
+        hload<PI, R, 1>(sm, b0, odd, v);
+        const uint2 a = ldtw(A + (uint64_t)b * pd.N2 + n2);
+#pragma unroll
+        for (uint32_t k = 0; k < R; ++k) {
+            uint32_t o = v[k];
+            if (k > 0) o = shoup<PI>(o, q[k].x, q[k].y);
+            v[k] = shoup<PI>(o, a.x, a.y);
+        }
+        dft<PI, 1, (int)R>(v);
+        hstore_out<PI, R, 1>(sm, b0, odd, v);
+    }
+}
+
+template <int PI, uint32_t N1, int T>
+__device__ __forceinline__ void hcolf_mids(const PlanDev &pd, uint32_t *sm) {
+    using S = ColSched<N1>;
+    if constexpr (T < S::NS - 1) {
+        hcolmid<PI, S::radix(T), S::span(T), N1, false>(pd.cs[T], pd.tw[PI], sm, false);
+        __syncthreads();
+        hcolf_mids<PI, N1, T + 1>(pd, sm);
+    }
+}
+
+template <int PI, uint32_t N1, int T>
+__device__ __forceinline__ void hcoli_mids(const PlanDev &pd, uint32_t *sm) {
+    using S = ColSched<N1>;
+    if constexpr (T >= 0) {
+        hcolmid<PI, S::radix(T), S::span(T), N1, true>(pd.cs[T], pd.tw[PI], sm, T == 0);
+        __syncthreads();
+        hcoli_mids<PI, N1, T - 1>(pd, sm);
+    }
+}
+
+// grid (3 * N2/16, operands): blockIdx.x = 3 * half_tile + prime; x and y 16-byte aligned
+template <uint32_t N1>
+__global__ void __launch_bounds__(256, 2) k_col_fwd_h(const PlanDev pd, const uint32_t *__restrict__ x,
+                                                      uint64_t nx, const uint32_t *__restrict__ y,
+                                                      uint64_t ny, uint32_t *X, uint32_t *Y,
+                                                      uint32_t *status) {
+    using S = ColSched<N1>;
+    extern __shared__ __align__(16) uint32_t sm[];
+    const int pi = blockIdx.x % kPrimes;
+    const uint32_t j0 = (blockIdx.x / kPrimes) * 16;
+    const bool second = blockIdx.y != 0;
+    const uint32_t *src = second ? y : x;
+    const uint64_t n = second ? ny : nx;
+    uint32_t *dst = (second ? Y : X) + (uint64_t)pi * pd.N;
+    const uint32_t n2 = j0 + (threadIdx.x & 15);
+    uint32_t bad = 0;
+    htile_load_async(sm, src, n, N1, pd.N2, j0);
+    DMUL_PRIME_SWITCH(pi, (hcolf0<PI, S::radix(0), N1>(pd.cs[0], pd.tw[PI], sm, bad)));
+    if (pi == 0 && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusInvalid);
+    __syncthreads();
+    DMUL_PRIME_SWITCH(pi, (hcolf_mids<PI, N1, 1>(pd, sm)));
+    DMUL_PRIME_SWITCH(pi, (hcolf_last<PI, S::radix(S::NS - 1), N1>(pd, sm, dst, n2)));
+}
+
+template <int PI, uint32_t N1>
+__device__ __forceinline__ void hcol_inv_body(const PlanDev &pd, const uint32_t *__restrict__ src,
+                                              uint32_t *sm, uint32_t j0) {
+    using S = ColSched<N1>;
+    htile_load_async(sm, src, pd.N, N1, pd.N2, j0);
+    hcoli_first<PI, S::radix(S::NS - 1), N1>(pd, sm, j0 + (threadIdx.x & 15));
+    __syncthreads();
+    hcoli_mids<PI, N1, S::NS - 2>(pd, sm);
+}
+
+// Cluster of six CTAs per 32-column tile: rank = 3 * half + prime, half 0 / 1 holding columns
+// [0, 16) / [16, 32) of the tile.  After the inverse column DFTs, each 32-coefficient chunk of a
+// row is recovered by CRT from the six CTAs' shared memory (lanes 0-15 read the CTAs of half 0,
+// lanes 16-31 those of half 1), so the chunk digit sums and spills are those of the full-width
+// pass.
+template <uint32_t N1, int MODE>
+__global__ void __launch_bounds__(256, 2) k_col_inv_h(const PlanDev pd, const uint32_t *__restrict__ X,
+                                                      uint64_t L, uint32_t *__restrict__ out,
+                                                      uint2 *__restrict__ spill) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const uint32_t rank = cluster.block_rank();
+    const uint32_t half = rank / kPrimes, pi = rank % kPrimes;
+    const uint32_t t0 = (blockIdx.x / (2 * kPrimes)) * 32;  // first column of the 32-column tile
+    const uint32_t j0 = t0 + 16 * half;
+    const uint32_t *src = X + (uint64_t)pi * pd.N;
+    DMUL_PRIME_SWITCH((int)pi, (hcol_inv_body<PI, N1>(pd, src, sm, j0)));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t c = lane & 15, hl = lane >> 4;
+    if (MODE == kInvResidues) {
+        for (uint32_t r = 2 * warp + hl; r < N1; r += 2 * nw) {
+            const uint64_t k = (uint64_t)r * pd.N2 + j0 + c;
+            if (k < L) out[(uint64_t)pi * L + k] = sm[hphys(r) * 16 + c];
+        }
+        return;
+    }
+    cluster.sync();
+    const uint32_t *s0 = cluster.map_shared_rank(sm, kPrimes * hl + 0);
+    const uint32_t *s1 = cluster.map_shared_rank(sm, kPrimes * hl + 1);
+    const uint32_t *s2 = cluster.map_shared_rank(sm, kPrimes * hl + 2);
+    for (uint32_t r = rank + 2 * kPrimes * warp; r < N1; r += 2 * kPrimes * nw) {
+        const uint64_t k0 = (uint64_t)r * pd.N2 + t0;  // first coefficient of this chunk
+        if (k0 >= L) continue;                          // warp-uniform
+        const uint32_t off = hphys(r) * 16 + c;
+        uint32_t d0, d1, d2;
+        crt_digits(s0[off], s1[off], s2[off], d0, d1, d2);
+        const uint64_t k = k0 + lane;
+        if (MODE == kInvTriples) {
+            if (k < L) { out[3 * k] = d0; out[3 * k + 1] = d1; out[3 * k + 2] = d2; }
+        } else {
+            uint32_t sv;
+            uint2 sp;
+            chunk_digits(d0, d1, d2, sv, sp);
+            if (k < L) out[k] = sv;
+            if (lane == 31) spill[k0 >> 5] = sp;
+        }
+    }
+    cluster.sync();
+}
+
+template <uint32_t N1>
+static cudaError_t launch_fwd_h(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
+                                uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status, cudaStream_t s) {
+    const size_t smem = (size_t)N1 * 16 * sizeof(uint32_t);
+    dim3 grid(kPrimes * (pd.N2 / 16), y ? 2 : 1);
+    k_col_fwd_h<N1><<<grid, pd.col_threads, smem, s>>>(pd, x, nx, y, ny, X, Y, status);
+    return cudaGetLastError();
+}
+
+template <uint32_t N1, int MODE>
+static cudaError_t launch_inv_h_mode(const PlanDev &pd, const uint32_t *X, uint64_t L, uint32_t *out,
+                                     uint2 *spill, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * kPrimes * (pd.N2 / 32), 1, 1);
+    cfg.blockDim = dim3(pd.col_threads, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)N1 * 16 * sizeof(uint32_t);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2 * kPrimes;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_col_inv_h<N1, MODE>, pd, X, L, out, spill);
+}
+
+template <uint32_t N1>
+static cudaError_t launch_inv_h(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
+                                uint32_t *out, uint2 *spill, cudaStream_t s) {
+    if (mode == kInvTriples) return launch_inv_h_mode<N1, kInvTriples>(pd, X, L, out, spill, s);
+    if (mode == kInvResidues) return launch_inv_h_mode<N1, kInvResidues>(pd, X, L, out, spill, s);
+    return launch_inv_h_mode<N1, kInvDigits>(pd, X, L, out, spill, s);
+}
+
+cudaError_t launch_col_fwd_h(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
+                             uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status, cudaStream_t s) {
+    switch (pd.N1) {
+        case 512: return launch_fwd_h<512>(pd, x, nx, y, ny, X, Y, status, s);
+        case 768: return launch_fwd_h<768>(pd, x, nx, y, ny, X, Y, status, s);
+        case 1024: return launch_fwd_h<1024>(pd, x, nx, y, ny, X, Y, status, s);
+        default: return launch_fwd_h<1536>(pd, x, nx, y, ny, X, Y, status, s);
+    }
+}
+
+cudaError_t launch_col_inv_h(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
+                             uint32_t *out, uint2 *spill, cudaStream_t s) {
+    switch (pd.N1) {
+        case 512: return launch_inv_h<512>(pd, X, L, mode, out, spill, s);
+        case 768: return launch_inv_h<768>(pd, X, L, mode, out, spill, s);
+        case 1024: return launch_inv_h<1024>(pd, X, L, mode, out, spill, s);
+        default: return launch_inv_h<1536>(pd, X, L, mode, out, spill, s);
+    }
+}
+
+template <uint32_t N1>
+static cudaError_t attrs_col_h() {
+    cudaError_t e;
+    const int smem = (int)(N1 * 16 * 4);
+    if ((e = cudaFuncSetAttribute(k_col_fwd_h<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_col_inv_h<N1, kInvTriples>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_col_inv_h<N1, kInvResidues>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+        return e;
+    return cudaFuncSetAttribute(k_col_inv_h<N1, kInvDigits>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                smem);
+}
+
+cudaError_t init_kernel_attributes_colhalf() {
+    cudaError_t e;
+    if ((e = attrs_col_h<512>())) return e;
+    if ((e = attrs_col_h<768>())) return e;
+    if ((e = attrs_col_h<1024>())) return e;
+    return attrs_col_h<1536>();
+}
+
+}  // namespace dml

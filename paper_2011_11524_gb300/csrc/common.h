@@ -53,6 +53,7 @@ struct PlanDev {
     uint32_t col_threads, row_threads;  // CTA sizes of the column and row passes (autotuned)
     uint32_t row_tma;                   // 1: persistent TMA-fed row pass with row_grid CTAs/prime
     uint32_t row_grid;
+    uint32_t col_half;                  // 1: column passes on N1 x 16 half tiles (colpass.cu)
     uint64_t offA, offQ, offAi, offQi;  // four-step twiddle tables (uint2 offsets)
     const uint2 *tw[kPrimes];           // per-prime table buffers (device)
 };

@@ -75,6 +75,13 @@ cudaError_t launch_col_fwd_ct(const PlanDev &pd, const uint32_t *x, uint64_t nx,
 cudaError_t launch_col_inv_ct(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
                               uint32_t *out, uint2 *spill, cudaStream_t s);
 cudaError_t init_kernel_attributes_colpass();
+// The same passes on N1 x 16 half tiles (pd.col_half): forward grid (3 N2/16, operands); inverse
+// in clusters of six CTAs (three primes x two halves of a 32-column tile).  col_threads <= 256.
+cudaError_t launch_col_fwd_h(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
+                             uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status, cudaStream_t s);
+cudaError_t launch_col_inv_h(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
+                             uint32_t *out, uint2 *spill, cudaStream_t s);
+cudaError_t init_kernel_attributes_colhalf();
 cudaError_t upload_constants_colpass(const PrimeConst pc[kPrimes], const CrtConst &crt);
 
 // The row pass the plan asks for: specialized when available, else the generic plain or TMA form.

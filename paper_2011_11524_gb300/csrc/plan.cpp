@@ -252,6 +252,12 @@ bool make_host_plan(uint64_t N, HostPlan *hp, uint32_t n1_override) {
     return (int)hp->col_radix.size() <= kMaxStages && (int)hp->row_radix.size() <= kMaxStages;
 }
 
+bool col_half_supported(const HostPlan &hp) {
+    const uint32_t n1 = hp.N1;
+    return (n1 == 512 || n1 == 768 || n1 == 1024 || n1 == 1536) && hp.N2 % 32 == 0 &&
+           !hp.col_radix.empty() && hp.col_radix.back() == 16;
+}
+
 std::vector<uint32_t> candidate_n1(uint64_t N) {
     std::vector<uint32_t> out;
     for (uint32_t n1 = 2; n1 <= kMaxN1; n1 *= 2) {
@@ -364,6 +370,7 @@ void build_tables(const HostPlan &hp, PlanDev *pd, std::vector<uint32_t> tables[
     pd->row_threads = hp.row_threads ? hp.row_threads : 256;
     pd->row_tma = hp.row_tma;
     pd->row_grid = hp.row_grid;
+    pd->col_half = hp.col_half;
     const uint64_t N = hp.N;
     const uint32_t N1 = hp.N1, N2 = hp.N2;
     const int s = (int)hp.col_radix.size();

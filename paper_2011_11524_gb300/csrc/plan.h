@@ -40,7 +40,11 @@ struct HostPlan {
     std::vector<uint32_t> col_radix, row_radix;
     uint32_t col_threads = 0, row_threads = 0;  // 0: the default for the split
     uint32_t row_tma = 0, row_grid = 0;         // persistent TMA-fed row pass and its CTAs/prime
+    uint32_t col_half = 0;                      // column passes on N1 x 16 half tiles
 };
+// The column passes can run on N1 x 16 half tiles: N1 one of the specialized lengths with its
+// planned schedule (last stage radix 16) and whole 32-column tiles for the six-CTA CRT clusters.
+bool col_half_supported(const HostPlan &hp);
 // Candidate column lengths N1 for a transform length N (the autotuner's search space).
 std::vector<uint32_t> candidate_n1(uint64_t N);
 bool make_host_plan(uint64_t N, HostPlan *hp, uint32_t n1_override = 0);

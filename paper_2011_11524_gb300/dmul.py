@@ -29,6 +29,7 @@ DMUL_FLAG_STAGE_TIMING = 2
 DMUL_FLAG_NO_SMALL = 4
 DMUL_FLAG_NO_AUTOTUNE = 8
 DMUL_FLAG_ROW_TMA = 16
+DMUL_FLAG_COL_HALF = 32
 
 # every symbol include/dmul.h declares
 EXPORTS = [
@@ -62,7 +63,8 @@ class dmul_plan_info(ctypes.Structure):
                 ("N2", ctypes.c_uint32), ("col_radix", ctypes.c_uint32 * 8),
                 ("row_radix", ctypes.c_uint32 * 8), ("sixstep", ctypes.c_uint32),
                 ("col_threads", ctypes.c_uint32), ("row_threads", ctypes.c_uint32),
-                ("row_tma", ctypes.c_uint32), ("row_grid", ctypes.c_uint32)]
+                ("row_tma", ctypes.c_uint32), ("row_grid", ctypes.c_uint32),
+                ("col_half", ctypes.c_uint32)]
 
 
 _lib = None

@@ -332,11 +332,21 @@ SPECIALIZED_COLS = [((150001, 150000), 768, 512),     # N = 3 * 2^17
                     ((524287, 400003), 1024, 1024)]   # N = 2^20
 
 
+@pytest.fixture(scope="module")
+def ctx_half(d):
+    """As ctx_def, with the column passes on N1 x 16 half tiles (six-CTA CRT clusters)."""
+    c = d.Context(0, flags=d.DMUL_FLAG_NO_SMALL | d.DMUL_FLAG_NO_AUTOTUNE | d.DMUL_FLAG_COL_HALF)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("half", [False, True], ids=["full_tiles", "half_tiles"])
 @pytest.mark.parametrize("shape,n1,n2", SPECIALIZED_COLS)
-def test_specialized_column_pass(d, ctx_def, shape, n1, n2):
+def test_specialized_column_pass(d, request, half, shape, n1, n2):
+    ctx_def = request.getfixturevalue("ctx_half" if half else "ctx_def")
     n, m = shape
     info = d.dmul_get_plan(ctx_def.handle, n + m)
-    assert (info.N1, info.N2) == (n1, n2)
+    assert (info.N1, info.N2, info.col_half) == (n1, n2, int(half))
     rng = _rng(11000 + n1)
     x, y = _rand(rng, n), _rand(rng, m)
     for square in (False, True):

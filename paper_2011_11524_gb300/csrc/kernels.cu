@@ -144,16 +144,26 @@ cudaError_t launch_triples_to_digits(const uint32_t *d, uint64_t L, uint32_t *ou
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) k_carry(uint32_t *__restrict__ z, const uint2 *__restrict__ spill,
-                                               uint64_t L, CarryCtl *ctl, uint64_t *nz,
-                                               uint32_t *status, uint32_t ntiles) {
-    carry_tile(z, spill, L, ctl, nz, status, ntiles);
+template <int NT, int PER>
+__global__ void __launch_bounds__(NT) k_carry(uint32_t *__restrict__ z, const uint2 *__restrict__ spill,
+                                              uint64_t L, CarryCtl *ctl, uint64_t *nz, uint32_t *status,
+                                              uint32_t ntiles) {
+    carry_tile<NT, PER>(z, spill, L, ctl, nz, status, ntiles);
 }
 
+// Long products take 8192-limb tiles (512 threads x 16), so that every tile of a product of a few
+// million limbs is resident at once and the look-back chain is short; shorter ones 2048-limb tiles
+// (256 x 8) for parallelism.  ctl holds flags for ceil(L / kCarryLimbs) tiles, enough for either.
 cudaError_t launch_carry(uint32_t *z, const uint2 *spill, uint64_t L, CarryCtl *ctl, uint64_t *nz,
                          uint32_t *status, cudaStream_t s) {
-    const uint64_t ntiles = (L + kCarryLimbs - 1) / kCarryLimbs;
-    k_carry<<<(unsigned)ntiles, 256, 0, s>>>(z, spill, L, ctl, nz, status, (uint32_t)ntiles);
+    constexpr uint64_t kBig = 512 * 16;
+    if (L >= 256 * kBig) {
+        const uint64_t ntiles = (L + kBig - 1) / kBig;
+        k_carry<512, 16><<<(unsigned)ntiles, 512, 0, s>>>(z, spill, L, ctl, nz, status, (uint32_t)ntiles);
+    } else {
+        const uint64_t ntiles = (L + kCarryLimbs - 1) / kCarryLimbs;
+        k_carry<256, 8><<<(unsigned)ntiles, 256, 0, s>>>(z, spill, L, ctl, nz, status, (uint32_t)ntiles);
+    }
     return cudaGetLastError();
 }
 

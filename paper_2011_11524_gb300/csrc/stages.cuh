@@ -748,7 +748,7 @@ __device__ __forceinline__ void col_inv_crt(const PlanDev &pd, const uint32_t *_
     col_crt_epilogue(pd, L, mode, out, spill, sm);
 }
 
-// One 2048-limb tile of the decoupled-lookahead carry scan (256 threads).
+// One tile (NT threads x PER limbs) of the decoupled-lookahead carry scan.
 //
 // A tile publishes its aggregate carry map (status 1) and, once it knows its carry-in, its
 // carry-out (status 2).  A tile whose map is constant -- its carry-out does not depend on its
@@ -756,34 +756,41 @@ __device__ __forceinline__ void col_inv_crt(const PlanDev &pd, const uint32_t *_
 // once, so successors rarely wait.  The look-back runs on a whole warp: 32 predecessors per round,
 // the maps before the nearest finished predecessor composed by a warp reduction.  Every wait is
 // bounded; on expiry the tile records a timeout and proceeds with carry 0.
+template <int NT, int PER>
 __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2 *__restrict__ spill,
                                            uint64_t L, CarryCtl *ctl, uint64_t *nz,
                                            uint32_t *status, uint32_t ntiles) {
-    __shared__ uint32_t s_tile, s_cin, s_warp[8];
-    __shared__ uint64_t s_top[8];
+    // every 32-limb chunk start (where a spill lands) is the first limb of some thread
+    static_assert(NT % 32 == 0 && NT <= 1024 && PER % 4 == 0 && 32 % PER == 0, "tile shape");
+    constexpr int NW = NT / 32;
+    __shared__ uint32_t s_tile, s_cin, s_warp[NW];
+    __shared__ uint64_t s_top[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(&ctl->ticket, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
-    const uint64_t base = (uint64_t)tile * kCarryLimbs + (uint64_t)tid * 8;
-    const bool vec = ((((uintptr_t)z) & 15) == 0) && (base + 8 <= L);
-    uint32_t v[8];
+    const uint64_t base = (uint64_t)tile * (NT * PER) + (uint64_t)tid * PER;
+    const bool vec = ((((uintptr_t)z) & 15) == 0) && (base + PER <= L);
+    uint32_t v[PER];
     if (vec) {
-        const uint4 a = *(const uint4 *)(z + base), b = *(const uint4 *)(z + base + 4);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+#pragma unroll
+        for (int i = 0; i < PER; i += 4) {
+            const uint4 a = *(const uint4 *)(z + base + i);
+            v[i] = a.x; v[i + 1] = a.y; v[i + 2] = a.z; v[i + 3] = a.w;
+        }
     } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = (base + i < L) ? z[base + i] : 0u;
+        for (int i = 0; i < PER; ++i) v[i] = (base + i < L) ? z[base + i] : 0u;
     }
     if ((base & 31) == 0 && base > 0 && base < L) {
         uint2 sp = spill[(base >> 5) - 1];
         v[0] += sp.x;
         v[1] += sp.y;
     }
-    // map of this thread's 8 positions
+    // map of this thread's PER positions
     uint32_t c0 = 0, c1 = 1, c2 = 2;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < PER; ++i) {
         c0 = qdig(v[i] + c0);
         c1 = qdig(v[i] + c1);
         c2 = qdig(v[i] + c2);
@@ -803,7 +810,7 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
     if (warp == 0) {
         uint32_t agg = kIdentityMap;
         if (lane == 0) {
-            for (int w = 0; w < 8; ++w) {
+            for (int w = 0; w < NW; ++w) {
                 uint32_t wf = s_warp[w];
                 s_warp[w] = agg;  // exclusive prefix of warp w
                 agg = map_compose(wf, agg);
@@ -862,9 +869,9 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
     __syncthreads();
     uint32_t c = map_apply(map_compose(exc, s_warp[warp]), s_cin);
     uint64_t top = 0;
-    uint32_t o[8];
+    uint32_t o[PER];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < PER; ++i) {
         uint32_t t = v[i] + c;
         uint32_t q = qdig(t);
         o[i] = t - q * kBase;
@@ -875,11 +882,11 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
         }
     }
     if (vec) {
-        *(uint4 *)(z + base) = make_uint4(o[0], o[1], o[2], o[3]);
-        *(uint4 *)(z + base + 4) = make_uint4(o[4], o[5], o[6], o[7]);
+#pragma unroll
+        for (int i = 0; i < PER; i += 4) *(uint4 *)(z + base + i) = make_uint4(o[i], o[i + 1], o[i + 2], o[i + 3]);
     } else {
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < PER; ++i)
             if (base + i < L) z[base + i] = o[i];
     }
     // highest nonzero limb
@@ -892,7 +899,7 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
     __syncthreads();
     if (tid == 0) {
         uint64_t t = 0;
-        for (int w = 0; w < 8; ++w) t = s_top[w] > t ? s_top[w] : t;
+        for (int w = 0; w < NW; ++w) t = s_top[w] > t ? s_top[w] : t;
         if (t) atomicMax((unsigned long long *)&ctl->top, (unsigned long long)t);
         __threadfence();
         uint32_t prev = atomicAdd(&ctl->done, 1u);

@@ -228,6 +228,38 @@ def test_carry_adversarial(d, ctx, L):
         assert nz == len(oracle.normalize(ref))
 
 
+@pytest.mark.parametrize("L", [2_097_152, 2_200_001, 4_194_307])
+def test_carry_long(d, ctx, L):
+    """Products of millions of limbs take the large carry tiles (8192 limbs): a carry rippling
+    through every tile (no tile's map is constant, so each look-back composes its predecessors'
+    maps), runs of 10^9-1 across tile and chunk boundaries, and near-maximal coefficients."""
+    rng = _rng(6100 + L)
+    for kind in ("run", "runs", "max"):
+        if kind == "run":
+            c = np.full(L, B - 1, np.uint64)
+            c[0] = B
+            c[-1] = 0
+        elif kind == "runs":
+            c = rng.integers(0, 3 * B, size=L, dtype=np.uint64)
+            for start in list(range(8192 - 7, L - 40000, 8192 * 37)) + list(rng.integers(0, L - 40000, 64)):
+                ln = int(rng.integers(1, 30000))
+                c[int(start):int(start) + ln] = B - 1
+                c[int(start)] += int(rng.integers(0, 3))
+            c[-2:] = 0
+        else:
+            c = rng.integers(0, 2**62, size=L, dtype=np.uint64)
+            c[-1] = 0
+            c[-2] = int(rng.integers(0, B))
+            c[-3] = int(rng.integers(0, B * B // 2))
+        tri = np.stack([c % B, (c // B) % B, c // (B * B)], axis=1).astype(np.uint32)
+        z, nz = ctx.carry(d.to_device(tri.reshape(-1)), L)
+        words = np.stack([c, np.zeros(L, np.uint64)], axis=1)
+        ref, fin = oracle.carry(words)
+        assert fin == 0
+        assert np.array_equal(d.to_host(z), ref), kind
+        assert nz == len(oracle.normalize(ref))
+
+
 def test_carry_overflow_flagged(d, ctx):
     """A coefficient vector whose value does not fit L limbs is reported, not silently truncated."""
     L = 100

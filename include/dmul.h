@@ -229,6 +229,12 @@ uint64_t dmul_max_min_limbs(void);
  * *n is in: capacity, out: the number of stages.  Synchronizes the context's last stream. */
 int dmul_stage_times(dmul_ctx *ctx, const char **names, double *ms, uint64_t *launches, int *n);
 
+/* Switch stage timing on (on != 0) or off for the calls that follow, whatever the context's
+ * DMUL_FLAG_STAGE_TIMING said; timings already recorded stay available to dmul_stage_times.
+ * With timing off, consecutive pipeline kernels overlap their launch with the predecessor's
+ * drain (the event records between stages would serialize them). */
+int dmul_stage_timing(dmul_ctx *ctx, int on);
+
 /* Integer-pipe probe: runs a kernel of independent 32-bit multiply-adds (the IMAD pipe of the
  * modular arithmetic) on every SM and returns the achieved rate in operations per second. */
 int dmul_probe_imad(dmul_ctx *ctx, double *imad_per_s);

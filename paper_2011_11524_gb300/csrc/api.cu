@@ -386,8 +386,7 @@ int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
         cudaEventRecord(e0, s);
         launch_col_fwd(pe->pd, jd.x, jd.nx, jd.y, jd.ny, c->X, c->Y, c->status, s);
         launch_row_any(pe->pd, c->X, c->Y, false, c->status, s);
-        launch_col_inv(pe->pd, c->X, Lt, kInvDigits, jd.z, c->spill, s);
-        cudaMemsetAsync(c->ctl, 0, carry_ctl_bytes(Lt), s);
+        launch_col_inv(pe->pd, c->X, Lt, kInvDigits, jd.z, c->spill, s, c->ctl, carry_ctl_bytes(Lt));
         launch_carry(jd.z, c->spill, Lt, (CarryCtl *)c->ctl, nzb, c->status, s);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
@@ -449,15 +448,18 @@ int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, si
     const bool square = (x == y && nx == ny);
     rc = enqueue_transforms(c, pe, x, nx, y, ny, square, s);
     if (rc) return rc;
-    if (c->cfg.flags & DMUL_FLAG_SIXSTEP) {
+    const bool six = (c->cfg.flags & DMUL_FLAG_SIXSTEP) != 0;
+    if (six) {
         Timed t(c, kStCrt, s);
         CK(launch_crt_natural(c->X, N, L, mode, mode == kInvDigits ? z : mode_out, c->spill, s));
+        if (mode == kInvDigits) CK(cudaMemsetAsync(c->ctl, 0, carry_ctl_bytes(L), s));
     } else {
+        // the inverse pass also clears the carry scan's control block (no memset in between)
         Timed t(c, kStColInv, s);
-        CK(launch_col_inv(pe->pd, c->X, L, mode, mode == kInvDigits ? z : mode_out, c->spill, s));
+        CK(launch_col_inv(pe->pd, c->X, L, mode, mode == kInvDigits ? z : mode_out, c->spill, s,
+                          mode == kInvDigits ? c->ctl : nullptr, mode == kInvDigits ? carry_ctl_bytes(L) : 0));
     }
     if (mode == kInvDigits) {
-        CK(cudaMemsetAsync(c->ctl, 0, carry_ctl_bytes(L), s));
         Timed t(c, kStCarry, s);
         CK(launch_carry(z, c->spill, L, (CarryCtl *)c->ctl, nz, c->status, s));
     }
@@ -805,6 +807,17 @@ int dmul_stage_times(dmul_ctx *c, const char **names, double *ms, uint64_t *laun
         c->timers[i].launches = 0;
     }
     *n = k;
+    return DMUL_OK;
+}
+
+int dmul_stage_timing(dmul_ctx *c, int on) {
+    if (!c) return DMUL_ERR_INVALID;
+    if (c->timing && !on && c->ev_used) {
+        int rc = set_device(c);
+        if (rc) return rc;
+        collect_timers(c);  // keep what was recorded so far for dmul_stage_times
+    }
+    c->timing = on != 0;
     return DMUL_OK;
 }
 

@@ -222,6 +222,8 @@ __global__ void __launch_bounds__(512) k_col_fwd_ct(const PlanDev pd, const uint
                                                     uint64_t ny, uint32_t *X, uint32_t *Y,
                                                     uint32_t *status) {
     extern __shared__ __align__(16) uint32_t sm[];
+    pdl_trigger();
+    pdl_wait();
     const int pi = blockIdx.x % kPrimes;
     const uint32_t tile = blockIdx.x / kPrimes;
     const bool second = blockIdx.y != 0;
@@ -235,8 +237,12 @@ __global__ void __launch_bounds__(512) k_col_fwd_ct(const PlanDev pd, const uint
 template <uint32_t N1, int MODE>
 __global__ void __launch_bounds__(512) k_col_inv_ct(const PlanDev pd, const uint32_t *__restrict__ X,
                                                     uint64_t L, uint32_t *__restrict__ out,
-                                                    uint2 *__restrict__ spill) {
+                                                    uint2 *__restrict__ spill, uint64_t *zero,
+                                                    uint32_t nzero) {
     extern __shared__ __align__(16) uint32_t sm[];
+    pdl_trigger();
+    pdl_wait();
+    zero_words(zero, nzero);
     const int pi = (int)cg::this_cluster().block_rank();
     const uint32_t n2 = (blockIdx.x / kPrimes) * 32 + (threadIdx.x & 31);
     const uint32_t *src = X + (uint64_t)pi * pd.N;
@@ -269,8 +275,7 @@ static cudaError_t launch_fwd_ct(const PlanDev &pd, const uint32_t *x, uint64_t 
                                  cudaStream_t s) {
     const size_t smem = (size_t)N1 * 32 * sizeof(uint32_t);
     dim3 grid(kPrimes * (pd.N2 / 32), y ? 2 : 1);
-    k_col_fwd_ct<N1><<<grid, pd.col_threads, smem, s>>>(pd, x, nx, y, ny, X, Y, status);
-    return cudaGetLastError();
+    return launch_pdl(k_col_fwd_ct<N1>, grid, dim3(pd.col_threads), smem, s, 1, pd, x, nx, y, ny, X, Y, status);
 }
 
 cudaError_t launch_col_fwd_ct(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
@@ -286,37 +291,27 @@ cudaError_t launch_col_fwd_ct(const PlanDev &pd, const uint32_t *x, uint64_t nx,
 
 template <uint32_t N1, int MODE>
 static cudaError_t launch_inv_ct_mode(const PlanDev &pd, const uint32_t *X, uint64_t L,
-                                      uint32_t *out, uint2 *spill, cudaStream_t s) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kPrimes * (pd.N2 / 32), 1, 1);
-    cfg.blockDim = dim3(pd.col_threads, 1, 1);
-    cfg.dynamicSmemBytes = (size_t)N1 * 32 * sizeof(uint32_t);
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = kPrimes;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_col_inv_ct<N1, MODE>, pd, X, L, out, spill);
+                                      uint32_t *out, uint2 *spill, cudaStream_t s, uint64_t *zero,
+                                      uint32_t nzero) {
+    return launch_pdl(k_col_inv_ct<N1, MODE>, dim3(kPrimes * (pd.N2 / 32)), dim3(pd.col_threads),
+                      (size_t)N1 * 32 * sizeof(uint32_t), s, kPrimes, pd, X, L, out, spill, zero, nzero);
 }
 
 template <uint32_t N1>
 static cudaError_t launch_inv_ct(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
-                                 uint32_t *out, uint2 *spill, cudaStream_t s) {
-    if (mode == kInvTriples) return launch_inv_ct_mode<N1, kInvTriples>(pd, X, L, out, spill, s);
-    if (mode == kInvResidues) return launch_inv_ct_mode<N1, kInvResidues>(pd, X, L, out, spill, s);
-    return launch_inv_ct_mode<N1, kInvDigits>(pd, X, L, out, spill, s);
+                                 uint32_t *out, uint2 *spill, cudaStream_t s, uint64_t *zero, uint32_t nzero) {
+    if (mode == kInvTriples) return launch_inv_ct_mode<N1, kInvTriples>(pd, X, L, out, spill, s, zero, nzero);
+    if (mode == kInvResidues) return launch_inv_ct_mode<N1, kInvResidues>(pd, X, L, out, spill, s, zero, nzero);
+    return launch_inv_ct_mode<N1, kInvDigits>(pd, X, L, out, spill, s, zero, nzero);
 }
 
 cudaError_t launch_col_inv_ct(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
-                              uint32_t *out, uint2 *spill, cudaStream_t s) {
+                              uint32_t *out, uint2 *spill, cudaStream_t s, uint64_t *zero, uint32_t nzero) {
     switch (pd.N1) {
-        case 512: return launch_inv_ct<512>(pd, X, L, mode, out, spill, s);
-        case 768: return launch_inv_ct<768>(pd, X, L, mode, out, spill, s);
-        case 1024: return launch_inv_ct<1024>(pd, X, L, mode, out, spill, s);
-        default: return launch_inv_ct<1536>(pd, X, L, mode, out, spill, s);
+        case 512: return launch_inv_ct<512>(pd, X, L, mode, out, spill, s, zero, nzero);
+        case 768: return launch_inv_ct<768>(pd, X, L, mode, out, spill, s, zero, nzero);
+        case 1024: return launch_inv_ct<1024>(pd, X, L, mode, out, spill, s, zero, nzero);
+        default: return launch_inv_ct<1536>(pd, X, L, mode, out, spill, s, zero, nzero);
     }
 }
 
@@ -563,6 +558,8 @@ __global__ void __launch_bounds__(256, 2) k_col_fwd_h(const PlanDev pd, const ui
                                                       uint32_t *status) {
     using S = ColSched<N1>;
     extern __shared__ __align__(16) uint32_t sm[];
+    pdl_trigger();
+    pdl_wait();
     const int pi = blockIdx.x % kPrimes;
     const uint32_t j0 = (blockIdx.x / kPrimes) * 16;
     const bool second = blockIdx.y != 0;
@@ -597,8 +594,12 @@ __device__ __forceinline__ void hcol_inv_body(const PlanDev &pd, const uint32_t 
 template <uint32_t N1, int MODE>
 __global__ void __launch_bounds__(256, 2) k_col_inv_h(const PlanDev pd, const uint32_t *__restrict__ X,
                                                       uint64_t L, uint32_t *__restrict__ out,
-                                                      uint2 *__restrict__ spill) {
+                                                      uint2 *__restrict__ spill, uint64_t *zero,
+                                                      uint32_t nzero) {
     extern __shared__ __align__(16) uint32_t sm[];
+    pdl_trigger();
+    pdl_wait();
+    zero_words(zero, nzero);
     cg::cluster_group cluster = cg::this_cluster();
     const uint32_t rank = cluster.block_rank();
     const uint32_t half = rank / kPrimes, pi = rank % kPrimes;
@@ -644,34 +645,22 @@ static cudaError_t launch_fwd_h(const PlanDev &pd, const uint32_t *x, uint64_t n
                                 uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status, cudaStream_t s) {
     const size_t smem = (size_t)N1 * 16 * sizeof(uint32_t);
     dim3 grid(kPrimes * (pd.N2 / 16), y ? 2 : 1);
-    k_col_fwd_h<N1><<<grid, pd.col_threads, smem, s>>>(pd, x, nx, y, ny, X, Y, status);
-    return cudaGetLastError();
+    return launch_pdl(k_col_fwd_h<N1>, grid, dim3(pd.col_threads), smem, s, 1, pd, x, nx, y, ny, X, Y, status);
 }
 
 template <uint32_t N1, int MODE>
 static cudaError_t launch_inv_h_mode(const PlanDev &pd, const uint32_t *X, uint64_t L, uint32_t *out,
-                                     uint2 *spill, cudaStream_t s) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * kPrimes * (pd.N2 / 32), 1, 1);
-    cfg.blockDim = dim3(pd.col_threads, 1, 1);
-    cfg.dynamicSmemBytes = (size_t)N1 * 16 * sizeof(uint32_t);
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 2 * kPrimes;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_col_inv_h<N1, MODE>, pd, X, L, out, spill);
+                                     uint2 *spill, cudaStream_t s, uint64_t *zero, uint32_t nzero) {
+    return launch_pdl(k_col_inv_h<N1, MODE>, dim3(2 * kPrimes * (pd.N2 / 32)), dim3(pd.col_threads),
+                      (size_t)N1 * 16 * sizeof(uint32_t), s, 2 * kPrimes, pd, X, L, out, spill, zero, nzero);
 }
 
 template <uint32_t N1>
 static cudaError_t launch_inv_h(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
-                                uint32_t *out, uint2 *spill, cudaStream_t s) {
-    if (mode == kInvTriples) return launch_inv_h_mode<N1, kInvTriples>(pd, X, L, out, spill, s);
-    if (mode == kInvResidues) return launch_inv_h_mode<N1, kInvResidues>(pd, X, L, out, spill, s);
-    return launch_inv_h_mode<N1, kInvDigits>(pd, X, L, out, spill, s);
+                                uint32_t *out, uint2 *spill, cudaStream_t s, uint64_t *zero, uint32_t nzero) {
+    if (mode == kInvTriples) return launch_inv_h_mode<N1, kInvTriples>(pd, X, L, out, spill, s, zero, nzero);
+    if (mode == kInvResidues) return launch_inv_h_mode<N1, kInvResidues>(pd, X, L, out, spill, s, zero, nzero);
+    return launch_inv_h_mode<N1, kInvDigits>(pd, X, L, out, spill, s, zero, nzero);
 }
 
 cudaError_t launch_col_fwd_h(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
@@ -685,12 +674,12 @@ cudaError_t launch_col_fwd_h(const PlanDev &pd, const uint32_t *x, uint64_t nx, 
 }
 
 cudaError_t launch_col_inv_h(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
-                             uint32_t *out, uint2 *spill, cudaStream_t s) {
+                             uint32_t *out, uint2 *spill, cudaStream_t s, uint64_t *zero, uint32_t nzero) {
     switch (pd.N1) {
-        case 512: return launch_inv_h<512>(pd, X, L, mode, out, spill, s);
-        case 768: return launch_inv_h<768>(pd, X, L, mode, out, spill, s);
-        case 1024: return launch_inv_h<1024>(pd, X, L, mode, out, spill, s);
-        default: return launch_inv_h<1536>(pd, X, L, mode, out, spill, s);
+        case 512: return launch_inv_h<512>(pd, X, L, mode, out, spill, s, zero, nzero);
+        case 768: return launch_inv_h<768>(pd, X, L, mode, out, spill, s, zero, nzero);
+        case 1024: return launch_inv_h<1024>(pd, X, L, mode, out, spill, s, zero, nzero);
+        default: return launch_inv_h<1536>(pd, X, L, mode, out, spill, s, zero, nzero);
     }
 }
 

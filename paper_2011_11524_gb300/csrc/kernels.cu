@@ -20,6 +20,8 @@ __global__ void __launch_bounds__(512) k_col_fwd(const PlanDev pd, const uint32_
                                                  uint64_t ny, uint32_t *X, uint32_t *Y,
                                                  uint32_t *status) {
     extern __shared__ uint32_t sm[];
+    pdl_trigger();
+    pdl_wait();
     const int pi = blockIdx.x % kPrimes;
     const uint32_t tile = blockIdx.x / kPrimes;
     const bool second = blockIdx.y != 0;
@@ -38,13 +40,14 @@ cudaError_t launch_col_fwd(const PlanDev &pd, const uint32_t *x, uint64_t nx, co
     const size_t smem = (size_t)pd.N1 * 32 * sizeof(uint32_t);
     const int threads = (int)pd.col_threads;
     dim3 grid(kPrimes * (pd.N2 / 32), y ? 2 : 1);
-    k_col_fwd<<<grid, threads, smem, s>>>(pd, x, nx, y, ny, X, Y, status);
-    return cudaGetLastError();
+    return launch_pdl(k_col_fwd, grid, dim3(threads), smem, s, 1, pd, x, nx, y, ny, X, Y, status);
 }
 
 template <bool SQR>
 __global__ void __launch_bounds__(256) k_row_mul(const PlanDev pd, uint32_t *X, const uint32_t *Y) {
     extern __shared__ uint32_t sm[];
+    pdl_trigger();
+    pdl_wait();
     const uint32_t row = blockIdx.x;
     const int pi = blockIdx.y;
     uint32_t *xr = X + (uint64_t)pi * pd.N + (uint64_t)row * pd.N2;
@@ -56,6 +59,8 @@ template <bool SQR>
 __global__ void __launch_bounds__(256) k_row_mul_tma(const PlanDev pd, uint32_t *X, const uint32_t *Y,
                                                      uint32_t *status) {
     extern __shared__ __align__(16) uint32_t sm[];
+    pdl_trigger();
+    pdl_wait();
     const int pi = blockIdx.y;
     DMUL_PRIME_SWITCH(pi, (row_mul_tma_body<PI, SQR>(pd, sm, X, Y, status)));
 }
@@ -65,9 +70,8 @@ size_t row_tma_smem(const PlanDev &pd) { return (size_t)6 * pd.N2 * 4 + 16; }
 cudaError_t launch_row_mul_tma(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
                                uint32_t *status, cudaStream_t s) {
     dim3 grid(pd.row_grid ? pd.row_grid : 256, kPrimes);
-    if (square) k_row_mul_tma<true><<<grid, pd.row_threads, row_tma_smem(pd), s>>>(pd, X, Y, status);
-    else k_row_mul_tma<false><<<grid, pd.row_threads, row_tma_smem(pd), s>>>(pd, X, Y, status);
-    return cudaGetLastError();
+    if (square) return launch_pdl(k_row_mul_tma<true>, grid, dim3(pd.row_threads), row_tma_smem(pd), s, 1, pd, X, Y, status);
+    return launch_pdl(k_row_mul_tma<false>, grid, dim3(pd.row_threads), row_tma_smem(pd), s, 1, pd, X, Y, status);
 }
 
 cudaError_t launch_row_any(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
@@ -81,39 +85,35 @@ cudaError_t launch_row_mul(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bo
                            cudaStream_t s) {
     dim3 grid(pd.N1, kPrimes);
     const size_t smem = (size_t)(square ? 1 : 2) * pd.N2 * sizeof(uint32_t);
-    if (square) k_row_mul<true><<<grid, pd.row_threads, smem, s>>>(pd, X, Y);
-    else k_row_mul<false><<<grid, pd.row_threads, smem, s>>>(pd, X, Y);
-    return cudaGetLastError();
+    if (square) return launch_pdl(k_row_mul<true>, grid, dim3(pd.row_threads), smem, s, 1, pd, X, Y);
+    return launch_pdl(k_row_mul<false>, grid, dim3(pd.row_threads), smem, s, 1, pd, X, Y);
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(512) k_col_inv(const PlanDev pd, const uint32_t *__restrict__ X,
                                                  uint64_t L, uint32_t *__restrict__ out,
-                                                 uint2 *__restrict__ spill) {
+                                                 uint2 *__restrict__ spill, uint64_t *zero, uint32_t nzero) {
     extern __shared__ uint32_t sm[];
+    pdl_trigger();
+    pdl_wait();
+    zero_words(zero, nzero);
     col_inv_crt(pd, X, L, MODE, out, spill, sm);
 }
 
 cudaError_t launch_col_inv(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
-                           uint32_t *out, uint2 *spill, cudaStream_t s) {
+                           uint32_t *out, uint2 *spill, cudaStream_t s, void *zero, size_t zero_bytes) {
+    uint64_t *zw = (uint64_t *)zero;
+    const uint32_t nzero = (uint32_t)(zero_bytes / 8);
     if (col_pass_specialized(pd))
-        return pd.col_half ? launch_col_inv_h(pd, X, L, mode, out, spill, s)
-                           : launch_col_inv_ct(pd, X, L, mode, out, spill, s);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kPrimes * (pd.N2 / 32), 1, 1);
-    cfg.blockDim = dim3(pd.col_threads, 1, 1);
-    cfg.dynamicSmemBytes = (size_t)pd.N1 * 32 * sizeof(uint32_t);
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = kPrimes;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    if (mode == kInvTriples) return cudaLaunchKernelEx(&cfg, k_col_inv<kInvTriples>, pd, X, L, out, spill);
-    if (mode == kInvResidues) return cudaLaunchKernelEx(&cfg, k_col_inv<kInvResidues>, pd, X, L, out, spill);
-    return cudaLaunchKernelEx(&cfg, k_col_inv<kInvDigits>, pd, X, L, out, spill);
+        return pd.col_half ? launch_col_inv_h(pd, X, L, mode, out, spill, s, zw, nzero)
+                           : launch_col_inv_ct(pd, X, L, mode, out, spill, s, zw, nzero);
+    const dim3 grid(kPrimes * (pd.N2 / 32)), block(pd.col_threads);
+    const size_t smem = (size_t)pd.N1 * 32 * sizeof(uint32_t);
+    if (mode == kInvTriples)
+        return launch_pdl(k_col_inv<kInvTriples>, grid, block, smem, s, kPrimes, pd, X, L, out, spill, zw, nzero);
+    if (mode == kInvResidues)
+        return launch_pdl(k_col_inv<kInvResidues>, grid, block, smem, s, kPrimes, pd, X, L, out, spill, zw, nzero);
+    return launch_pdl(k_col_inv<kInvDigits>, grid, block, smem, s, kPrimes, pd, X, L, out, spill, zw, nzero);
 }
 
 // digit triples -> within-chunk digit sums + spills (the CRT stage's epilogue on given triples)
@@ -148,23 +148,26 @@ template <int NT, int PER>
 __global__ void __launch_bounds__(NT) k_carry(uint32_t *__restrict__ z, const uint2 *__restrict__ spill,
                                               uint64_t L, CarryCtl *ctl, uint64_t *nz, uint32_t *status,
                                               uint32_t ntiles) {
+    pdl_trigger();
+    pdl_wait();
     carry_tile<NT, PER>(z, spill, L, ctl, nz, status, ntiles);
 }
 
 // Long products take 8192-limb tiles (512 threads x 16), so that every tile of a product of a few
 // million limbs is resident at once and the look-back chain is short; shorter ones 2048-limb tiles
-// (256 x 8) for parallelism.  ctl holds flags for ceil(L / kCarryLimbs) tiles, enough for either.
+// (256 x 8) for parallelism.  ctl holds flags for ceil(L / kCarryLimbs) tiles, enough for either;
+// it must be zero when the kernel starts.
 cudaError_t launch_carry(uint32_t *z, const uint2 *spill, uint64_t L, CarryCtl *ctl, uint64_t *nz,
                          uint32_t *status, cudaStream_t s) {
     constexpr uint64_t kBig = 512 * 16;
     if (L >= 256 * kBig) {
         const uint64_t ntiles = (L + kBig - 1) / kBig;
-        k_carry<512, 16><<<(unsigned)ntiles, 512, 0, s>>>(z, spill, L, ctl, nz, status, (uint32_t)ntiles);
-    } else {
-        const uint64_t ntiles = (L + kCarryLimbs - 1) / kCarryLimbs;
-        k_carry<256, 8><<<(unsigned)ntiles, 256, 0, s>>>(z, spill, L, ctl, nz, status, (uint32_t)ntiles);
+        return launch_pdl(k_carry<512, 16>, dim3((unsigned)ntiles), dim3(512), 0, s, 1, z, spill, L, ctl, nz,
+                          status, (uint32_t)ntiles);
     }
-    return cudaGetLastError();
+    const uint64_t ntiles = (L + kCarryLimbs - 1) / kCarryLimbs;
+    return launch_pdl(k_carry<256, 8>, dim3((unsigned)ntiles), dim3(256), 0, s, 1, z, spill, L, ctl, nz, status,
+                      (uint32_t)ntiles);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -1,5 +1,6 @@
 // kernels.cuh -- launch interface of the multiplication pipeline kernels (host side).
 #pragma once
+#include <utility>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include "common.h"
@@ -20,6 +21,33 @@ struct CarryCtl {
 inline size_t carry_ctl_bytes(uint64_t L) {
     uint64_t ntiles = (L + kCarryLimbs - 1) / kCarryLimbs;
     return sizeof(CarryCtl) + ntiles * sizeof(uint64_t);
+}
+
+// Launch with programmatic stream serialization (the kernel may begin while its predecessor in the
+// stream drains; it calls pdl_wait() before touching memory) and, for cluster > 1, a cluster shape.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              unsigned cluster, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    unsigned n = 0;
+    at[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[n].val.programmaticStreamSerializationAllowed = 1;
+    ++n;
+    if (cluster > 1) {
+        at[n].id = cudaLaunchAttributeClusterDimension;
+        at[n].val.clusterDim.x = cluster;
+        at[n].val.clusterDim.y = 1;
+        at[n].val.clusterDim.z = 1;
+        ++n;
+    }
+    cfg.attrs = at;
+    cfg.numAttrs = n;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // One job of a batched launch (device-resident descriptor).
@@ -73,14 +101,14 @@ cudaError_t launch_col_fwd_ct(const PlanDev &pd, const uint32_t *x, uint64_t nx,
                               uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status,
                               cudaStream_t s);
 cudaError_t launch_col_inv_ct(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
-                              uint32_t *out, uint2 *spill, cudaStream_t s);
+                              uint32_t *out, uint2 *spill, cudaStream_t s, uint64_t *zero, uint32_t nzero);
 cudaError_t init_kernel_attributes_colpass();
 // The same passes on N1 x 16 half tiles (pd.col_half): forward grid (3 N2/16, operands); inverse
 // in clusters of six CTAs (three primes x two halves of a 32-column tile).  col_threads <= 256.
 cudaError_t launch_col_fwd_h(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
                              uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status, cudaStream_t s);
 cudaError_t launch_col_inv_h(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
-                             uint32_t *out, uint2 *spill, cudaStream_t s);
+                             uint32_t *out, uint2 *spill, cudaStream_t s, uint64_t *zero, uint32_t nzero);
 cudaError_t init_kernel_attributes_colhalf();
 cudaError_t upload_constants_colpass(const PrimeConst pc[kPrimes], const CrtConst &crt);
 
@@ -91,8 +119,12 @@ cudaError_t launch_row_any(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bo
 // Inverse column pass + (mode) CRT and digit split.  kInvDigits writes the within-chunk digit
 // sums to out[0..L) and the chunk spills to spill; kInvTriples writes d[3k..3k+2]; kInvResidues
 // writes r[pi*L + k].
+// zero/zero_bytes (optional, a multiple of 8 bytes): device words the kernel clears after its
+// predecessor in the stream has finished -- the carry scan's control block, so that no separate
+// memset separates the two kernels.
 cudaError_t launch_col_inv(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
-                           uint32_t *out, uint2 *spill, cudaStream_t s);
+                           uint32_t *out, uint2 *spill, cudaStream_t s, void *zero = nullptr,
+                           size_t zero_bytes = 0);
 
 // Digit triples -> within-chunk digit sums + spills (the tail of the CRT stage, on its own).
 cudaError_t launch_triples_to_digits(const uint32_t *d, uint64_t L, uint32_t *out, uint2 *spill,

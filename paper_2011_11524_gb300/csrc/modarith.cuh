@@ -34,6 +34,14 @@ static __constant__ CrtConst c_crt;
 
 __device__ __forceinline__ uint32_t umin32(uint32_t a, uint32_t b) { return a < b ? a : b; }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start while its predecessor in the stream drains; pdl_wait() blocks until that predecessor has
+// completed and its memory is visible (a no-op without the launch attribute), pdl_trigger() lets
+// the successor launch once every CTA of this grid has issued it.  Every pipeline kernel calls
+// pdl_trigger() first and pdl_wait() before its first global access.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // [0, 4p) -> [0, 2p)
 template <int PI>
 __device__ __forceinline__ uint32_t red2p(uint32_t a) { return umin32(a, a - c_prime[PI].p2); }

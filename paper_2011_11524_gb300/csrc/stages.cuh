@@ -44,6 +44,13 @@ namespace dml {
 
 __device__ __forceinline__ uint2 ldtw(const uint2 *p) { return __ldg(p); }
 
+// Grid-strided zeroing of n words (the next pipeline stage's control block; p may be null).
+__device__ __forceinline__ void zero_words(uint64_t *p, uint32_t n) {
+    if (!p) return;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = 0;
+}
+
 // Row-buffer index with an XOR swizzle of the 32-word bank rows: bank = (a mod 32) ^ f(a div 32),
 // f(r) = (r mod 16) | ((r >> 3) & 1) << 4.  Every stage pattern of every row schedule the planner
 // emits (a small radix first, then radix 16) then hits 32 distinct banks per warp access.

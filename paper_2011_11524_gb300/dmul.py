@@ -36,7 +36,7 @@ EXPORTS = [
     "dmul_init", "dmul_destroy", "dmul_strerror", "dmul_sync", "dmul_mul", "dmul_sqr",
     "dmul_mul_host", "dmul_batch", "dmul_submit", "dmul_poll", "dmul_wait", "dmul_conv_residues",
     "dmul_conv_coeffs", "dmul_carry", "dmul_transpose", "dmul_get_plan", "dmul_primes",
-    "dmul_lambda", "dmul_max_min_limbs", "dmul_stage_times", "dmul_probe_imad",
+    "dmul_lambda", "dmul_max_min_limbs", "dmul_stage_times", "dmul_stage_timing", "dmul_probe_imad",
     "dmul_carry_noalloc",
 ]
 
@@ -102,6 +102,7 @@ def load() -> ctypes.CDLL:
         "dmul_max_min_limbs": ([], u64),
         "dmul_stage_times": ([vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(u64), ctypes.POINTER(i32)], i32),
+        "dmul_stage_timing": ([vp, i32], i32),
         "dmul_probe_imad": ([vp, ctypes.POINTER(ctypes.c_double)], i32),
     }
     for name, (args, res) in sig.items():
@@ -360,6 +361,11 @@ class Context:
 
     def stage_times(self):
         return dmul_stage_times(self.handle)
+
+    def stage_timing(self, on: bool):
+        rc = load().dmul_stage_timing(self.handle, 1 if on else 0)
+        if rc:
+            raise DmulError(rc, "dmul_stage_timing")
 
     def probe_imad(self) -> float:
         return dmul_probe_imad(self.handle)

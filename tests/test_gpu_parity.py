@@ -228,11 +228,12 @@ def test_carry_adversarial(d, ctx, L):
         assert nz == len(oracle.normalize(ref))
 
 
-@pytest.mark.parametrize("L", [2_097_152, 2_200_001, 4_194_307])
+@pytest.mark.parametrize("L", [2_097_152, 2_200_001, 4_194_307, 8_400_007])
 def test_carry_long(d, ctx, L):
-    """Products of millions of limbs take the large carry tiles (8192 limbs): a carry rippling
-    through every tile (no tile's map is constant, so each look-back composes its predecessors'
-    maps), runs of 10^9-1 across tile and chunk boundaries, and near-maximal coefficients."""
+    """Products of millions of limbs take the large carry tiles (8192 limbs; beyond 1024 tiles the
+    carry-ins come from a separate scan of the tile maps): a carry rippling through every tile (no
+    tile map is constant), runs of 10^9-1 across tile and chunk boundaries, near-maximal
+    coefficients."""
     rng = _rng(6100 + L)
     for kind in ("run", "runs", "max"):
         if kind == "run":

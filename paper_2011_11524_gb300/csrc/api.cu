@@ -340,8 +340,11 @@ int check_sizes(dmul_ctx *c, size_t nx, size_t ny, uint64_t *N) {
 
 // The forward transforms of x (and y), the pointwise product and the inverse transforms; the
 // residues of the convolution are then in c->X (four-step order: inverse column pass pending).
+// y_ready (optional): an event after which y may be read -- the forward pass of x is enqueued
+// before the wait, so that y's upload overlaps it.
 int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
-                       const uint32_t *y, size_t ny, bool square, cudaStream_t s);
+                       const uint32_t *y, size_t ny, bool square, cudaStream_t s,
+                       cudaEvent_t y_ready = nullptr);
 
 // A lone short product can run as one cluster (the fused kernel: one launch, three SMs) or as the
 // four-step pipeline (four launches, many CTAs).  Which is faster depends on the length; the
@@ -408,7 +411,7 @@ int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
 
 int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny,
                 uint32_t *z, size_t z_cap, uint64_t *nz, cudaStream_t s, InvMode mode,
-                uint32_t *mode_out) {
+                uint32_t *mode_out, cudaEvent_t y_ready = nullptr) {
     uint64_t N;
     int rc = check_sizes(c, nx, ny, &N);
     if (rc) return rc;
@@ -435,6 +438,7 @@ int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, si
         jd.x = x; jd.y = y; jd.z = z; jd.nz = nz; jd.nx = nx; jd.ny = ny; jd.L = L;
         jd.square = (x == y && nx == ny) ? 1u : 0u;
         c->last_stream = s;
+        if (y_ready) CK(cudaStreamWaitEvent(s, y_ready, 0));
         Timed t(c, kStSmall, s);
         CK(launch_small_mul_one(se->sp, jd, c->status, s));
         return DMUL_OK;
@@ -446,7 +450,7 @@ int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, si
     if (rc) return rc;
     c->last_stream = s;
     const bool square = (x == y && nx == ny);
-    rc = enqueue_transforms(c, pe, x, nx, y, ny, square, s);
+    rc = enqueue_transforms(c, pe, x, nx, y, ny, square, s, y_ready);
     if (rc) return rc;
     const bool six = (c->cfg.flags & DMUL_FLAG_SIXSTEP) != 0;
     if (six) {
@@ -467,10 +471,17 @@ int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, si
 }
 
 int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
-                       const uint32_t *y, size_t ny, bool square, cudaStream_t s) {
+                       const uint32_t *y, size_t ny, bool square, cudaStream_t s, cudaEvent_t y_ready) {
     const PlanDev &pd = pe->pd;
     if (!(c->cfg.flags & DMUL_FLAG_SIXSTEP)) {
-        {
+        if (y_ready && !square) {
+            // x's forward pass first, then (once y is uploaded) y's
+            Timed t(c, kStColFwd, s);
+            CK(launch_col_fwd(pd, x, nx, nullptr, 0, c->X, nullptr, c->status, s));
+            CK(cudaStreamWaitEvent(s, y_ready, 0));
+            CK(launch_col_fwd(pd, y, ny, nullptr, 0, c->Y, nullptr, c->status, s));
+        } else {
+            if (y_ready) CK(cudaStreamWaitEvent(s, y_ready, 0));
             Timed t(c, kStColFwd, s);
             CK(launch_col_fwd(pd, x, nx, square ? nullptr : y, ny, c->X, c->Y, c->status, s));
         }
@@ -480,6 +491,7 @@ int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
     }
     // Six-step form (Sec. 7.2): [N1 x N2] -> transpose -> row DFTs of length N1 -> transpose
     // back -> (twiddle fused into the row DFT kernel) -> fused row pass -> and the mirror.
+    if (y_ready) CK(cudaStreamWaitEvent(s, y_ready, 0));
     const uint64_t N = pd.N;
     for (int op = 0; op < (square ? 1 : 2); ++op) {
         uint32_t *A = op ? c->Y : c->X;
@@ -648,6 +660,12 @@ void dmul_destroy(dmul_ctx *c) {
     destroy_batch_state(c);
 
     if (c->hx) { cudaFree(c->hx); cudaFree(c->hy); cudaFree(c->hz); cudaFree(c->hnz); }
+    if (c->h_tail) {
+        cudaFreeHost(c->h_tail);
+        cudaStreamDestroy(c->copy_stream);
+        cudaEventDestroy(c->ev_start);
+        cudaEventDestroy(c->ev_y);
+    }
     for (auto &e : c->ev_pool) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
@@ -733,6 +751,12 @@ int dmul_mul_host(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, 
     if (z_cap < L) return DMUL_ERR_CAPACITY;
     rc = set_device(c);
     if (rc) return rc;
+    if (!c->h_tail) {
+        CK(cudaMallocHost(&c->h_tail, 64));
+        CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->ev_y, cudaEventDisableTiming));
+    }
     if (c->h_cap < L) {
         if (c->hx) { cudaFree(c->hx); cudaFree(c->hy); cudaFree(c->hz); cudaFree(c->hnz); c->used -= c->h_cap * 12 + 64; }
         c->hx = c->hy = c->hz = nullptr;
@@ -746,16 +770,36 @@ int dmul_mul_host(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, 
         c->h_cap = L;
     }
     cudaStream_t s = c->own_stream;
+    // x is uploaded on the compute stream; y on the copy stream, overlapping x's forward pass
     CK(cudaMemcpyAsync(c->hx, x, nx * 4, cudaMemcpyHostToDevice, s));
-    if (!square) CK(cudaMemcpyAsync(c->hy, y, ny * 4, cudaMemcpyHostToDevice, s));
-    rc = enqueue_mul(c, c->hx, nx, square ? c->hx : c->hy, ny, c->hz, L, c->hnz, s, kInvDigits, nullptr);
-    if (rc) return rc;
+    cudaEvent_t y_ready = nullptr;
+    if (!square) {
+        CK(cudaEventRecord(c->ev_start, s));  // earlier work on s (readers of hy) is done first
+        CK(cudaStreamWaitEvent(c->copy_stream, c->ev_start, 0));
+        CK(cudaMemcpyAsync(c->hy, y, ny * 4, cudaMemcpyHostToDevice, c->copy_stream));
+        CK(cudaEventRecord(c->ev_y, c->copy_stream));
+        y_ready = c->ev_y;
+    }
+    rc = enqueue_mul(c, c->hx, nx, square ? c->hx : c->hy, ny, c->hz, L, c->hnz, s, kInvDigits, nullptr,
+                     y_ready);
+    if (rc) {
+        cudaStreamSynchronize(c->copy_stream);
+        return rc;
+    }
     CK(cudaMemcpyAsync(z, c->hz, L * 4, cudaMemcpyDeviceToHost, s));
-    uint64_t n64 = 0;
-    CK(cudaMemcpyAsync(&n64, c->hnz, 8, cudaMemcpyDeviceToHost, s));
-    rc = dmul_sync(c, s);
-    if (nz) *nz = (size_t)n64;
-    return rc;
+    // the normalized length and the status word into pinned memory: one synchronization
+    CK(cudaMemcpyAsync(&c->h_tail[0], c->hnz, 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&c->h_tail[1], c->status, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (nz) *nz = (size_t)c->h_tail[0];
+    const uint32_t st = (uint32_t)c->h_tail[1];
+    if (st) {
+        CK(cudaMemsetAsync(c->status, 0, 4, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    if (st & kStatusTimeout) return DMUL_ERR_TIMEOUT;
+    if (st & kStatusInvalid) return DMUL_ERR_INVALID;
+    return DMUL_OK;
 }
 
 int dmul_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, void *stream) {

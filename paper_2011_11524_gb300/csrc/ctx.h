@@ -86,6 +86,9 @@ struct dmul_ctx {
     uint32_t *hx = nullptr, *hy = nullptr, *hz = nullptr;
     uint64_t *hnz = nullptr;
     size_t h_cap = 0;
+    uint64_t *h_tail = nullptr;            // pinned: [0] normalized length, [1] status word
+    cudaStream_t copy_stream = nullptr;    // uploads of the second operand
+    cudaEvent_t ev_start = nullptr, ev_y = nullptr;
     cudaStream_t own_stream = nullptr;
     cudaStream_t last_stream = nullptr;
     // stage timing

@@ -297,9 +297,12 @@ def test_argument_errors(d, ctx):
     assert d.dmul_mul(ctx.handle, t, big, t, 10, z, big + 10, None) == d.DMUL_ERR_TOO_LARGE
 
 
-def test_host_buffer_entry_point(d, ctx):
-    rng = _rng(7100)
-    x, y = _rand(rng, 7777), _rand(rng, 5555)
+@pytest.mark.parametrize("n,m", [(7777, 5555), (300000, 250001), (1 << 20, (1 << 20) - 3)])
+def test_host_buffer_entry_point(d, ctx, n, m):
+    """dmul_mul_host: host buffers in and out (y's upload overlaps x's forward pass on the
+    four-step path), the normalized length and the status word returned with the product."""
+    rng = _rng(7100 + n)
+    x, y = _rand(rng, n), _rand(rng, m)
     z = np.zeros(len(x) + len(y), np.uint32)
     rc, nz = d.dmul_mul_host(ctx.handle, x, len(x), y, len(y), z, len(z))
     assert rc == 0
@@ -308,6 +311,13 @@ def test_host_buffer_entry_point(d, ctx):
     z2 = np.zeros(2 * len(x), np.uint32)
     rc, nz = d.dmul_mul_host(ctx.handle, x, len(x), x, len(x), z2, len(z2))
     assert rc == 0 and np.array_equal(z2, oracle.mul(x, x))
+    # an invalid limb is reported through the host entry point, and the context stays usable
+    bad = y.copy()
+    bad[len(bad) // 2] = B
+    rc, _ = d.dmul_mul_host(ctx.handle, x, len(x), bad, len(bad), z, len(z))
+    assert rc == d.DMUL_ERR_INVALID
+    rc, nz = d.dmul_mul_host(ctx.handle, x, len(x), y, len(y), z, len(z))
+    assert rc == 0 and np.array_equal(z, ref)
 
 
 # ---- six-step form (Sec. 7.2) with the in-place transposes of Sec. 7.6 -------------------------

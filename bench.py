@@ -118,6 +118,18 @@ def _transform_mults(n: int, radices: list[int]) -> float:
     return tot
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each stage's kernel on the
+# 2^24 x 2^24-digit workload, from one ncu --set full capture of the current kernels (cold L2;
+# summarized under profiles/).  Keyed by (stage, N, N1, N2, half-width column tiles); a stage whose
+# kernel changes after the capture must be dropped from this table until it is captured again.
+NCU_TRAFFIC = {
+    ("col_fwd", 4194304, 1024, 4096, 1): 24.156928e6 + 46.069248e6,
+    ("row_mul", 4194304, 1024, 4096, 1): 100.979968e6 + 8.389888e6,
+    ("col_inv_crt", 4194304, 1024, 4096, 1): 58.190848e6 + 1.070592e6,
+    ("carry_scan", 4194304, 1024, 4096, 1): 15.883008e6,
+}
+
+
 def work_model(info, nx: int, ny: int, square: bool) -> dict:
     N, N1, N2 = info.N, info.N1, info.N2
     cr = [r for r in info.col_radix if r]
@@ -272,6 +284,7 @@ def run_ours(args, rank, world, local):
                 "frac": round(gbs / hbm_peak, 4), "traffic": None, "kernel": dom,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                 "imad_tps": round(imad_t, 3), "imad_frac": round(imad_t / imad_peak_t, 4)}
+    roof["traffic"] = NCU_TRAFFIC.get((dom, int(info.N), int(info.N1), int(info.N2), int(info.col_half)))
     launches = sum(v[1] for v in stages.values()) // max(1, stage_steps)
 
     out = {

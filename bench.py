@@ -123,9 +123,7 @@ def _transform_mults(n: int, radices: list[int]) -> float:
 # summarized under profiles/).  Keyed by (stage, N, N1, N2, half-width column tiles); a stage whose
 # kernel changes after the capture must be dropped from this table until it is captured again.
 NCU_TRAFFIC = {
-    ("col_fwd", 4194304, 1024, 4096, 1): 24.156928e6 + 46.069248e6,
     ("row_mul", 4194304, 1024, 4096, 1): 100.979968e6 + 8.389888e6,
-    ("col_inv_crt", 4194304, 1024, 4096, 1): 58.190848e6 + 1.070592e6,
     ("carry_scan", 4194304, 1024, 4096, 1): 15.883008e6,
 }
 

@@ -552,7 +552,7 @@ __device__ __forceinline__ void hcoli_mids(const PlanDev &pd, uint32_t *sm) {
 
 // grid (3 * N2/16, operands): blockIdx.x = 3 * half_tile + prime; x and y 16-byte aligned
 template <uint32_t N1>
-__global__ void __launch_bounds__(256, 2) k_col_fwd_h(const PlanDev pd, const uint32_t *__restrict__ x,
+__global__ void __launch_bounds__(256, 3) k_col_fwd_h(const PlanDev pd, const uint32_t *__restrict__ x,
                                                       uint64_t nx, const uint32_t *__restrict__ y,
                                                       uint64_t ny, uint32_t *X, uint32_t *Y,
                                                       uint32_t *status) {
@@ -592,7 +592,7 @@ __device__ __forceinline__ void hcol_inv_body(const PlanDev &pd, const uint32_t 
 // lanes 16-31 those of half 1), so the chunk digit sums and spills are those of the full-width
 // pass.
 template <uint32_t N1, int MODE>
-__global__ void __launch_bounds__(256, 2) k_col_inv_h(const PlanDev pd, const uint32_t *__restrict__ X,
+__global__ void __launch_bounds__(256, 3) k_col_inv_h(const PlanDev pd, const uint32_t *__restrict__ X,
                                                       uint64_t L, uint32_t *__restrict__ out,
                                                       uint2 *__restrict__ spill, uint64_t *zero,
                                                       uint32_t nzero) {

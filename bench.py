@@ -123,7 +123,6 @@ def _transform_mults(n: int, radices: list[int]) -> float:
 # summarized under profiles/).  Keyed by (stage, N, N1, N2, half-width column tiles); a stage whose
 # kernel changes after the capture must be dropped from this table until it is captured again.
 NCU_TRAFFIC = {
-    ("row_mul", 4194304, 1024, 4096, 1): 100.979968e6 + 8.389888e6,
     ("carry_scan", 4194304, 1024, 4096, 1): 15.883008e6,
 }
 

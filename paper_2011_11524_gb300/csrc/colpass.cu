@@ -54,7 +54,7 @@ __device__ __forceinline__ void colf0_ct(const Stage &st, const uint2 *tw, uint3
             if (PI == 0) a = red2p<PI>(a);  // 10^9 < 4 p0: [0, 10^9) -> [0, 2 p0)
             v[u] = a;
         }
-        dft<PI, 0, (int)R>(v);
+        dft<PI, 0, (int)R, 1>(v);
 #pragma unroll
         for (uint32_t k = 0; k < R; ++k) {
             uint32_t o = v[outpos<(int)R>((int)k)];
@@ -82,7 +82,7 @@ __device__ __forceinline__ void colmid_ct(const Stage &st, const uint2 *tw, uint
 #pragma unroll
         for (uint32_t u = 0; u < R; ++u) v[u] = sm[(base + u * stride) * 32 + lane];
         if (!INV) {
-            dft<PI, 0, (int)R>(v);
+            dft<PI, 0, (int)R, has_tw ? 1 : 0>(v);
 #pragma unroll
             for (uint32_t k = 0; k < R; ++k) {
                 uint32_t o = v[outpos<(int)R>((int)k)];
@@ -133,7 +133,7 @@ __device__ __forceinline__ void colf_last_ct(const PlanDev &pd, const uint32_t *
 #pragma unroll
         for (uint32_t u = 0; u < R; ++u) v[u] = sm[(b * R + u) * 32 + lane];
         const uint2 a = ldtw(A + (uint64_t)b * pd.N2 + n2);
-        dft<PI, 0, (int)R>(v);
+        dft<PI, 0, (int)R, 2>(v);
 #pragma unroll
         for (uint32_t k = 0; k < R; ++k) {
             uint32_t o = v[outpos<(int)R>((int)k)];
@@ -425,7 +425,7 @@ __device__ __forceinline__ void hcolf0(const Stage &st, const uint2 *tw, uint32_
             bad |= (v[u] >= kBase);
             if (PI == 0) v[u] = red2p<PI>(v[u]);  // 10^9 < 4 p0: [0, 10^9) -> [0, 2 p0)
         }
-        dft<PI, 0, (int)R>(v);
+        dft<PI, 0, (int)R, 1>(v);
 #pragma unroll
         for (uint32_t k = 1; k < R; ++k) {
             const uint2 w = ldtw(tw + st.tw + (k - 1) * stride + j);
@@ -451,7 +451,7 @@ __device__ __forceinline__ void hcolmid(const Stage &st, const uint2 *tw, uint32
         uint32_t v[R];
         hload<PI, R, stride>(sm, b0, odd, v);
         if (!INV) {
-            dft<PI, 0, (int)R>(v);
+            dft<PI, 0, (int)R, has_tw ? 1 : 0>(v);
             if (has_tw) {
 #pragma unroll
                 for (uint32_t k = 1; k < R; ++k) {
@@ -492,7 +492,7 @@ __device__ __forceinline__ void hcolf_last(const PlanDev &pd, const uint32_t *sm
         uint32_t v[R];
         hload<PI, R, 1>(sm, hbase<1>(b * R, c), hodd<1>(b * R), v);
         const uint2 a = ldtw(A + (uint64_t)b * pd.N2 + n2);
-        dft<PI, 0, (int)R>(v);
+        dft<PI, 0, (int)R, 2>(v);
 #pragma unroll
         for (uint32_t k = 0; k < R; ++k) {
             uint32_t o = v[outpos<(int)R>((int)k)];

@@ -69,12 +69,14 @@ __device__ __forceinline__ uint32_t mont(uint32_t a, uint32_t b) {
 
 // Gentleman-Sande (DIF) butterfly of Sec. 5.3 on unadjusted values: x' = x + y,
 // y' = (x - y) * xi_16^e.  e == 0 is the factor-1 butterfly of Sec. 5.6 (no multiply).
-template <int PI, int DIR, int E>
+// RS / RD = false leave the sum / the factor-1 difference in [0, 4p) unreduced: allowed only
+// where that output goes straight into a Shoup product (which takes any 32-bit input).
+template <int PI, int DIR, int E, bool RS = true, bool RD = true>
 __device__ __forceinline__ void bfly(uint32_t &x, uint32_t &y) {
-    uint32_t s = red2p<PI>(x + y);
+    uint32_t s = RS ? red2p<PI>(x + y) : x + y;
     uint32_t d = x - y + c_prime[PI].p2;
     if constexpr (E == 0) {
-        d = red2p<PI>(d);
+        if constexpr (RD) d = red2p<PI>(d);
     } else {
         d = shoup<PI>(d, c_prime[PI].w16[DIR][E], c_prime[PI].w16s[DIR][E]);
     }
@@ -95,33 +97,39 @@ __device__ __forceinline__ constexpr int outpos(int k) {
     if constexpr (R == 3) return k; else return brev(k, ilog2c(R));
 }
 
-template <int PI, int DIR, int R, int H, int S, int J>
+// LAZY (last level only): 0 every output reduced to [0, 2p); 1 only output k = 0 (slot 0)
+// reduced, the others left in [0, 4p) for a following twiddle product; 2 no output reduced.
+template <int PI, int DIR, int R, int H, int S, int J, int LAZY>
 __device__ __forceinline__ void dft_level_j(uint32_t (&v)[R]) {
     if constexpr (J < H) {
-        bfly<PI, DIR, J * (8 / H)>(v[S + J], v[S + J + H]);
-        dft_level_j<PI, DIR, R, H, S, J + 1>(v);
+        constexpr bool last = (H == 1);
+        constexpr bool rs = !last || LAZY == 0 || (LAZY == 1 && S + J == 0);
+        constexpr bool rd = !last || LAZY == 0;
+        bfly<PI, DIR, J * (8 / H), rs, rd>(v[S + J], v[S + J + H]);
+        dft_level_j<PI, DIR, R, H, S, J + 1, LAZY>(v);
     }
 }
-template <int PI, int DIR, int R, int H, int S>
+template <int PI, int DIR, int R, int H, int S, int LAZY>
 __device__ __forceinline__ void dft_level_s(uint32_t (&v)[R]) {
     if constexpr (S < R) {
-        dft_level_j<PI, DIR, R, H, S, 0>(v);
-        dft_level_s<PI, DIR, R, H, S + 2 * H>(v);
+        dft_level_j<PI, DIR, R, H, S, 0, LAZY>(v);
+        dft_level_s<PI, DIR, R, H, S + 2 * H, LAZY>(v);
     }
 }
-template <int PI, int DIR, int R, int H>
+template <int PI, int DIR, int R, int H, int LAZY>
 __device__ __forceinline__ void dft_levels(uint32_t (&v)[R]) {
     if constexpr (H >= 1) {
-        dft_level_s<PI, DIR, R, H, 0>(v);
-        dft_levels<PI, DIR, R, H / 2>(v);
+        dft_level_s<PI, DIR, R, H, 0, LAZY>(v);
+        dft_levels<PI, DIR, R, H / 2, LAZY>(v);
     }
 }
 
 // In-register R-point DFT (DIR 0: root xi_R, DIR 1: xi_R^-1), no scaling.  Input in natural
 // order v[0..R); output k is left in v[outpos<R>(k)].  For R = 2^a this is the radix-2 DIF
 // network of Sec. 5.3 without its final bit reversal (Sec. 5.4); the butterfly at level of half
-// size H and offset J uses xi_{2H}^J = xi_16^(J * 8 / H).
-template <int PI, int DIR, int R>
+// size H and offset J uses xi_{2H}^J = xi_16^(J * 8 / H).  Outputs are in [0, 2p), except with
+// LAZY (R = 2^a only; see dft_level_j) where the caller multiplies them by a twiddle next.
+template <int PI, int DIR, int R, int LAZY = 0>
 __device__ __forceinline__ void dft(uint32_t (&v)[R]) {
     if constexpr (R == 3) {
         // X0 = a+b+c, X1 = (a-c) + w(b-c), X2 = (a-b) - w(b-c), with w = xi_3^(+-1)
@@ -133,7 +141,7 @@ __device__ __forceinline__ void dft(uint32_t (&v)[R]) {
         uint32_t x2 = red2p<PI>(red2p<PI>(a - b + p2) - t + p2);
         v[0] = x0; v[1] = x1; v[2] = x2;
     } else {
-        dft_levels<PI, DIR, R, R / 2>(v);
+        dft_levels<PI, DIR, R, R / 2, LAZY>(v);
     }
 }
 

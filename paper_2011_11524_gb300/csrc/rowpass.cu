@@ -52,7 +52,7 @@ __device__ __forceinline__ void fwd_stage_ct(const Stage &st, const uint2 *tw, u
 #pragma unroll
             for (uint32_t u = 0; u < R; ++u) v[u] = sb[swz(base + u * stride)];
         }
-        dft<PI, 0, (int)R>(v);
+        dft<PI, 0, (int)R, has_tw ? 1 : 0>(v);  // outputs k > 0 go straight into the twiddle product
 #pragma unroll
         for (uint32_t k = 0; k < R; ++k) {
             uint32_t o = v[outpos<(int)R>((int)k)];

@@ -93,19 +93,23 @@ __device__ __forceinline__ void colmid_ct(const Stage &st, const uint2 *tw, uint
                 sm[(base + k * stride) * 32 + lane] = o;
             }
         } else {
-            if (has_tw) {
+            // inputs left unreduced by the previous inverse stage: 0 reduced, the others
+            // multiplied by their twiddles; outputs unreduced unless this is the last stage
+            static_assert(has_tw, "every inverse column stage after the first has twiddles");
+            v[0] = red2p<PI>(v[0]);
 #pragma unroll
-                for (uint32_t k = 1; k < R; ++k) {
-                    const uint2 w = ldtw(tw + st.twi + (k - 1) * stride + j);
-                    v[k] = shoup<PI>(v[k], w.x, w.y);
-                }
+            for (uint32_t k = 1; k < R; ++k) {
+                const uint2 w = ldtw(tw + st.twi + (k - 1) * stride + j);
+                v[k] = shoup<PI>(v[k], w.x, w.y);
             }
-            dft<PI, 1, (int)R>(v);
+            if (final_reduce) {
+                dft<PI, 1, (int)R>(v);
 #pragma unroll
-            for (uint32_t u = 0; u < R; ++u) {
-                uint32_t o = v[outpos<(int)R>((int)u)];
-                if (final_reduce) o = red1p<PI>(o);
-                sm[(base + u * stride) * 32 + lane] = o;
+                for (uint32_t u = 0; u < R; ++u) sm[(base + u * stride) * 32 + lane] = red1p<PI>(v[outpos<(int)R>((int)u)]);
+            } else {
+                dft<PI, 1, (int)R, 2>(v);
+#pragma unroll
+                for (uint32_t u = 0; u < R; ++u) sm[(base + u * stride) * 32 + lane] = v[outpos<(int)R>((int)u)];
             }
         }
     }
@@ -161,7 +165,7 @@ __device__ __forceinline__ void coli_first_ct(const PlanDev &pd, uint32_t *sm, u
             if (k > 0) o = shoup<PI>(o, q[k].x, q[k].y);
             v[k] = shoup<PI>(o, a.x, a.y);
         }
-        dft<PI, 1, (int)R>(v);
+        dft<PI, 1, (int)R, 2>(v);  // the next inverse stage reduces / untwiddles its inputs
 #pragma unroll
         for (uint32_t u = 0; u < R; ++u) sm[(b * R + u) * 32 + lane] = v[outpos<(int)R>((int)u)];
     }
@@ -460,17 +464,20 @@ __device__ __forceinline__ void hcolmid(const Stage &st, const uint2 *tw, uint32
                 }
             }
         } else {
-            if (has_tw) {
+            // as colmid_ct: input 0 reduced, the others untwiddled; outputs unreduced unless last
+            static_assert(has_tw, "every inverse column stage after the first has twiddles");
+            v[0] = red2p<PI>(v[0]);
 #pragma unroll
-                for (uint32_t k = 1; k < R; ++k) {
-                    const uint2 w = ldtw(tw + st.twi + (k - 1) * stride + j);
-                    v[k] = shoup<PI>(v[k], w.x, w.y);
-                }
+            for (uint32_t k = 1; k < R; ++k) {
+                const uint2 w = ldtw(tw + st.twi + (k - 1) * stride + j);
+                v[k] = shoup<PI>(v[k], w.x, w.y);
             }
-            dft<PI, 1, (int)R>(v);
             if (final_reduce) {
+                dft<PI, 1, (int)R>(v);
 #pragma unroll
                 for (uint32_t u = 0; u < R; ++u) v[u] = red1p<PI>(v[u]);
+            } else {
+                dft<PI, 1, (int)R, 2>(v);
             }
         }
         hstore_out<PI, R, stride>(sm, b0, odd, v);
@@ -525,7 +532,7 @@ __device__ __forceinline__ void hcoli_first(const PlanDev &pd, uint32_t *sm, uin
             if (k > 0) o = shoup<PI>(o, q[k].x, q[k].y);
             v[k] = shoup<PI>(o, a.x, a.y);
         }
-        dft<PI, 1, (int)R>(v);
+        dft<PI, 1, (int)R, 2>(v);  // the next inverse stage reduces / untwiddles its inputs
         hstore_out<PI, R, 1>(sm, b0, odd, v);
     }
 }

@@ -77,14 +77,18 @@ __device__ __forceinline__ void inv_stage_ct(const Stage &st, const uint2 *tw, u
         uint32_t v[R];
 #pragma unroll
         for (uint32_t k = 0; k < R; ++k) v[k] = sb[swz(base + k * stride)];
-        if (has_tw) {
+        // The previous inverse stage left its outputs unreduced: input 0 is reduced here, the
+        // others go through their twiddle product.  This stage's outputs stay unreduced too: the
+        // next inverse stage does the same, and after the last one the inverse column pass
+        // multiplies every input by a four-step twiddle.
+        static_assert(has_tw, "every inverse row stage after the center has twiddles");
+        v[0] = red2p<PI>(v[0]);
 #pragma unroll
-            for (uint32_t k = 1; k < R; ++k) {
-                const uint2 w = ldtw(tw + st.twi + (k - 1) * stride + j);
-                v[k] = shoup<PI>(v[k], w.x, w.y);
-            }
+        for (uint32_t k = 1; k < R; ++k) {
+            const uint2 w = ldtw(tw + st.twi + (k - 1) * stride + j);
+            v[k] = shoup<PI>(v[k], w.x, w.y);
         }
-        dft<PI, 1, (int)R>(v);
+        dft<PI, 1, (int)R, 2>(v);
         if (gout) {
 #pragma unroll
             for (uint32_t u = 0; u < R; ++u) gout[base + u * stride] = v[outpos<(int)R>((int)u)];
@@ -126,7 +130,7 @@ __device__ __forceinline__ void row_core_ct(const PlanDev &pd, uint32_t *sx, uin
     using S = Pow2Sched<N>;
     const uint2 *tw = pd.tw[PI];
     fwd_stages_ct<PI, N, 0>(pd, tw, sx, sy, xin, yin, SQR ? 1u : 2u);
-    row_center<PI, (int)S::radix(S::NS - 1), SQR>(sx, sy, N);
+    row_center_lazy<PI, (int)S::radix(S::NS - 1), SQR, true>(sx, sy, N);
     __syncthreads();
     inv_stages_ct<PI, N, S::NS - 2>(pd, tw, sx, xout);
 }

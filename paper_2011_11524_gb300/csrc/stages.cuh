@@ -416,8 +416,10 @@ __device__ __forceinline__ void row_inv_stage(const Stage &st, const uint2 *tw, 
 }
 
 // Last forward stage (m == R) of every operand, pointwise product (or square), first inverse stage.
-template <int PI, int R, bool SQR>
-__device__ __forceinline__ void row_center(uint32_t *sx, const uint32_t *sy, uint32_t n) {
+// LAZY_OUT: the inverse DFT's outputs stay in [0, 4p) (the next inverse stage reduces its
+// untwiddled input k = 0 and multiplies the others by their twiddles first).
+template <int PI, int R, bool SQR, bool LAZY_OUT>
+__device__ __forceinline__ void row_center_lazy(uint32_t *sx, const uint32_t *sy, uint32_t n) {
     const uint32_t groups = n / R;
     for (uint32_t b = threadIdx.x; b < groups; b += blockDim.x) {
         uint32_t v[2][R];
@@ -434,10 +436,15 @@ __device__ __forceinline__ void row_center(uint32_t *sx, const uint32_t *sy, uin
             const uint32_t a = v[0][outpos<R>(k)];
             z[k] = mont<PI>(a, SQR ? a : v[1][outpos<R>(k)]);
         }
-        dft<PI, 1, R>(z);
+        dft<PI, 1, R, LAZY_OUT ? 2 : 0>(z);
 #pragma unroll
         for (int u = 0; u < R; ++u) sx[swz(b * R + u)] = z[outpos<R>(u)];
     }
+}
+
+template <int PI, int R, bool SQR>
+__device__ __forceinline__ void row_center(uint32_t *sx, const uint32_t *sy, uint32_t n) {
+    row_center_lazy<PI, R, SQR, false>(sx, sy, n);
 }
 
 // The fused row pass on one row: inputs read from xin / yin (plain layout: global memory, or a

@@ -30,11 +30,24 @@ struct Pow2Sched {
     }
 };
 
+// Working buffers of the specialized pass: one padding word after every 16 (index a + a/16, N + N/16
+// words per row).  Every stage's rows base + u*s (s a multiple of 16, or the 16 consecutive rows
+// of the center) then sit at pidx(base) + u*(s + s/16): one address per group, immediate offsets
+// per row.  Banks: conflict-free for s = 16 and the center; one lane pair of a warp shares a bank
+// in the stages with s >= 256 (a CPU check over every access of the four schedules).
+template <uint32_t N>
+struct RowPad {
+    static constexpr uint32_t NP = N + N / 16;
+};
+__device__ __forceinline__ uint32_t pidx(uint32_t a) { return a + (a >> 4); }
+
 template <int PI, uint32_t R, uint32_t M, uint32_t N>
 __device__ __forceinline__ void fwd_stage_ct(const Stage &st, const uint2 *tw, uint32_t *sx,
                                              uint32_t *sy, const uint32_t *gx, const uint32_t *gy,
                                              bool from_plain, uint32_t nops) {
     constexpr uint32_t stride = M / R;
+    constexpr uint32_t pstride = stride + stride / 16;
+    static_assert(stride % 16 == 0, "padded rows need strides that are multiples of 16");
     constexpr uint32_t per_op = N / R;
     constexpr bool has_tw = M > R;
     for (uint32_t g = threadIdx.x; g < per_op * nops; g += blockDim.x) {
@@ -43,6 +56,7 @@ __device__ __forceinline__ void fwd_stage_ct(const Stage &st, const uint2 *tw, u
         uint32_t *sb = second ? sy : sx;
         const uint32_t blk = gg / stride, j = gg % stride;
         const uint32_t base = blk * M + j;
+        uint32_t *pb = sb + pidx(base);
         uint32_t v[R];
         if (from_plain) {
             const uint32_t *src = second ? gy : gx;
@@ -50,7 +64,7 @@ __device__ __forceinline__ void fwd_stage_ct(const Stage &st, const uint2 *tw, u
             for (uint32_t u = 0; u < R; ++u) v[u] = src[base + u * stride];
         } else {
 #pragma unroll
-            for (uint32_t u = 0; u < R; ++u) v[u] = sb[swz(base + u * stride)];
+            for (uint32_t u = 0; u < R; ++u) v[u] = pb[u * pstride];
         }
         dft<PI, 0, (int)R, has_tw ? 1 : 0>(v);  // outputs k > 0 go straight into the twiddle product
 #pragma unroll
@@ -60,7 +74,7 @@ __device__ __forceinline__ void fwd_stage_ct(const Stage &st, const uint2 *tw, u
                 const uint2 w = ldtw(tw + st.tw + (k - 1) * stride + j);
                 o = shoup<PI>(o, w.x, w.y);
             }
-            sb[swz(base + k * stride)] = o;
+            pb[k * pstride] = o;
         }
     }
 }
@@ -69,14 +83,17 @@ template <int PI, uint32_t R, uint32_t M, uint32_t N>
 __device__ __forceinline__ void inv_stage_ct(const Stage &st, const uint2 *tw, uint32_t *sb,
                                              uint32_t *gout) {
     constexpr uint32_t stride = M / R;
+    constexpr uint32_t pstride = stride + stride / 16;
+    static_assert(stride % 16 == 0, "padded rows need strides that are multiples of 16");
     constexpr uint32_t groups = N / R;
     constexpr bool has_tw = M > R;
     for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
         const uint32_t blk = g / stride, j = g % stride;
         const uint32_t base = blk * M + j;
+        uint32_t *pb = sb + pidx(base);
         uint32_t v[R];
 #pragma unroll
-        for (uint32_t k = 0; k < R; ++k) v[k] = sb[swz(base + k * stride)];
+        for (uint32_t k = 0; k < R; ++k) v[k] = pb[k * pstride];
         // The previous inverse stage left its outputs unreduced: input 0 is reduced here, the
         // others go through their twiddle product.  This stage's outputs stay unreduced too: the
         // next inverse stage does the same, and after the last one the inverse column pass
@@ -94,7 +111,7 @@ __device__ __forceinline__ void inv_stage_ct(const Stage &st, const uint2 *tw, u
             for (uint32_t u = 0; u < R; ++u) gout[base + u * stride] = v[outpos<(int)R>((int)u)];
         } else {
 #pragma unroll
-            for (uint32_t u = 0; u < R; ++u) sb[swz(base + u * stride)] = v[outpos<(int)R>((int)u)];
+            for (uint32_t u = 0; u < R; ++u) pb[u * pstride] = v[outpos<(int)R>((int)u)];
         }
     }
 }
@@ -123,6 +140,33 @@ __device__ __forceinline__ void inv_stages_ct(const PlanDev &pd, const uint2 *tw
     }
 }
 
+// Last forward stage of x (and y), pointwise Montgomery product, first inverse stage, on the 16
+// consecutive rows 16b .. 16b+15 (padded index 17b + u); the inverse outputs stay unreduced.
+template <int PI, bool SQR>
+__device__ __forceinline__ void row_center_ct(uint32_t *sx, const uint32_t *sy, uint32_t groups) {
+    constexpr int R = 16;
+    for (uint32_t b = threadIdx.x; b < groups; b += blockDim.x) {
+        uint32_t v[2][R];
+#pragma unroll
+        for (int op = 0; op < (SQR ? 1 : 2); ++op) {
+            const uint32_t *sb = (op ? sy : sx) + 17 * b;
+#pragma unroll
+            for (int u = 0; u < R; ++u) v[op][u] = sb[u];
+            dft<PI, 0, R>(v[op]);
+        }
+        uint32_t z[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const uint32_t a = v[0][outpos<R>(k)];
+            z[k] = mont<PI>(a, SQR ? a : v[1][outpos<R>(k)]);
+        }
+        dft<PI, 1, R, 2>(z);
+        uint32_t *sb = sx + 17 * b;
+#pragma unroll
+        for (int u = 0; u < R; ++u) sb[u] = z[outpos<R>(u)];
+    }
+}
+
 template <int PI, uint32_t N, bool SQR>
 __device__ __forceinline__ void row_core_ct(const PlanDev &pd, uint32_t *sx, uint32_t *sy,
                                             const uint32_t *xin, const uint32_t *yin,
@@ -130,7 +174,8 @@ __device__ __forceinline__ void row_core_ct(const PlanDev &pd, uint32_t *sx, uin
     using S = Pow2Sched<N>;
     const uint2 *tw = pd.tw[PI];
     fwd_stages_ct<PI, N, 0>(pd, tw, sx, sy, xin, yin, SQR ? 1u : 2u);
-    row_center_lazy<PI, (int)S::radix(S::NS - 1), SQR, true>(sx, sy, N);
+    static_assert(S::radix(S::NS - 1) == 16, "the center stage is radix 16");
+    row_center_ct<PI, SQR>(sx, sy, N / 16);
     __syncthreads();
     inv_stages_ct<PI, N, S::NS - 2>(pd, tw, sx, xout);
 }
@@ -144,16 +189,17 @@ __global__ void __launch_bounds__(256) k_row_ct(const PlanDev pd, uint32_t *X, c
     const int pi = blockIdx.y;
     uint32_t *xr = X + (uint64_t)pi * pd.N + (uint64_t)row * N;
     const uint32_t *yr = SQR ? nullptr : Y + (uint64_t)pi * pd.N + (uint64_t)row * N;
-    DMUL_PRIME_SWITCH(pi, (row_core_ct<PI, N, SQR>(pd, sm, sm + N, xr, yr, xr)));
+    DMUL_PRIME_SWITCH(pi, (row_core_ct<PI, N, SQR>(pd, sm, sm + RowPad<N>::NP, xr, yr, xr)));
 }
 
 // persistent TMA-fed form (see row_mul_tma_body in stages.cuh for the protocol)
 template <int PI, uint32_t N, bool SQR>
 __device__ __forceinline__ void row_tma_ct_body(const PlanDev &pd, uint32_t *sm, uint32_t *X,
                                                 const uint32_t *Y, uint32_t *status) {
+    constexpr uint32_t NP = RowPad<N>::NP;
     uint32_t *land = sm;
-    uint32_t *sx = sm + 4 * N, *sy = sm + 5 * N;
-    uint64_t *bar = (uint64_t *)(sm + 6 * N);
+    uint32_t *sx = sm + 4 * N, *sy = sm + 4 * N + NP;
+    uint64_t *bar = (uint64_t *)(sm + 4 * N + 2 * NP);  // an even word offset: 8-byte aligned
     const uint32_t G = gridDim.x;
     const uint64_t base = (uint64_t)PI * pd.N;
     constexpr uint32_t bytes = N * 4;
@@ -204,6 +250,10 @@ __global__ void __launch_bounds__(256) k_row_tma_ct(const PlanDev pd, uint32_t *
     DMUL_PRIME_SWITCH(pi, (row_tma_ct_body<PI, N, SQR>(pd, sm, X, Y, status)));
 }
 
+// landing area (two rows of x and y, plain) + padded working buffers + two mbarriers
+template <uint32_t N>
+static constexpr size_t row_tma_ct_smem() { return ((size_t)4 * N + 2 * RowPad<N>::NP) * 4 + 16; }
+
 template <uint32_t N>
 static bool schedule_matches(const PlanDev &pd) {
     using S = Pow2Sched<N>;
@@ -218,12 +268,12 @@ static cudaError_t launch_ct(const PlanDev &pd, uint32_t *X, const uint32_t *Y, 
                              uint32_t *status, cudaStream_t s) {
     if (pd.row_tma) {
         dim3 grid(pd.row_grid ? pd.row_grid : 256, kPrimes);
-        const size_t smem = (size_t)6 * N * 4 + 16;
+        const size_t smem = row_tma_ct_smem<N>();
         if (square) return launch_pdl(k_row_tma_ct<N, true>, grid, dim3(pd.row_threads), smem, s, 1, pd, X, Y, status);
         return launch_pdl(k_row_tma_ct<N, false>, grid, dim3(pd.row_threads), smem, s, 1, pd, X, Y, status);
     } else {
         dim3 grid(pd.N1, kPrimes);
-        const size_t smem = (size_t)(square ? 1 : 2) * N * 4;
+        const size_t smem = (size_t)(square ? 1 : 2) * RowPad<N>::NP * 4;
         if (square) return launch_pdl(k_row_ct<N, true>, grid, dim3(pd.row_threads), smem, s, 1, pd, X, Y);
         return launch_pdl(k_row_ct<N, false>, grid, dim3(pd.row_threads), smem, s, 1, pd, X, Y);
     }
@@ -253,7 +303,7 @@ cudaError_t launch_row_pass_ct(const PlanDev &pd, uint32_t *X, const uint32_t *Y
 template <uint32_t N>
 static cudaError_t attrs_ct() {
     cudaError_t e;
-    const int plain = 2 * N * 4, tma = 6 * N * 4 + 16;
+    const int plain = 2 * RowPad<N>::NP * 4, tma = (int)row_tma_ct_smem<N>();
     if ((e = cudaFuncSetAttribute(k_row_ct<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, plain)))
         return e;
     if ((e = cudaFuncSetAttribute(k_row_ct<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, plain)))

@@ -357,12 +357,18 @@ namespace dml {
 
 __device__ __forceinline__ uint32_t hphys(uint32_t r) { return r ^ ((r >> 4) & 1u); }
 
-// Stage the N1 x 16 tile at column j0 (16-byte aligned source; words >= n read as 0).
-__device__ __forceinline__ void htile_load_async(uint32_t *sm, const uint32_t *__restrict__ src,
-                                                 uint64_t n, uint32_t N1, uint32_t N2, uint32_t j0) {
-    const uint32_t chunks = N1 * 4;  // 16-byte chunks: 4 per 16-word row
+// Issue (without waiting) the copies of the half tile's rows r with HALF * K/2 <= r mod K <
+// (HALF + 1) * K/2 as one cp.async group (words >= n read as 0; src 16-byte aligned).  With
+// K = N1 these are rows [0, N1/2) or [N1/2, N1): the groups of 16 consecutive rows of the inverse
+// first stage's first or second half.
+template <uint32_t N1, uint32_t K, uint32_t HALF>
+__device__ __forceinline__ void htile_issue(uint32_t *sm, const uint32_t *__restrict__ src, uint64_t n,
+                                            uint32_t N2, uint32_t j0) {
+    constexpr uint32_t per = K / 2;
+    constexpr uint32_t chunks = (N1 / K) * per * 4;  // 16-byte chunks: 4 per 16-word row
     for (uint32_t idx = threadIdx.x; idx < chunks; idx += blockDim.x) {
-        const uint32_t row = idx >> 2, q = idx & 3;
+        const uint32_t rr = idx >> 2, q = idx & 3;
+        const uint32_t row = (rr / per) * K + HALF * per + rr % per;
         const uint64_t g = (uint64_t)row * N2 + j0 + 4 * q;
         const uint32_t valid = g >= n ? 0u : (n - g >= 4 ? 4u : (uint32_t)(n - g));
         const uint32_t *s = valid ? src + g : src;
@@ -370,7 +376,11 @@ __device__ __forceinline__ void htile_load_async(uint32_t *sm, const uint32_t *_
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(s), "r"(valid * 4)
                      : "memory");
     }
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait_sync() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
     __syncthreads();
 }
 
@@ -512,15 +522,13 @@ __device__ __forceinline__ void hcolf_last(const PlanDev &pd, const uint32_t *sm
 
 // first inverse stage on the staged half tile: inverse four-step twiddle, inverse DFT
 template <int PI, uint32_t R, uint32_t N1>
-__device__ __forceinline__ void hcoli_first(const PlanDev &pd, uint32_t *sm, uint32_t n2) {
+__device__ __forceinline__ void hcoli_first(const PlanDev &pd, uint32_t *sm, uint32_t n2, const uint2 (&q)[R],
+                                            uint32_t b_lo, uint32_t b_hi) {
     static_assert(R == 16, "half tiles need a last stage of radix 16");
-    constexpr uint32_t nb = N1 / R;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t c = lane & 15, h = lane >> 4;
     const uint2 *A = pd.tw[PI] + pd.offAi;
-    uint2 q[R];
-    load_q<PI, R>(pd.tw[PI] + pd.offQi, pd.N2, n2, q);
-    for (uint32_t b = 2 * warp + h; b < nb; b += 2 * nw) {
+    for (uint32_t b = b_lo + 2 * warp + h; b < b_hi; b += 2 * nw) {
         const uint32_t b0 = hbase<1>(b * R, c);
         const int odd = hodd<1>(b * R);
         uint32_t v[R];
@@ -575,7 +583,11 @@ __global__ void __launch_bounds__(256, 3) k_col_fwd_h(const PlanDev pd, const ui
     uint32_t *dst = (second ? Y : X) + (uint64_t)pi * pd.N;
     const uint32_t n2 = j0 + (threadIdx.x & 15);
     uint32_t bad = 0;
-    htile_load_async(sm, src, n, N1, pd.N2, j0);
+    // the whole tile, then the first stage (starting the first stage on half the tile measured
+    // slower here than waiting for all of it: three CTAs per SM already overlap loads)
+    htile_issue<N1, N1, 0>(sm, src, n, pd.N2, j0);
+    htile_issue<N1, N1, 1>(sm, src, n, pd.N2, j0);
+    cp_async_wait_sync<0>();
     DMUL_PRIME_SWITCH(pi, (hcolf0<PI, S::radix(0), N1>(pd.cs[0], pd.tw[PI], sm, bad)));
     if (pi == 0 && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, kStatusInvalid);
     __syncthreads();
@@ -587,8 +599,18 @@ template <int PI, uint32_t N1>
 __device__ __forceinline__ void hcol_inv_body(const PlanDev &pd, const uint32_t *__restrict__ src,
                                               uint32_t *sm, uint32_t j0) {
     using S = ColSched<N1>;
-    htile_load_async(sm, src, pd.N, N1, pd.N2, j0);
-    hcoli_first<PI, S::radix(S::NS - 1), N1>(pd, sm, j0 + (threadIdx.x & 15));
+    constexpr uint32_t R = S::radix(S::NS - 1), nb = N1 / R;
+    const uint32_t n2 = j0 + (threadIdx.x & 15);
+    // the tile in two halves of rows; the four-step Q twiddles load while the copies fly, and the
+    // first stage starts on the first half while the second half lands
+    htile_issue<N1, N1, 0>(sm, src, pd.N, pd.N2, j0);
+    htile_issue<N1, N1, 1>(sm, src, pd.N, pd.N2, j0);
+    uint2 q[R];
+    load_q<PI, R>(pd.tw[PI] + pd.offQi, pd.N2, n2, q);
+    cp_async_wait_sync<1>();
+    hcoli_first<PI, R, N1>(pd, sm, n2, q, 0, nb / 2);
+    cp_async_wait_sync<0>();
+    hcoli_first<PI, R, N1>(pd, sm, n2, q, nb / 2, nb);
     __syncthreads();
     hcoli_mids<PI, N1, S::NS - 2>(pd, sm);
 }
@@ -627,6 +649,7 @@ __global__ void __launch_bounds__(256, 3) k_col_inv_h(const PlanDev pd, const ui
     const uint32_t *s0 = cluster.map_shared_rank(sm, kPrimes * hl + 0);
     const uint32_t *s1 = cluster.map_shared_rank(sm, kPrimes * hl + 1);
     const uint32_t *s2 = cluster.map_shared_rank(sm, kPrimes * hl + 2);
+#pragma unroll 2
     for (uint32_t r = rank + 2 * kPrimes * warp; r < N1; r += 2 * kPrimes * nw) {
         const uint64_t k0 = (uint64_t)r * pd.N2 + t0;  // first coefficient of this chunk
         if (k0 >= L) continue;                          // warp-uniform

@@ -638,6 +638,7 @@ int dmul_init(dmul_ctx **out, const dmul_config *cfg) {
     CK(init_kernel_attributes_rowpass());
     CK(init_kernel_attributes_colpass());
     CK(init_kernel_attributes_colhalf());
+    CK(init_kernel_attributes_colbatch());
     int rc = dev_alloc(c.get(), (void **)&c->status, 256);
     if (rc) return rc;
     CK(cudaMemset(c->status, 0, 256));

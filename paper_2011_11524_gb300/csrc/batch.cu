@@ -464,9 +464,19 @@ static int launch_work(dmul_ctx *c, BatchState *b, const std::vector<GroupLaunch
         PlanEntry *pe;
         int rc = get_plan(c, G.N, &pe);
         if (rc) return rc;
-        if (launch_col_fwd_b(pe->pd, jd, (int)G.count, status, st) != cudaSuccess) return DMUL_ERR_CUDA;
-        if (launch_row_mul_b(pe->pd, jd, (int)G.count, st) != cudaSuccess) return DMUL_ERR_CUDA;
-        if (launch_col_inv_b(pe->pd, jd, (int)G.count, st) != cudaSuccess) return DMUL_ERR_CUDA;
+        const PlanDev &pd = pe->pd;
+        // the specialized passes where the plan has their schedule (the column passes also need
+        // 16-byte aligned operands), else the generic ones
+        const bool cs = G.aligned && col_pass_specialized(pd), rs = row_pass_specialized(pd);
+        if ((cs ? launch_col_fwd_bs(pd, jd, (int)G.count, status, st)
+                : launch_col_fwd_b(pd, jd, (int)G.count, status, st)) != cudaSuccess)
+            return DMUL_ERR_CUDA;
+        if ((rs ? launch_row_pass_ct_b(pd, jd, (int)G.count, st) : launch_row_mul_b(pd, jd, (int)G.count, st)) !=
+            cudaSuccess)
+            return DMUL_ERR_CUDA;
+        if ((col_pass_specialized(pd) ? launch_col_inv_bs(pd, jd, (int)G.count, st)
+                                      : launch_col_inv_b(pd, jd, (int)G.count, st)) != cudaSuccess)
+            return DMUL_ERR_CUDA;
         if (launch_carry_b(jd, (int)G.count, G.maxtiles, status, st) != cudaSuccess) return DMUL_ERR_CUDA;
     }
     return DMUL_OK;
@@ -630,8 +640,13 @@ int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count,
     }
     for (auto &G : groups) {
         uint32_t mt = 0;
-        for (size_t i = G.first; i < G.first + G.count; ++i) mt = std::max(mt, b->hjobs[i].ntiles);
+        bool al = true;
+        for (size_t i = G.first; i < G.first + G.count; ++i) {
+            mt = std::max(mt, b->hjobs[i].ntiles);
+            al = al && ((uintptr_t)b->hjobs[i].x & 15) == 0 && ((uintptr_t)b->hjobs[i].y & 15) == 0;
+        }
         G.maxtiles = mt;
+        G.aligned = al;
     }
     // plans are built outside any capture
     for (auto &G : groups) {
@@ -677,7 +692,7 @@ int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count,
         return DMUL_OK;
     }
     std::vector<std::tuple<int, uint64_t, size_t>> key;
-    for (auto &G : groups) key.emplace_back(G.small ? 1 : 0, G.N, G.count);
+    for (auto &G : groups) key.emplace_back((G.small ? 1 : 0) | (G.aligned ? 2 : 0), G.N, G.count);
     for (size_t i = 0; i < count; ++i) key.emplace_back(2, (uint64_t)b->hjobs[i].square, b->hjobs[i].ntiles);
     auto it = b->graphs.find(key);
     if (it == b->graphs.end()) {

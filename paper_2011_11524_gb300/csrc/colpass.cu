@@ -237,6 +237,21 @@ __global__ void __launch_bounds__(512) k_col_fwd_ct(const PlanDev pd, const uint
     DMUL_PRIME_SWITCH(pi, (col_fwd_ct_body<PI, N1>(pd, sm, src, n, dst, tile, status)));
 }
 
+// the same for a batch of jobs of one transform length (job = blockIdx.z)
+template <uint32_t N1>
+__global__ void __launch_bounds__(512) k_col_fwd_ct_b(const PlanDev pd, const JobDev *__restrict__ jobs,
+                                                      uint32_t *status) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    const JobDev &J = jobs[blockIdx.z];
+    const bool second = blockIdx.y != 0;
+    if (second && J.square) return;
+    const int pi = blockIdx.x % kPrimes;
+    const uint32_t tile = blockIdx.x / kPrimes;
+    uint32_t *dst = (second ? J.Y : J.X) + (uint64_t)pi * pd.N;
+    DMUL_PRIME_SWITCH(pi, (col_fwd_ct_body<PI, N1>(pd, sm, second ? J.y : J.x, second ? J.ny : J.nx, dst,
+                                                   tile, status)));
+}
+
 // cluster of three CTAs (rank = prime) per 32-column tile, then the CRT epilogue
 template <uint32_t N1, int MODE>
 __global__ void __launch_bounds__(512) k_col_inv_ct(const PlanDev pd, const uint32_t *__restrict__ X,
@@ -252,6 +267,17 @@ __global__ void __launch_bounds__(512) k_col_inv_ct(const PlanDev pd, const uint
     const uint32_t *src = X + (uint64_t)pi * pd.N;
     DMUL_PRIME_SWITCH(pi, (col_inv_ct_body<PI, N1>(pd, src, sm, n2)));
     col_crt_epilogue(pd, L, MODE, out, spill, sm);
+}
+
+// the same (digit sums) for a batch of jobs of one transform length (job = blockIdx.z)
+template <uint32_t N1>
+__global__ void __launch_bounds__(512) k_col_inv_ct_b(const PlanDev pd, const JobDev *__restrict__ jobs) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    const JobDev &J = jobs[blockIdx.z];
+    const int pi = (int)cg::this_cluster().block_rank();
+    const uint32_t n2 = (blockIdx.x / kPrimes) * 32 + (threadIdx.x & 31);
+    DMUL_PRIME_SWITCH(pi, (col_inv_ct_body<PI, N1>(pd, J.X + (uint64_t)pi * pd.N, sm, n2)));
+    col_crt_epilogue(pd, J.L, kInvDigits, J.z, J.spill, sm);
 }
 
 template <uint32_t N1>
@@ -567,20 +593,10 @@ __device__ __forceinline__ void hcoli_mids(const PlanDev &pd, uint32_t *sm) {
 
 // grid (3 * N2/16, operands): blockIdx.x = 3 * half_tile + prime; x and y 16-byte aligned
 template <uint32_t N1>
-__global__ void __launch_bounds__(256, 3) k_col_fwd_h(const PlanDev pd, const uint32_t *__restrict__ x,
-                                                      uint64_t nx, const uint32_t *__restrict__ y,
-                                                      uint64_t ny, uint32_t *X, uint32_t *Y,
-                                                      uint32_t *status) {
+__device__ __forceinline__ void col_fwd_h_run(const PlanDev &pd, uint32_t *sm, const uint32_t *__restrict__ src,
+                                              uint64_t n, uint32_t *__restrict__ dst, uint32_t j0, int pi,
+                                              uint32_t *status) {
     using S = ColSched<N1>;
-    extern __shared__ __align__(16) uint32_t sm[];
-    pdl_trigger();
-    pdl_wait();
-    const int pi = blockIdx.x % kPrimes;
-    const uint32_t j0 = (blockIdx.x / kPrimes) * 16;
-    const bool second = blockIdx.y != 0;
-    const uint32_t *src = second ? y : x;
-    const uint64_t n = second ? ny : nx;
-    uint32_t *dst = (second ? Y : X) + (uint64_t)pi * pd.N;
     const uint32_t n2 = j0 + (threadIdx.x & 15);
     uint32_t bad = 0;
     // the whole tile, then the first stage (starting the first stage on half the tile measured
@@ -593,6 +609,33 @@ __global__ void __launch_bounds__(256, 3) k_col_fwd_h(const PlanDev pd, const ui
     __syncthreads();
     DMUL_PRIME_SWITCH(pi, (hcolf_mids<PI, N1, 1>(pd, sm)));
     DMUL_PRIME_SWITCH(pi, (hcolf_last<PI, S::radix(S::NS - 1), N1>(pd, sm, dst, n2)));
+}
+
+template <uint32_t N1>
+__global__ void __launch_bounds__(256, 3) k_col_fwd_h(const PlanDev pd, const uint32_t *__restrict__ x,
+                                                      uint64_t nx, const uint32_t *__restrict__ y,
+                                                      uint64_t ny, uint32_t *X, uint32_t *Y,
+                                                      uint32_t *status) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    pdl_trigger();
+    pdl_wait();
+    const int pi = blockIdx.x % kPrimes;
+    const bool second = blockIdx.y != 0;
+    col_fwd_h_run<N1>(pd, sm, second ? y : x, second ? ny : nx, (second ? Y : X) + (uint64_t)pi * pd.N,
+                      (blockIdx.x / kPrimes) * 16, pi, status);
+}
+
+// the same for a batch of jobs of one transform length (job = blockIdx.z)
+template <uint32_t N1>
+__global__ void __launch_bounds__(256, 3) k_col_fwd_h_b(const PlanDev pd, const JobDev *__restrict__ jobs,
+                                                        uint32_t *status) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    const JobDev &J = jobs[blockIdx.z];
+    const bool second = blockIdx.y != 0;
+    if (second && J.square) return;
+    const int pi = blockIdx.x % kPrimes;
+    col_fwd_h_run<N1>(pd, sm, second ? J.y : J.x, second ? J.ny : J.nx,
+                      (second ? J.Y : J.X) + (uint64_t)pi * pd.N, (blockIdx.x / kPrimes) * 16, pi, status);
 }
 
 template <int PI, uint32_t N1>
@@ -621,14 +664,9 @@ __device__ __forceinline__ void hcol_inv_body(const PlanDev &pd, const uint32_t 
 // lanes 16-31 those of half 1), so the chunk digit sums and spills are those of the full-width
 // pass.
 template <uint32_t N1, int MODE>
-__global__ void __launch_bounds__(256, 3) k_col_inv_h(const PlanDev pd, const uint32_t *__restrict__ X,
-                                                      uint64_t L, uint32_t *__restrict__ out,
-                                                      uint2 *__restrict__ spill, uint64_t *zero,
-                                                      uint32_t nzero) {
-    extern __shared__ __align__(16) uint32_t sm[];
-    pdl_trigger();
-    pdl_wait();
-    zero_words(zero, nzero);
+__device__ __forceinline__ void col_inv_h_run(const PlanDev &pd, uint32_t *sm, const uint32_t *__restrict__ X,
+                                              uint64_t L, uint32_t *__restrict__ out,
+                                              uint2 *__restrict__ spill) {
     cg::cluster_group cluster = cg::this_cluster();
     const uint32_t rank = cluster.block_rank();
     const uint32_t half = rank / kPrimes, pi = rank % kPrimes;
@@ -668,6 +706,26 @@ __global__ void __launch_bounds__(256, 3) k_col_inv_h(const PlanDev pd, const ui
         }
     }
     cluster.sync();
+}
+
+template <uint32_t N1, int MODE>
+__global__ void __launch_bounds__(256, 3) k_col_inv_h(const PlanDev pd, const uint32_t *__restrict__ X,
+                                                      uint64_t L, uint32_t *__restrict__ out,
+                                                      uint2 *__restrict__ spill, uint64_t *zero,
+                                                      uint32_t nzero) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    pdl_trigger();
+    pdl_wait();
+    zero_words(zero, nzero);
+    col_inv_h_run<N1, MODE>(pd, sm, X, L, out, spill);
+}
+
+// the same (digit sums) for a batch of jobs of one transform length (job = blockIdx.z)
+template <uint32_t N1>
+__global__ void __launch_bounds__(256, 3) k_col_inv_h_b(const PlanDev pd, const JobDev *__restrict__ jobs) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    const JobDev &J = jobs[blockIdx.z];
+    col_inv_h_run<N1, kInvDigits>(pd, sm, J.X, J.L, J.z, J.spill);
 }
 
 template <uint32_t N1>
@@ -735,6 +793,82 @@ cudaError_t init_kernel_attributes_colhalf() {
     if ((e = attrs_col_h<768>())) return e;
     if ((e = attrs_col_h<1024>())) return e;
     return attrs_col_h<1536>();
+}
+
+// ---- batched launches (the medium products of dmul_batch, one transform length per launch) ----
+template <uint32_t N1>
+static cudaError_t launch_fwd_b(const PlanDev &pd, const JobDev *jobs, int njobs, uint32_t *status,
+                                cudaStream_t s) {
+    if (pd.col_half) {
+        dim3 grid(kPrimes * (pd.N2 / 16), 2, (unsigned)njobs);
+        k_col_fwd_h_b<N1><<<grid, pd.col_threads, (size_t)N1 * 16 * 4, s>>>(pd, jobs, status);
+    } else {
+        dim3 grid(kPrimes * (pd.N2 / 32), 2, (unsigned)njobs);
+        k_col_fwd_ct_b<N1><<<grid, pd.col_threads, (size_t)N1 * 32 * 4, s>>>(pd, jobs, status);
+    }
+    return cudaGetLastError();
+}
+
+template <uint32_t N1>
+static cudaError_t launch_inv_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(pd.col_threads, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (pd.col_half) {
+        cfg.gridDim = dim3(2 * kPrimes * (pd.N2 / 32), 1, (unsigned)njobs);
+        cfg.dynamicSmemBytes = (size_t)N1 * 16 * 4;
+        at[0].val.clusterDim.x = 2 * kPrimes;
+        return cudaLaunchKernelEx(&cfg, k_col_inv_h_b<N1>, pd, jobs);
+    }
+    cfg.gridDim = dim3(kPrimes * (pd.N2 / 32), 1, (unsigned)njobs);
+    cfg.dynamicSmemBytes = (size_t)N1 * 32 * 4;
+    at[0].val.clusterDim.x = kPrimes;
+    return cudaLaunchKernelEx(&cfg, k_col_inv_ct_b<N1>, pd, jobs);
+}
+
+cudaError_t launch_col_fwd_bs(const PlanDev &pd, const JobDev *jobs, int njobs, uint32_t *status,
+                              cudaStream_t s) {
+    switch (pd.N1) {
+        case 512: return launch_fwd_b<512>(pd, jobs, njobs, status, s);
+        case 768: return launch_fwd_b<768>(pd, jobs, njobs, status, s);
+        case 1024: return launch_fwd_b<1024>(pd, jobs, njobs, status, s);
+        default: return launch_fwd_b<1536>(pd, jobs, njobs, status, s);
+    }
+}
+
+cudaError_t launch_col_inv_bs(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s) {
+    switch (pd.N1) {
+        case 512: return launch_inv_b<512>(pd, jobs, njobs, s);
+        case 768: return launch_inv_b<768>(pd, jobs, njobs, s);
+        case 1024: return launch_inv_b<1024>(pd, jobs, njobs, s);
+        default: return launch_inv_b<1536>(pd, jobs, njobs, s);
+    }
+}
+
+template <uint32_t N1>
+static cudaError_t attrs_col_b() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_col_fwd_ct_b<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(N1 * 32 * 4))))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_col_inv_ct_b<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(N1 * 32 * 4))))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_col_fwd_h_b<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(N1 * 16 * 4))))
+        return e;
+    return cudaFuncSetAttribute(k_col_inv_h_b<N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(N1 * 16 * 4));
+}
+
+cudaError_t init_kernel_attributes_colbatch() {
+    cudaError_t e;
+    if ((e = attrs_col_b<512>())) return e;
+    if ((e = attrs_col_b<768>())) return e;
+    if ((e = attrs_col_b<1024>())) return e;
+    return attrs_col_b<1536>();
 }
 
 }  // namespace dml

@@ -44,6 +44,7 @@ struct GroupLaunch {
     uint64_t N;
     size_t first, count;   // range in the descriptor array
     uint32_t maxtiles;
+    bool aligned = false;  // every operand of the group 16-byte aligned (specialized kernels allowed)
 };
 
 struct BatchState {

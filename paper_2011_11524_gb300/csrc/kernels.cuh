@@ -110,6 +110,14 @@ cudaError_t launch_col_fwd_h(const PlanDev &pd, const uint32_t *x, uint64_t nx, 
 cudaError_t launch_col_inv_h(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
                              uint32_t *out, uint2 *spill, cudaStream_t s, uint64_t *zero, uint32_t nzero);
 cudaError_t init_kernel_attributes_colhalf();
+// The specialized passes for a batch of medium products of one transform length (job =
+// blockIdx.z; every operand 16-byte aligned), full or half tiles per pd.col_half, and the
+// specialized row pass (plain form; squarings per job).
+cudaError_t launch_col_fwd_bs(const PlanDev &pd, const JobDev *jobs, int njobs, uint32_t *status,
+                              cudaStream_t s);
+cudaError_t launch_col_inv_bs(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s);
+cudaError_t launch_row_pass_ct_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s);
+cudaError_t init_kernel_attributes_colbatch();
 cudaError_t upload_constants_colpass(const PrimeConst pc[kPrimes], const CrtConst &crt);
 
 // The row pass the plan asks for: specialized when available, else the generic plain or TMA form.

@@ -192,6 +192,22 @@ __global__ void __launch_bounds__(256) k_row_ct(const PlanDev pd, uint32_t *X, c
     DMUL_PRIME_SWITCH(pi, (row_core_ct<PI, N, SQR>(pd, sm, sm + RowPad<N>::NP, xr, yr, xr)));
 }
 
+// the plain form for a batch of jobs of one transform length (job = blockIdx.z)
+template <uint32_t N>
+__global__ void __launch_bounds__(256) k_row_ct_b(const PlanDev pd, const JobDev *__restrict__ jobs) {
+    extern __shared__ uint32_t sm[];
+    const JobDev &J = jobs[blockIdx.z];
+    const uint32_t row = blockIdx.x;
+    const int pi = blockIdx.y;
+    uint32_t *xr = J.X + (uint64_t)pi * pd.N + (uint64_t)row * N;
+    if (J.square) {
+        DMUL_PRIME_SWITCH(pi, (row_core_ct<PI, N, true>(pd, sm, sm + RowPad<N>::NP, xr, nullptr, xr)));
+    } else {
+        const uint32_t *yr = J.Y + (uint64_t)pi * pd.N + (uint64_t)row * N;
+        DMUL_PRIME_SWITCH(pi, (row_core_ct<PI, N, false>(pd, sm, sm + RowPad<N>::NP, xr, yr, xr)));
+    }
+}
+
 // persistent TMA-fed form (see row_mul_tma_body in stages.cuh for the protocol)
 template <int PI, uint32_t N, bool SQR>
 __device__ __forceinline__ void row_tma_ct_body(const PlanDev &pd, uint32_t *sm, uint32_t *X,
@@ -308,6 +324,8 @@ static cudaError_t attrs_ct() {
         return e;
     if ((e = cudaFuncSetAttribute(k_row_ct<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, plain)))
         return e;
+    if ((e = cudaFuncSetAttribute(k_row_ct_b<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, plain)))
+        return e;
     if ((e = cudaFuncSetAttribute(k_row_tma_ct<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, tma)))
         return e;
     return cudaFuncSetAttribute(k_row_tma_ct<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tma);
@@ -319,6 +337,22 @@ cudaError_t init_kernel_attributes_rowpass() {
     if ((e = attrs_ct<2048>())) return e;
     if ((e = attrs_ct<4096>())) return e;
     return attrs_ct<8192>();
+}
+
+template <uint32_t N>
+static cudaError_t launch_ct_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s) {
+    dim3 grid(pd.N1, kPrimes, (unsigned)njobs);
+    k_row_ct_b<N><<<grid, pd.row_threads, (size_t)2 * RowPad<N>::NP * 4, s>>>(pd, jobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_pass_ct_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s) {
+    switch (pd.N2) {
+        case 1024: return launch_ct_b<1024>(pd, jobs, njobs, s);
+        case 2048: return launch_ct_b<2048>(pd, jobs, njobs, s);
+        case 4096: return launch_ct_b<4096>(pd, jobs, njobs, s);
+        default: return launch_ct_b<8192>(pd, jobs, njobs, s);
+    }
 }
 
 }  // namespace dml

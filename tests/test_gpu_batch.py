@@ -130,3 +130,39 @@ def test_served_mix_same_as_alone(d):
                 za, nza = alone.mul(tx, ty)
                 assert torch.equal(za, z) and nza == int(nz.item())
         assert d.dmul_wait(srv.handle, 10**9) == d.DMUL_ERR_UNKNOWN_TICKET
+
+
+@pytest.mark.parametrize("half", [False, True], ids=["full_tiles", "half_tiles"])
+def test_batch_specialized_splits(d, half):
+    """Medium jobs whose default splits take the specialized passes (N = 2^19: 512 x 1024, both
+    column and row specialized; N = 3 * 2^17: 768 x 512, column specialized), with squarings, and
+    a group holding an operand that is not 16-byte aligned (its column passes fall back to the
+    generic kernels)."""
+    flags = d.DMUL_FLAG_NO_AUTOTUNE | (d.DMUL_FLAG_COL_HALF if half else 0)
+    rng = np.random.Generator(np.random.PCG64(61 + half))
+
+    def rand(n):
+        a = rng.integers(0, 10**9, size=n, dtype=np.uint64).astype(np.uint32)
+        a[-1] = max(1, int(a[-1]))
+        return a
+
+    shapes = [(250001, 240000, False), (262000, 262000, True), (200003, 150000, False),
+              (160000, 160000, True)]
+    jobs = [wl.Job(rand(nx), None, True) if sq else wl.Job(rand(nx), rand(ny), False)
+            for nx, ny, sq in shapes]
+    jobs = [wl.Job(j.x, j.x, True) if j.square else j for j in jobs]
+    with d.Context(0, flags=flags) as c:
+        for misaligned in (False, True):
+            dev = _prep(d, jobs)
+            if misaligned:  # job 2's x one limb into a larger buffer: 4-byte, not 16-byte aligned
+                tx, nx, ty, ny, z, L, nz = dev[2]
+                buf = torch.zeros(nx + 1, dtype=torch.int32, device="cuda")
+                buf[1:] = tx
+                dev[2] = (buf[1:], nx, ty, ny, z, L, nz)
+                assert buf[1:].data_ptr() % 16 != 0
+            assert d.dmul_batch(c.handle, d.make_jobs(dev), len(dev)) == 0
+            assert d.dmul_sync(c.handle) == 0
+            _check(d, jobs, dev)
+        for nx, ny, sq in shapes[:1]:
+            info = d.dmul_get_plan(c.handle, nx + ny)
+            assert (info.N1, info.N2, info.col_half) == (512, 1024, int(half))

@@ -432,9 +432,25 @@ def run_served(d, torch, dev, count=2000, load=0.7, budget_gib=8):
     dj = _upload_jobs(d, torch, jobs, dev)
     arr = d.make_jobs(dj)
     budget = budget_gib << 30
+    # one request of every transform length the stream uses: plans (twiddle tables, autotuned
+    # splits) are built before the measurement and stay resident, as in a running server
+    def tlen(n):  # the smallest 2^k or 3 * 2^k >= n (>= 64): the transform length class
+        best, p = None, 1
+        while best is None or p <= best:
+            for c in (p, 3 * p):
+                if c >= max(n, 64) and (best is None or c < best):
+                    best = c
+            p *= 2
+        return best
+    warm, seen = [], set()
+    for i, j in enumerate(jobs):
+        nlen = tlen(len(j.x) + len(j.y))
+        if nlen not in seen:
+            seen.add(nlen)
+            warm.append(i)
     # saturated rate: everything submitted at once
     with d.Context(dev.index or 0, hbm_budget_bytes=budget) as srv:
-        for i in range(min(64, count)):  # plans and autotuning outside the measurement
+        for i in warm + list(range(min(64, count))):
             d.dmul_wait(srv.handle, d.dmul_submit(srv.handle, arr[i])[1])
         t0 = time.perf_counter()
         tk = [d.dmul_submit(srv.handle, arr[i])[1] for i in range(count)]
@@ -468,7 +484,7 @@ def run_served(d, torch, dev, count=2000, load=0.7, budget_gib=8):
     with d.Context(dev.index or 0) as plain:
         stream = torch.cuda.Stream(device=dev)
         sp = stream.cuda_stream
-        for (tx, nx, ty, ny, z, L, nz) in dj[:64]:
+        for (tx, nx, ty, ny, z, L, nz) in [dj[i] for i in warm] + dj[:64]:
             d.dmul_mul(plain.handle, tx, nx, ty, ny, z, L, nz, sp)
         assert d.dmul_sync(plain.handle, sp) == 0
         torch.cuda.synchronize()

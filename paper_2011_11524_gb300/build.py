@@ -67,8 +67,11 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         return obj
 
     srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(compile_one, srcs))
+    # the largest translation units (the template instantiations) first, one per core
+    order = sorted(srcs, key=lambda f: -os.path.getsize(f))
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 8))) as ex:
+        done = dict(zip(order, ex.map(compile_one, order)))
+    objs = [done[f] for f in srcs]
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -143,11 +143,14 @@ static int autotune_plan(dmul_ctx *c, uint64_t N, std::unique_ptr<PlanEntry> *be
         if (rc) break;
         float cand_ms = 1e30f;
         uint32_t cand_ct = 0, cand_rt = 0, cand_tma = 0, cand_grid = 0, cand_half = 0;
-        // column-pass variants: full-width tiles (256 or 512 threads) or half tiles (128 or 256)
+        // column-pass variants: full-width tiles (256 or 512 threads; 128 for short columns) or
+        // half tiles (128 or 256; 64 for short columns)
         std::vector<std::pair<uint32_t, uint32_t>> colv = {{0u, 256u}, {0u, 512u}};
+        if (n1 <= 384) colv.push_back({0u, 128u});
         if (col_half_supported(hp)) {
             colv.push_back({1u, 128u});
             colv.push_back({1u, 256u});
+            if (n1 <= 192) colv.push_back({1u, 64u});
         }
         // row-pass variants: plain (one CTA per row) or persistent TMA-fed with G CTAs per prime
         std::vector<std::pair<uint32_t, uint32_t>> rowv = {{0u, 0u}};
@@ -637,8 +640,6 @@ int dmul_init(dmul_ctx **out, const dmul_config *cfg) {
     CK(init_kernel_attributes_batch());
     CK(init_kernel_attributes_rowpass());
     CK(init_kernel_attributes_colpass());
-    CK(init_kernel_attributes_colhalf());
-    CK(init_kernel_attributes_colbatch());
     int rc = dev_alloc(c.get(), (void **)&c->status, 256);
     if (rc) return rc;
     CK(cudaMemset(c->status, 0, 256));

@@ -34,9 +34,7 @@ __global__ void __launch_bounds__(512) k_col_fwd(const PlanDev pd, const uint32_
 cudaError_t launch_col_fwd(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
                            uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status, cudaStream_t s) {
     const bool aligned = ((uintptr_t)x & 15) == 0 && ((uintptr_t)y & 15) == 0;
-    if (aligned && col_pass_specialized(pd))
-        return pd.col_half ? launch_col_fwd_h(pd, x, nx, y, ny, X, Y, status, s)
-                           : launch_col_fwd_ct(pd, x, nx, y, ny, X, Y, status, s);
+    if (aligned && col_pass_specialized(pd)) return launch_col_fwd_spec(pd, x, nx, y, ny, X, Y, status, s);
     const size_t smem = (size_t)pd.N1 * 32 * sizeof(uint32_t);
     const int threads = (int)pd.col_threads;
     dim3 grid(kPrimes * (pd.N2 / 32), y ? 2 : 1);
@@ -104,9 +102,7 @@ cudaError_t launch_col_inv(const PlanDev &pd, const uint32_t *X, uint64_t L, Inv
                            uint32_t *out, uint2 *spill, cudaStream_t s, void *zero, size_t zero_bytes) {
     uint64_t *zw = (uint64_t *)zero;
     const uint32_t nzero = (uint32_t)(zero_bytes / 8);
-    if (col_pass_specialized(pd))
-        return pd.col_half ? launch_col_inv_h(pd, X, L, mode, out, spill, s, zw, nzero)
-                           : launch_col_inv_ct(pd, X, L, mode, out, spill, s, zw, nzero);
+    if (mode == kInvDigits && col_pass_specialized(pd)) return launch_col_inv_spec(pd, X, L, out, spill, s, zw, nzero);
     const dim3 grid(kPrimes * (pd.N2 / 32)), block(pd.col_threads);
     const size_t smem = (size_t)pd.N1 * 32 * sizeof(uint32_t);
     if (mode == kInvTriples)

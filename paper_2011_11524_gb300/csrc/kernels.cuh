@@ -85,7 +85,7 @@ cudaError_t launch_row_mul(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bo
 cudaError_t launch_row_mul_tma(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
                                uint32_t *status, cudaStream_t s);
 
-// Specialized row passes for N2 in {1024, 2048, 4096, 8192} with the planner's schedule
+// Specialized row passes for N2 in {256, 512, 1024, 2048, 4096, 8192} with the planner's schedule
 // (rowpass.cu), plain or TMA-fed per pd.row_tma.
 bool row_pass_specialized(const PlanDev &pd);
 cudaError_t launch_row_pass_ct(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
@@ -93,31 +93,24 @@ cudaError_t launch_row_pass_ct(const PlanDev &pd, uint32_t *X, const uint32_t *Y
 cudaError_t init_kernel_attributes_rowpass();
 cudaError_t upload_constants_rowpass(const PrimeConst pc[kPrimes], const CrtConst &crt);
 
-// Specialized column passes for N1 in {512, 768, 1024, 1536} with the planner's schedule
-// (colpass.cu); launch_col_fwd / launch_col_inv dispatch to them when the schedule matches (and,
-// forward, when both operands are 16-byte aligned).
+// Specialized column passes (colpass.cuh; N1 in {64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536}
+// with the planner's schedule), on full or half tiles per pd.col_half.  launch_col_fwd /
+// launch_col_inv dispatch to them when the schedule matches (forward: both operands 16-byte
+// aligned; inverse: the digit-sum mode).  The batched forms take a job array (job = blockIdx.z;
+// every operand 16-byte aligned).
 bool col_pass_specialized(const PlanDev &pd);
-cudaError_t launch_col_fwd_ct(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
-                              uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status,
-                              cudaStream_t s);
-cudaError_t launch_col_inv_ct(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
-                              uint32_t *out, uint2 *spill, cudaStream_t s, uint64_t *zero, uint32_t nzero);
-cudaError_t init_kernel_attributes_colpass();
-// The same passes on N1 x 16 half tiles (pd.col_half): forward grid (3 N2/16, operands); inverse
-// in clusters of six CTAs (three primes x two halves of a 32-column tile).  col_threads <= 256.
-cudaError_t launch_col_fwd_h(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
-                             uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status, cudaStream_t s);
-cudaError_t launch_col_inv_h(const PlanDev &pd, const uint32_t *X, uint64_t L, InvMode mode,
-                             uint32_t *out, uint2 *spill, cudaStream_t s, uint64_t *zero, uint32_t nzero);
-cudaError_t init_kernel_attributes_colhalf();
-// The specialized passes for a batch of medium products of one transform length (job =
-// blockIdx.z; every operand 16-byte aligned), full or half tiles per pd.col_half, and the
-// specialized row pass (plain form; squarings per job).
+cudaError_t launch_col_fwd_spec(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
+                                uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *status, cudaStream_t s);
+cudaError_t launch_col_inv_spec(const PlanDev &pd, const uint32_t *X, uint64_t L, uint32_t *out, uint2 *spill,
+                                cudaStream_t s, uint64_t *zero, uint32_t nzero);
 cudaError_t launch_col_fwd_bs(const PlanDev &pd, const JobDev *jobs, int njobs, uint32_t *status,
                               cudaStream_t s);
 cudaError_t launch_col_inv_bs(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s);
+cudaError_t init_kernel_attributes_colpass();
+cudaError_t upload_constants_colpass(const PrimeConst pc[kPrimes], const CrtConst &crt);
+// The specialized row pass for a batch of medium products of one transform length (plain form;
+// squarings per job).
 cudaError_t launch_row_pass_ct_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s);
-cudaError_t init_kernel_attributes_colbatch();
 cudaError_t upload_constants_colpass(const PrimeConst pc[kPrimes], const CrtConst &crt);
 
 // The row pass the plan asks for: specialized when available, else the generic plain or TMA form.

@@ -254,7 +254,9 @@ bool make_host_plan(uint64_t N, HostPlan *hp, uint32_t n1_override) {
 
 bool col_half_supported(const HostPlan &hp) {
     const uint32_t n1 = hp.N1;
-    return (n1 == 512 || n1 == 768 || n1 == 1024 || n1 == 1536) && hp.N2 % 32 == 0 &&
+    const bool spec = n1 == 64 || n1 == 96 || n1 == 128 || n1 == 192 || n1 == 256 || n1 == 384 || n1 == 512 ||
+                      n1 == 768 || n1 == 1024 || n1 == 1536;
+    return spec && hp.N2 % 32 == 0 &&
            !hp.col_radix.empty() && hp.col_radix.back() == 16;
 }
 

@@ -369,7 +369,15 @@ def ctx_def(d):
 
 
 # (n, m) whose transform length gets the default split N1 x N2 with the given N1
-SPECIALIZED_COLS = [((150001, 150000), 768, 512),     # N = 3 * 2^17
+SPECIALIZED_COLS = [((3000, 3000), 96, 64),           # N = 3 * 2^11
+                    ((4000, 4001), 64, 128),          # N = 2^13
+                    ((8000, 8000), 128, 128),         # N = 2^14
+                    ((12000, 12000), 192, 128),       # N = 3 * 2^13
+                    ((16000, 12001), 128, 256),       # N = 2^15 (row pass specialized too)
+                    ((25000, 20000), 384, 128),       # N = 3 * 2^14
+                    ((33000, 32000), 256, 256),       # N = 2^16 (row pass specialized too)
+                    ((50001, 45000), 384, 256),       # N = 3 * 2^15 (row pass specialized too)
+                    ((150001, 150000), 768, 512),     # N = 3 * 2^17 (row pass specialized too)
                     ((262143, 200000), 512, 1024),    # N = 2^19
                     ((300000, 299999), 1536, 512),    # N = 3 * 2^18
                     ((524287, 400003), 1024, 1024)]   # N = 2^20

@@ -141,7 +141,7 @@ cudaError_t launch_triples_to_digits(const uint32_t *d, uint64_t L, uint32_t *ou
 }
 
 template <int NT, int PER>
-__global__ void __launch_bounds__(NT) k_carry(uint32_t *__restrict__ z, const uint2 *__restrict__ spill,
+__global__ void __launch_bounds__(NT, 1536 / NT) k_carry(uint32_t *__restrict__ z, const uint2 *__restrict__ spill,
                                               uint64_t L, CarryCtl *ctl, uint64_t *nz, uint32_t *status,
                                               uint32_t ntiles) {
     pdl_trigger();

@@ -695,12 +695,25 @@ __device__ __forceinline__ uint32_t map_compose(uint32_t g, uint32_t f) {
 }
 __device__ __forceinline__ uint32_t qdig(uint32_t t) { return (t >= kBase) + (t >= 2u * kBase); }
 
-__device__ __forceinline__ void st_release(uint64_t *p, uint64_t v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+__device__ __forceinline__ void st_relaxed(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
-__device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t *p) {
     uint64_t v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_add_release(uint32_t *p, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -768,8 +781,15 @@ __device__ __forceinline__ void col_inv_crt(const PlanDev &pd, const uint32_t *_
 // carry-out (status 2).  A tile whose map is constant -- its carry-out does not depend on its
 // carry-in, the usual case unless its digit sums sit at 10^9 - 1 -- publishes its carry-out at
 // once, so successors rarely wait.  The look-back runs on a whole warp: 32 predecessors per round,
-// the maps before the nearest finished predecessor composed by a warp reduction.  Every wait is
-// bounded; on expiry the tile records a timeout and proceeds with carry 0.
+// the maps before the nearest finished predecessor composed by a warp reduction.  A flag word holds
+// its status and its value together (one 64-bit access), so publishing and polling need no memory
+// ordering beyond the word itself.  Every wait is bounded; on expiry the tile records a timeout
+// and proceeds with carry 0.
+//
+// A run of positions maps carries monotonically with out(2) - out(0) <= 1, and its map is constant
+// unless every position of the run has a digit sum within 2 of a multiple of 10^9.  The per-thread
+// map therefore follows the carry chains from 0 and from 2; only when they end apart (never, for
+// random digits) is the chain from 1 followed too.
 template <int NT, int PER>
 __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2 *__restrict__ spill,
                                            uint64_t L, CarryCtl *ctl, uint64_t *nz,
@@ -777,7 +797,7 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
     // every 32-limb chunk start (where a spill lands) is the first limb of some thread
     static_assert(NT % 32 == 0 && NT <= 1024 && PER % 4 == 0 && 32 % PER == 0, "tile shape");
     constexpr int NW = NT / 32;
-    __shared__ uint32_t s_tile, s_cin, s_warp[NW];
+    __shared__ uint32_t s_tile, s_cin, s_early, s_warp[NW];
     __shared__ uint64_t s_top[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_tile = atomicAdd(&ctl->ticket, 1u);
@@ -801,15 +821,25 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
         v[0] += sp.x;
         v[1] += sp.y;
     }
-    // map of this thread's PER positions
-    uint32_t c0 = 0, c1 = 1, c2 = 2;
+    // map of this thread's PER positions: chains from carry 0 and 2 (and 1 only if they differ)
+    uint32_t c0 = 0, c2 = 2;
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
         c0 = qdig(v[i] + c0);
-        c1 = qdig(v[i] + c1);
         c2 = qdig(v[i] + c2);
     }
+    uint32_t c1 = c0;
+    if (c2 != c0) {
+        c1 = 1;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) c1 = qdig(v[i] + c1);
+    }
     uint32_t f = c0 | (c1 << 2) | (c2 << 4);
+    // The tile's map is the composition of its threads' maps; when the last thread's map is
+    // constant, so is the tile's, whatever came before: its carry-out is known now, and that thread
+    // publishes it at once (the usual case), ahead of every scan and barrier of the tile.
+    const bool early = c0 == c2;
+    if (tid == NT - 1 && early) st_relaxed(&ctl->flags[tile], 2ull | ((uint64_t)c0 << 8));
     // inclusive warp scan (earlier lanes first)
     uint32_t inc = f;
 #pragma unroll
@@ -820,46 +850,57 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
     uint32_t exc = __shfl_up_sync(0xffffffffu, inc, 1);
     if (lane == 0) exc = kIdentityMap;
     if (lane == 31) s_warp[warp] = inc;
+    if (tid == NT - 1) s_early = early ? 1u : 0u;
     __syncthreads();
+    // every warp scans the warp maps across its lanes: its own exclusive prefix, and the tile's map
+    uint32_t wi = lane < NW ? s_warp[lane] : kIdentityMap;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t o = __shfl_up_sync(0xffffffffu, wi, d);
+        if (lane >= d) wi = map_compose(wi, o);
+    }
+    const uint32_t wpre = warp == 0 ? kIdentityMap : __shfl_sync(0xffffffffu, wi, warp - 1);
     if (warp == 0) {
-        uint32_t agg = kIdentityMap;
-        if (lane == 0) {
-            for (int w = 0; w < NW; ++w) {
-                uint32_t wf = s_warp[w];
-                s_warp[w] = agg;  // exclusive prefix of warp w
-                agg = map_compose(wf, agg);
-            }
-        }
-        agg = __shfl_sync(0xffffffffu, agg, 0);
+        const uint32_t agg = __shfl_sync(0xffffffffu, wi, NW - 1);
         const uint32_t a0 = map_apply(agg, 0);
         const bool constant = (a0 == map_apply(agg, 1)) && (a0 == map_apply(agg, 2));
-        if (lane == 0) {
-            if (tile == 0 || constant) st_release(&ctl->flags[tile], 2ull | ((uint64_t)map_apply(agg, 0) << 8));
-            else st_release(&ctl->flags[tile], 1ull | ((uint64_t)agg << 8));
+        const bool published = s_early != 0;
+        if (lane == 0 && !published) {
+            if (tile == 0 || constant) st_relaxed(&ctl->flags[tile], 2ull | ((uint64_t)a0 << 8));
+            else st_relaxed(&ctl->flags[tile], 1ull | ((uint64_t)agg << 8));
         }
         uint32_t cin = 0;
         if (tile > 0) {
             uint32_t acc = kIdentityMap;  // maps of the predecessors already passed, newest last-applied
             int64_t top_t = (int64_t)tile - 1;
             for (;;) {
+                // poll the window of 32 predecessors until the ones up to the nearest finished
+                // one (or all 32, if none has finished) have published: only those are needed
                 const int64_t t = top_t - lane;
-                uint64_t w = 2ull;  // before tile 0: a finished tile with carry-out 0
+                uint64_t w;
+                unsigned incl;
+                int first;
                 bool late = false;
-                if (t >= 0) {
-                    uint32_t spins = 0;
-                    while (((w = ld_acquire(&ctl->flags[t])) & 3u) == 0) {
-                        if (++spins > kSpinLimit) { late = true; break; }
-                        __nanosleep(32);
-                    }
+                for (uint32_t spins = 0;; ++spins) {
+                    w = t >= 0 ? ld_relaxed(&ctl->flags[t]) : 2ull;  // before tile 0: carry-out 0
+                    const uint32_t st = (uint32_t)w & 3u;
+                    incl = __ballot_sync(0xffffffffu, st == 2u);
+                    const unsigned ready = __ballot_sync(0xffffffffu, st != 0u);
+                    first = incl ? __ffs(incl) - 1 : 32;
+                    const unsigned need = first == 32 ? 0xffffffffu : (2u << first) - 1u;  // lanes 0..first
+                    if ((ready & need) == need) break;
+                    if (spins >= kSpinLimit) { late = true; break; }
                 }
-                if (__any_sync(0xffffffffu, late)) {
+                if (late) {
                     if (lane == 0) atomicOr(status, kStatusTimeout);
                     cin = 0;
                     break;
                 }
-                const uint32_t st = (uint32_t)w & 3u, val = (uint32_t)(w >> 8) & 63u;
-                const unsigned incl = __ballot_sync(0xffffffffu, st == 2u);
-                const int first = incl ? __ffs(incl) - 1 : 32;
+                const uint32_t val = (uint32_t)(w >> 8) & 63u;
+                if (first == 0) {  // the nearest predecessor is finished: its carry-out
+                    cin = map_apply(acc, __shfl_sync(0xffffffffu, val, 0));
+                    break;
+                }
                 // compose the maps of lanes [0, first): newer lanes are applied after older ones
                 uint32_t m = (lane < first) ? val : kIdentityMap;
 #pragma unroll
@@ -876,24 +917,27 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
                 acc = map_compose(acc, G);
                 top_t -= 32;
             }
-            if (lane == 0 && !constant) st_release(&ctl->flags[tile], 2ull | ((uint64_t)map_apply(agg, cin) << 8));
+            if (lane == 0 && !published && !constant)
+                st_relaxed(&ctl->flags[tile], 2ull | ((uint64_t)map_apply(agg, cin) << 8));
         }
         if (lane == 0) s_cin = cin;
     }
     __syncthreads();
-    uint32_t c = map_apply(map_compose(exc, s_warp[warp]), s_cin);
-    uint64_t top = 0;
+    uint32_t c = map_apply(map_compose(exc, wpre), s_cin);
     uint32_t o[PER];
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-        uint32_t t = v[i] + c;
-        uint32_t q = qdig(t);
+        const uint32_t t = v[i] + c;
+        const uint32_t q = qdig(t);
         o[i] = t - q * kBase;
         c = q;
-        if (base + i < L) {
-            if (o[i]) top = base + i + 1;
-            if (base + i == L - 1 && c != 0) atomicOr(status, kStatusInvalid);  // z >= B^L
-        }
+    }
+    if (base < L && base + PER >= L) {  // the thread holding position L-1: a carry out of it means z >= B^L
+        uint32_t cc = map_apply(map_compose(exc, wpre), s_cin);
+#pragma unroll
+        for (int i = 0; i < PER; ++i)
+            if (base + i < L) cc = qdig(v[i] + cc);
+        if (cc != 0) atomicOr(status, kStatusInvalid);
     }
     if (vec) {
 #pragma unroll
@@ -903,7 +947,20 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
         for (int i = 0; i < PER; ++i)
             if (base + i < L) z[base + i] = o[i];
     }
-    // highest nonzero limb
+    if (!nz) return;
+    // The normalized length: the highest nonzero limb lies in the last tile that has one.  Every
+    // tile but the last counts itself done (release: after its digits); the last tile finds its
+    // highest nonzero limb, and only when it has none waits (bounded) for the others and scans
+    // their digits backwards.
+    if (tile != ntiles - 1) {
+        __syncthreads();
+        if (tid == 0) red_add_release(&ctl->done, 1u);
+        return;
+    }
+    uint64_t top = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i)
+        if (base + i < L && o[i]) top = base + i + 1;
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) {
         uint64_t oo = __shfl_down_sync(0xffffffffu, top, d);
@@ -914,14 +971,15 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
     if (tid == 0) {
         uint64_t t = 0;
         for (int w = 0; w < NW; ++w) t = s_top[w] > t ? s_top[w] : t;
-        if (t) atomicMax((unsigned long long *)&ctl->top, (unsigned long long)t);
-        __threadfence();
-        uint32_t prev = atomicAdd(&ctl->done, 1u);
-        if (prev == ntiles - 1 && nz) {
-            __threadfence();
-            uint64_t tt = atomicAdd((unsigned long long *)&ctl->top, 0ull);
-            *nz = tt ? tt : 1;
+        if (!t) {
+            uint32_t spins = 0;
+            while (ld_acquire_u32(&ctl->done) != ntiles - 1) {
+                if (++spins > kSpinLimit) { atomicOr(status, kStatusTimeout); break; }
+            }
+            for (uint64_t k = (uint64_t)tile * (NT * PER); k > 0; --k)
+                if (ld_relaxed_u32(z + k - 1)) { t = k; break; }
         }
+        *nz = t ? t : 1;
     }
 }
 

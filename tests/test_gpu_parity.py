@@ -235,7 +235,7 @@ def test_carry_long(d, ctx, L):
     tile map is constant), runs of 10^9-1 across tile and chunk boundaries, near-maximal
     coefficients."""
     rng = _rng(6100 + L)
-    for kind in ("run", "runs", "max"):
+    for kind in ("run", "runs", "max", "zero_tail"):
         if kind == "run":
             c = np.full(L, B - 1, np.uint64)
             c[0] = B
@@ -247,11 +247,14 @@ def test_carry_long(d, ctx, L):
                 c[int(start):int(start) + ln] = B - 1
                 c[int(start)] += int(rng.integers(0, 3))
             c[-2:] = 0
-        else:
+        elif kind == "max":
             c = rng.integers(0, 2**62, size=L, dtype=np.uint64)
             c[-1] = 0
             c[-2] = int(rng.integers(0, B))
             c[-3] = int(rng.integers(0, B * B // 2))
+        else:  # the top 20000 coefficients zero: the normalized length lies below the last tile
+            c = rng.integers(0, 3 * B, size=L, dtype=np.uint64)
+            c[L - 20000:] = 0
         tri = np.stack([c % B, (c // B) % B, c // (B * B)], axis=1).astype(np.uint32)
         z, nz = ctx.carry(d.to_device(tri.reshape(-1)), L)
         words = np.stack([c, np.zeros(L, np.uint64)], axis=1)
@@ -259,6 +262,22 @@ def test_carry_long(d, ctx, L):
         assert fin == 0
         assert np.array_equal(d.to_host(z), ref), kind
         assert nz == len(oracle.normalize(ref))
+
+
+@pytest.mark.parametrize("L", [100, 8192, 2_097_152, 2_097_157])
+def test_carry_overflow_flagged_sizes(d, ctx, L):
+    """A carry out of the top limb is reported for every tile shape (the top position at a thread's
+    last limb, mid-thread, in small and large tiles), and the context stays usable."""
+    tri = np.zeros((L, 3), np.uint32)
+    tri[L - 1] = (5, 1, 0)  # 5 + 10^9 at the top limb
+    t = d.to_device(tri.reshape(-1))
+    z = torch.empty(L, dtype=torch.int32, device="cuda")
+    nz = torch.zeros(1, dtype=torch.int64, device="cuda")
+    assert d.dmul_carry(ctx.handle, t, L, z, L, nz) == 0
+    assert d.dmul_sync(ctx.handle) == d.DMUL_ERR_INVALID
+    tri[L - 1] = (5, 0, 0)
+    zz, n = ctx.carry(d.to_device(tri.reshape(-1)), L)
+    assert n == L and int(d.to_host(zz)[L - 1]) == 5
 
 
 def test_carry_overflow_flagged(d, ctx):

@@ -424,9 +424,10 @@ def run_batched(d, torch, dev, reps=3, count=4096):
             "plain_ms_for_same_jobs": plain_ms, "speedup_vs_plain": plain_ms / best}
 
 
-def run_served(d, torch, dev, count=2000, load=0.7, budget_gib=8):
+def run_served(d, torch, dev, count=2000, load=0.7, budget_gib=8, loads=(0.1, 0.3, 0.5, 0.9)):
     """Poisson stream of requests (digits log-uniform 10^2..10^7, 30% squarings) into the serving
-    loop at `load` x its measured saturated rate; p50/p99 latency from arrival to completion."""
+    loop at a sweep of arrival rates (fractions `loads` and `load` of its measured saturated rate);
+    p50/p99 latency from arrival to completion at each.  The headline point is `load`."""
     from paper_2011_11524_gb300 import workloads as wl
     _, jobs = wl.c5_stream(1.0, count)
     dj = _upload_jobs(d, torch, jobs, dev)
@@ -457,29 +458,34 @@ def run_served(d, torch, dev, count=2000, load=0.7, budget_gib=8):
         for t in tk:
             assert d.dmul_wait(srv.handle, t) == 0
         sat = count / (time.perf_counter() - t0)
-        rate = load * sat
-        arrivals, _ = wl.c5_stream(rate, count)
-        # one thread: submit at each arrival time, and in between watch the oldest outstanding
-        # ticket (completion is observed in arrival order)
-        tickets = [0] * count
-        done_t = [0.0] * count
-        start = time.perf_counter() + 0.05
-        i = head = 0
-        while head < count:
-            now = time.perf_counter()
-            if i < count and now >= start + float(arrivals[i]):
-                rc, tickets[i] = d.dmul_submit(srv.handle, arr[i])
-                assert rc == 0
-                i += 1
-                continue
-            if head < i:
-                rc, done = d.dmul_poll(srv.handle, tickets[head])
-                assert rc == 0
-                if done:
-                    done_t[head] = now
-                    head += 1
-        lat = sorted((done_t[i] - (start + float(arrivals[i]))) * 1e3 for i in range(count))
-        wall = max(done_t) - start
+        sweep = []
+        for ld in sorted(set(list(loads) + [load])):
+            rate = ld * sat
+            arrivals, _ = wl.c5_stream(rate, count)
+            # one thread: submit at each arrival time, and in between watch the oldest outstanding
+            # ticket (completion is observed in arrival order)
+            tickets = [0] * count
+            done_t = [0.0] * count
+            start = time.perf_counter() + 0.05
+            i = head = 0
+            while head < count:
+                now = time.perf_counter()
+                if i < count and now >= start + float(arrivals[i]):
+                    rc, tickets[i] = d.dmul_submit(srv.handle, arr[i])
+                    assert rc == 0
+                    i += 1
+                    continue
+                if head < i:
+                    rc, done = d.dmul_poll(srv.handle, tickets[head])
+                    assert rc == 0
+                    if done:
+                        done_t[head] = now
+                        head += 1
+            lat = sorted((done_t[i] - (start + float(arrivals[i]))) * 1e3 for i in range(count))
+            wall = max(done_t) - start
+            sweep.append({"load": ld, "offered_rate_per_s": rate, "mults_per_s": count / wall,
+                          "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]})
+        head_pt = next(p for p in sweep if p["load"] == load)
     # the same requests one at a time through the plain form, back to back
     with d.Context(dev.index or 0) as plain:
         stream = torch.cuda.Stream(device=dev)
@@ -496,9 +502,11 @@ def run_served(d, torch, dev, count=2000, load=0.7, budget_gib=8):
     digits = sum(len(j.x) + len(j.y) for j in jobs) * 9
     return {"workload": f"{count} Poisson requests, digits log-uniform 10^2..10^7, 30% squarings",
             "plain_mults_per_s_same_requests": plain_rate,
-            "hbm_budget_gib": budget_gib, "saturated_mults_per_s": sat, "offered_rate_per_s": rate,
-            "mults_per_s": count / wall, "digits_per_s": digits / wall,
-            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+            "hbm_budget_gib": budget_gib, "saturated_mults_per_s": sat,
+            "offered_rate_per_s": head_pt["offered_rate_per_s"], "mults_per_s": head_pt["mults_per_s"],
+            "digits_per_s": digits / count * head_pt["mults_per_s"],
+            "p50_ms": head_pt["p50_ms"], "p99_ms": head_pt["p99_ms"], "load": load,
+            "sweep": sweep}
 
 
 def cpu_baseline(x, y, z_gpu=None, budget_s=10.0, digits=DIGITS) -> dict:

@@ -130,7 +130,7 @@ static int autotune_plan(dmul_ctx *c, uint64_t N, std::unique_ptr<PlanEntry> *be
     int sms_i = 152;
     cudaDeviceGetAttribute(&sms_i, cudaDevAttrMultiProcessorCount, c->device);
     const uint32_t sms = (uint32_t)sms_i;
-    cudaMemsetAsync(in, 0, N * 4, s);
+    cudaMemsetAsync(in, 0x11, N * 4, s);  // valid nonzero limbs (0x11111111 < 10^9)
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -373,7 +373,8 @@ int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
     if ((rc = dev_alloc(c, (void **)&buf, 2 * Lt * 4))) return rc;
     if ((rc = dev_alloc(c, (void **)&nzb, 64))) { dev_free(c, buf, 2 * Lt * 4); return rc; }
     cudaStream_t s = c->own_stream;
-    cudaMemsetAsync(buf, 0, 2 * Lt * 4, s);
+    // operands of valid nonzero limbs (0x11111111 < 10^9): both paths do the work of a real product
+    cudaMemsetAsync(buf, 0x11, 2 * Lt * 4, s);
     JobDev jd;
     memset(&jd, 0, sizeof(jd));
     jd.x = buf; jd.y = buf + Lt / 2; jd.z = buf + Lt; jd.nz = nzb; jd.nx = Lt / 2; jd.ny = Lt / 2; jd.L = Lt;

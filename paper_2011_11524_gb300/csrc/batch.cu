@@ -35,6 +35,90 @@ DMUL_DEFINE_UPLOAD(upload_constants_batch)
 // ---------------------------------------------------------------------------------------------
 // fused small product
 // ---------------------------------------------------------------------------------------------
+// The transform buffers hold one padding word after every 16 (index a + a/16, N + N/16 words): the
+// rows base + u*s of a stage (every stride s of these schedules is a multiple of 16) sit at
+// spidx(base) + u*(s + s/16), one address per group with constant steps, and the radix-16 center's
+// 16 consecutive rows at 17b + u.
+__device__ __forceinline__ uint32_t spidx(uint32_t a) { return a + (a >> 4); }
+__host__ __device__ constexpr uint32_t small_np(uint32_t N) { return N + N / 16; }
+
+// forward stage t < ns-1 (twiddled: outputs k > 0 go to their twiddle products unreduced)
+template <int PI, int R>
+__device__ __forceinline__ void sfwd_stage(const Stage &st, const uint2 *tw, uint32_t *sx, uint32_t *sy,
+                                           uint32_t n, uint32_t nops) {
+    const uint32_t stride = st.m / R, ps = stride + (stride >> 4);
+    const uint32_t per_op = n / R;
+    for (uint32_t g = threadIdx.x; g < per_op * nops; g += blockDim.x) {
+        const bool second = g >= per_op;
+        const uint32_t gg = second ? g - per_op : g;
+        const uint32_t blk = gg / stride, j = gg - blk * stride;
+        uint32_t *pb = (second ? sy : sx) + spidx(blk * st.m + j);
+        uint32_t v[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) v[u] = pb[u * ps];
+        dft<PI, 0, R, 1>(v);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            uint32_t o = v[outpos<R>(k)];
+            if (k > 0) {
+                const uint2 w = ldtw(tw + st.tw + (k - 1) * stride + j);
+                o = shoup<PI>(o, w.x, w.y);
+            }
+            pb[k * ps] = o;
+        }
+    }
+}
+
+// inverse stage t < ns-1: input 0 reduced (its producer left it unreduced), the others untwiddled;
+// outputs unreduced (the next inverse stage, or the final scaling, multiplies them)
+template <int PI, int R>
+__device__ __forceinline__ void sinv_stage(const Stage &st, const uint2 *tw, uint32_t *sb, uint32_t n) {
+    const uint32_t stride = st.m / R, ps = stride + (stride >> 4);
+    const uint32_t groups = n / R;
+    for (uint32_t g = threadIdx.x; g < groups; g += blockDim.x) {
+        const uint32_t blk = g / stride, j = g - blk * stride;
+        uint32_t *pb = sb + spidx(blk * st.m + j);
+        uint32_t v[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = pb[k * ps];
+        v[0] = red2p<PI>(v[0]);
+#pragma unroll
+        for (int k = 1; k < R; ++k) {
+            const uint2 w = ldtw(tw + st.twi + (k - 1) * stride + j);
+            v[k] = shoup<PI>(v[k], w.x, w.y);
+        }
+        dft<PI, 1, R, 2>(v);
+#pragma unroll
+        for (int u = 0; u < R; ++u) pb[u * ps] = v[outpos<R>(u)];
+    }
+}
+
+// last forward stage (radix 16) of every operand, pointwise product (or square), first inverse stage
+template <int PI, bool SQR>
+__device__ __forceinline__ void scenter(uint32_t *sx, const uint32_t *sy, uint32_t n) {
+    constexpr int R = 16;
+    for (uint32_t b = threadIdx.x; b < n / R; b += blockDim.x) {
+        uint32_t v[2][R];
+#pragma unroll
+        for (int op = 0; op < (SQR ? 1 : 2); ++op) {
+            const uint32_t *sb = (op ? sy : sx) + 17 * b;
+#pragma unroll
+            for (int u = 0; u < R; ++u) v[op][u] = sb[u];
+            dft<PI, 0, R>(v[op]);
+        }
+        uint32_t z[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const uint32_t a = v[0][outpos<R>(k)];
+            z[k] = mont<PI>(a, SQR ? a : v[1][outpos<R>(k)]);
+        }
+        dft<PI, 1, R, 2>(z);
+        uint32_t *sb = sx + 17 * b;
+#pragma unroll
+        for (int u = 0; u < R; ++u) sb[u] = z[outpos<R>(u)];
+    }
+}
+
 template <int PI>
 __device__ __forceinline__ void small_transform(const SmallPlanDev &sp, const JobDev &J, uint32_t *sx, uint32_t *sy,
                                 uint32_t *status) {
@@ -46,12 +130,12 @@ __device__ __forceinline__ void small_transform(const SmallPlanDev &sp, const Jo
         uint32_t a = i < J.nx ? J.x[i] : 0u;
         bad |= (a >= kBase);
         if (PI == 0) a = red2p<0>(a);
-        sx[swz(i)] = a;
+        sx[spidx(i)] = a;
         if (!sq) {
             uint32_t b = i < J.ny ? J.y[i] : 0u;
             bad |= (b >= kBase);
             if (PI == 0) b = red2p<0>(b);
-            sy[swz(i)] = b;
+            sy[spidx(i)] = b;
         }
     }
     const int any_bad = __syncthreads_or((int)bad);
@@ -59,22 +143,19 @@ __device__ __forceinline__ void small_transform(const SmallPlanDev &sp, const Jo
     const int ns = sp.ns;
     const uint32_t nops = sq ? 1u : 2u;
     for (int t = 0; t < ns - 1; ++t) {
-        DMUL_RADIX_SWITCH(sp.st[t].R, (row_fwd_stage<PI, RR>(sp.st[t], tw, sx, sy, nullptr, nullptr, false, N, nops)));
+        DMUL_RADIX_SWITCH(sp.st[t].R, (sfwd_stage<PI, RR>(sp.st[t], tw, sx, sy, N, nops)));
         __syncthreads();
     }
-    if (sq) {
-        DMUL_RADIX_SWITCH(sp.st[ns - 1].R, (row_center<PI, RR, true>(sx, sy, N)));
-    } else {
-        DMUL_RADIX_SWITCH(sp.st[ns - 1].R, (row_center<PI, RR, false>(sx, sy, N)));
-    }
+    if (sq) scenter<PI, true>(sx, sy, N);
+    else scenter<PI, false>(sx, sy, N);
     __syncthreads();
     for (int t = ns - 2; t >= 0; --t) {
-        DMUL_RADIX_SWITCH(sp.st[t].R, (row_inv_stage<PI, RR>(sp.st[t], tw, sx, nullptr, N)));
+        DMUL_RADIX_SWITCH(sp.st[t].R, (sinv_stage<PI, RR>(sp.st[t], tw, sx, N)));
         __syncthreads();
     }
     for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
-        uint32_t v = sx[swz(i)];
-        sx[swz(i)] = red1p<PI>(shoup<PI>(v, sp.scale[PI], sp.scales[PI]));
+        const uint32_t a = spidx(i);
+        sx[a] = red1p<PI>(shoup<PI>(sx[a], sp.scale[PI], sp.scales[PI]));
     }
     __syncthreads();
 }
@@ -155,8 +236,8 @@ __global__ void __launch_bounds__(512) k_small_mul(const SmallPlanDev sp, const 
     cg::cluster_group cluster = cg::this_cluster();
     const int pi = (int)cluster.block_rank();
     const JobDev J = jobs ? jobs[blockIdx.y] : one;
-    uint32_t *sx = sm, *sy = sm + sp.N;
-    uint2 *spb = (uint2 *)(sm + 2 * sp.N);
+    uint32_t *sx = sm, *sy = sm + small_np(sp.N);
+    uint2 *spb = (uint2 *)(sm + 2 * small_np(sp.N));
     DMUL_PRIME_SWITCH(pi, (small_transform<PI>(sp, J, sx, sy, status)));
     cluster.sync();
     const uint32_t *s0 = cluster.map_shared_rank(sx, 0);
@@ -168,7 +249,7 @@ __global__ void __launch_bounds__(512) k_small_mul(const SmallPlanDev sp, const 
     for (uint32_t c = pi + kPrimes * warp; c < nch; c += kPrimes * nw) {
         const uint32_t k = c * 32 + lane;  // < N: L <= N and 32 | N
         uint32_t d0, d1, d2;
-        crt_digits(s0[swz(k)], s1[swz(k)], s2[swz(k)], d0, d1, d2);
+        crt_digits(s0[spidx(k)], s1[spidx(k)], s2[spidx(k)], d0, d1, d2);
         uint32_t sv;
         uint2 spv;
         chunk_digits(d0, d1, d2, sv, spv);
@@ -192,8 +273,8 @@ __global__ void __launch_bounds__(512) k_small_persist(const SmallPlanDev *__res
     __shared__ uint32_t s_job;
     cg::cluster_group cluster = cg::this_cluster();
     const int pi = (int)cluster.block_rank();
-    uint32_t *sx = sm, *sy = sm + maxN;
-    uint2 *spb = (uint2 *)(sm + 2 * maxN);
+    uint32_t *sx = sm, *sy = sm + small_np(maxN);
+    uint2 *spb = (uint2 *)(sm + 2 * small_np(maxN));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (;;) {
         if (pi == 0 && threadIdx.x == 0) {
@@ -215,7 +296,7 @@ __global__ void __launch_bounds__(512) k_small_persist(const SmallPlanDev *__res
         for (uint32_t c = pi + kPrimes * warp; c < nch; c += kPrimes * nw) {
             const uint32_t k = c * 32 + lane;
             uint32_t d0, d1, d2;
-            crt_digits(s0[swz(k)], s1[swz(k)], s2[swz(k)], d0, d1, d2);
+            crt_digits(s0[spidx(k)], s1[spidx(k)], s2[spidx(k)], d0, d1, d2);
             uint32_t sv;
             uint2 spv;
             chunk_digits(d0, d1, d2, sv, spv);
@@ -239,7 +320,7 @@ cudaError_t launch_small_persistent(const SmallPlanDev *plans, uint32_t maxN, co
     }
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(maxN >= 8192 ? 512 : 256, 1, 1);
-    cfg.dynamicSmemBytes = (size_t)2 * maxN * 4 + (size_t)(maxN / 32) * sizeof(uint2);
+    cfg.dynamicSmemBytes = (size_t)2 * small_np(maxN) * 4 + (size_t)(maxN / 32) * sizeof(uint2);
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -259,7 +340,7 @@ cudaError_t launch_small_persistent(const SmallPlanDev *plans, uint32_t maxN, co
     return cudaLaunchKernelEx(&cfg, k_small_persist, plans, jobs, njobs, maxN, counter, status);
 }
 
-static size_t small_smem(uint32_t N) { return (size_t)2 * N * 4 + (size_t)(N / 32) * sizeof(uint2); }
+static size_t small_smem(uint32_t N) { return (size_t)2 * small_np(N) * 4 + (size_t)(N / 32) * sizeof(uint2); }
 
 static cudaError_t small_launch(const SmallPlanDev &sp, const JobDev *jobs, int njobs, const JobDev &one,
                                 uint32_t *status, cudaStream_t s) {
@@ -443,17 +524,28 @@ static int batch_state(dmul_ctx *c, BatchState **out) {
 // Every short product of the batch runs in one persistent launch; each group of longer products
 // of one transform length runs as the four batched pipeline launches.  Work items are spread over
 // the given streams.
-struct SmallLaunch {
+// The short products run in up to three persistent launches by size class (transform length up to
+// 1536, 6144, 24576): each launch sizes its shared memory for its class, so that clusters of short
+// jobs pack several to an SM instead of each holding the room of the largest job in the batch.
+constexpr int kSmallClasses = 3;
+inline int small_class(uint64_t N) { return N <= 1536 ? 0 : (N <= 6144 ? 1 : 2); }
+struct SmallClass {
     size_t first = 0, count = 0;
     uint32_t maxN = 0;
+};
+struct SmallLaunch {
+    size_t count = 0;  // all short products
+    SmallClass cls[kSmallClasses];
     size_t nplans = 0;
 };
 
 static int launch_work(dmul_ctx *c, BatchState *b, const std::vector<GroupLaunch> &groups,
                        const SmallLaunch &sl, cudaStream_t *streams, int nstreams, uint32_t *status) {
     int si = 0;
-    if (sl.count) {
-        if (launch_small_persistent(b->dplans, sl.maxN, b->djobs + sl.first, (uint32_t)sl.count, b->dcounter,
+    for (int k = 0; k < kSmallClasses; ++k) {
+        const SmallClass &sc = sl.cls[k];
+        if (!sc.count) continue;
+        if (launch_small_persistent(b->dplans, sc.maxN, b->djobs + sc.first, (uint32_t)sc.count, b->dcounter + k,
                                     status, streams[si++ % nstreams]) != cudaSuccess)
             return DMUL_ERR_CUDA;
     }
@@ -491,7 +583,7 @@ static int upload_and_launch(dmul_ctx *c, BatchState *b, const std::vector<Group
     if (sl.count) {
         if (cudaMemcpyAsync(b->dplans, b->hplans, sl.nplans * sizeof(SmallPlanDev), cudaMemcpyHostToDevice, s) !=
                 cudaSuccess ||
-            cudaMemsetAsync(b->dcounter, 0, sizeof(uint32_t), s) != cudaSuccess)
+            cudaMemsetAsync(b->dcounter, 0, kSmallClasses * sizeof(uint32_t), s) != cudaSuccess)
             return DMUL_ERR_CUDA;
     }
     if (ctl_bytes && cudaMemsetAsync(b->arena + ctl_off, 0, ctl_bytes, s) != cudaSuccess) return DMUL_ERR_CUDA;
@@ -656,11 +748,16 @@ int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count,
     }
     // the persistent launch for the short products: their plan table and counter
     SmallLaunch sl;
+    size_t small_first = 0;
     for (size_t i = 0; i < count; ++i) {
         if (!items[i].small) continue;
-        if (!sl.count) sl.first = i;
+        if (!sl.count) small_first = i;
         ++sl.count;
-        sl.maxN = std::max<uint32_t>(sl.maxN, (uint32_t)items[i].N);
+        // the short items are sorted by decreasing N: each class is one contiguous range
+        SmallClass &sc = sl.cls[small_class(items[i].N)];
+        if (!sc.count) sc.first = i;
+        ++sc.count;
+        sc.maxN = std::max<uint32_t>(sc.maxN, (uint32_t)items[i].N);
     }
     if (sl.count) {
         if (!b->dcounter) {
@@ -669,7 +766,7 @@ int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count,
             if (cudaMallocHost(&b->hplans, kMaxSmallPlans * sizeof(SmallPlanDev)) != cudaSuccess) return DMUL_ERR_NOMEM;
         }
         std::vector<uint64_t> ns;
-        for (size_t i = sl.first; i < sl.first + sl.count; ++i) {
+        for (size_t i = small_first; i < small_first + sl.count; ++i) {
             auto f = std::find(ns.begin(), ns.end(), items[i].N);
             uint32_t id = (uint32_t)(f - ns.begin());
             if (f == ns.end()) {

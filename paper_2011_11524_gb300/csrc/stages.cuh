@@ -711,6 +711,23 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+// Maximum over the CTA (NT threads), returned to every thread; s: NT/32 words of shared memory
+// (reused after the final barrier).
+template <int NT>
+__device__ __forceinline__ uint64_t block_max_u64(uint64_t v, uint64_t *s) {
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        const uint64_t o = __shfl_down_sync(0xffffffffu, v, d);
+        v = o > v ? o : v;
+    }
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    uint64_t m = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) m = s[w] > m ? s[w] : m;
+    __syncthreads();
+    return m;
+}
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -949,38 +966,48 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
     }
     if (!nz) return;
     // The normalized length: the highest nonzero limb lies in the last tile that has one.  Every
-    // tile but the last counts itself done (release: after its digits); the last tile finds its
-    // highest nonzero limb, and only when it has none waits (bounded) for the others and scans
-    // their digits backwards.
+    // tile but the last marks in its flag word whether it has a nonzero limb and counts itself done
+    // (release: after its digits); the last tile finds its own highest nonzero limb, and only when
+    // it has none waits (bounded) for the others, finds the highest marked tile and scans its digits
+    // -- both searches spread over the CTA.
+    uint32_t any = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) any |= (base + i < L) ? o[i] : 0u;
     if (tile != ntiles - 1) {
-        __syncthreads();
-        if (tid == 0) red_add_release(&ctl->done, 1u);
+        const int tile_any = __syncthreads_or((int)(any != 0));
+        if (tid == NT - 1) {
+            // c: the carry out of the tile's last limb, the value published before
+            st_relaxed(&ctl->flags[tile], 2ull | ((uint64_t)c << 8) | ((uint64_t)(tile_any ? 1 : 0) << 16));
+            red_add_release(&ctl->done, 1u);
+        }
         return;
     }
     uint64_t top = 0;
 #pragma unroll
     for (int i = 0; i < PER; ++i)
         if (base + i < L && o[i]) top = base + i + 1;
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) {
-        uint64_t oo = __shfl_down_sync(0xffffffffu, top, d);
-        top = oo > top ? oo : top;
-    }
-    if (lane == 0) s_top[warp] = top;
-    __syncthreads();
-    if (tid == 0) {
-        uint64_t t = 0;
-        for (int w = 0; w < NW; ++w) t = s_top[w] > t ? s_top[w] : t;
-        if (!t) {
+    top = block_max_u64<NT>(top, s_top);
+    if (top == 0 && tile > 0) {
+        if (tid == 0) {
             uint32_t spins = 0;
             while (ld_acquire_u32(&ctl->done) != ntiles - 1) {
                 if (++spins > kSpinLimit) { atomicOr(status, kStatusTimeout); break; }
             }
-            for (uint64_t k = (uint64_t)tile * (NT * PER); k > 0; --k)
-                if (ld_relaxed_u32(z + k - 1)) { t = k; break; }
         }
-        *nz = t ? t : 1;
+        __syncthreads();
+        // the highest earlier tile with a nonzero limb
+        uint64_t hi = 0;  // tile index + 1
+        for (uint32_t t = tid; t < tile; t += NT)
+            if ((ld_relaxed(&ctl->flags[t]) >> 16) & 1u) hi = t + 1;
+        hi = block_max_u64<NT>(hi, s_top);
+        if (hi) {
+            const uint64_t t0 = (hi - 1) * (uint64_t)(NT * PER);
+            for (uint64_t k = t0 + tid; k < t0 + (uint64_t)NT * PER; k += NT)
+                if (ld_relaxed_u32(z + k)) top = top > k + 1 ? top : k + 1;
+            top = block_max_u64<NT>(top, s_top);
+        }
     }
+    if (tid == 0) *nz = top ? top : 1;
 }
 
 }  // namespace dml

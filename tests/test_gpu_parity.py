@@ -235,7 +235,7 @@ def test_carry_long(d, ctx, L):
     tile map is constant), runs of 10^9-1 across tile and chunk boundaries, near-maximal
     coefficients."""
     rng = _rng(6100 + L)
-    for kind in ("run", "runs", "max", "zero_tail"):
+    for kind in ("run", "runs", "max", "zero_tail", "zeros"):
         if kind == "run":
             c = np.full(L, B - 1, np.uint64)
             c[0] = B
@@ -252,9 +252,11 @@ def test_carry_long(d, ctx, L):
             c[-1] = 0
             c[-2] = int(rng.integers(0, B))
             c[-3] = int(rng.integers(0, B * B // 2))
-        else:  # the top 20000 coefficients zero: the normalized length lies below the last tile
+        elif kind == "zero_tail":  # the top 20000 coefficients zero: the normalized length lies below the last tile
             c = rng.integers(0, 3 * B, size=L, dtype=np.uint64)
             c[L - 20000:] = 0
+        else:  # a zero product: normalized length 1
+            c = np.zeros(L, np.uint64)
         tri = np.stack([c % B, (c // B) % B, c // (B * B)], axis=1).astype(np.uint32)
         z, nz = ctx.carry(d.to_device(tri.reshape(-1)), L)
         words = np.stack([c, np.zeros(L, np.uint64)], axis=1)

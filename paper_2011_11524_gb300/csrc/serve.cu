@@ -16,6 +16,7 @@ Server::Server(dmul_ctx *c) : ctx_(c) {
         if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) init_ok_ = false;
         if (cudaMalloc(&s->status, 64) != cudaSuccess || cudaMemset(s->status, 0, 64) != cudaSuccess)
             init_ok_ = false;
+        if (cudaMallocHost(&s->h_status, 64) != cudaSuccess) init_ok_ = false;
         if (init_batch_state(&s->bs) != DMUL_OK) init_ok_ = false;
         slots_.push_back(std::move(s));
     }
@@ -34,6 +35,7 @@ Server::~Server() {
         if (s->stream) cudaStreamSynchronize(s->stream);
         free_batch_state(ctx_, &s->bs);
         if (s->status) cudaFree(s->status);
+        if (s->h_status) cudaFreeHost(s->h_status);
         if (s->stream) cudaStreamDestroy(s->stream);
     }
 }
@@ -74,41 +76,42 @@ int Server::wait(uint64_t ticket) {
     return tk->status;
 }
 
+// Runs on CUDA's callback thread once the slot's batch and the copy of its status word are done:
+// completes the batch's tickets at once (no CUDA calls are allowed here); the worker recycles the
+// slot afterwards.
 void CUDART_CB Server::on_done(void *p) {
     Slot *s = (Slot *)p;
     Server *self = s->owner;
+    const uint32_t st = *(volatile uint32_t *)s->h_status;
+    const int rc = !st ? DMUL_OK : ((st & kStatusTimeout) ? DMUL_ERR_TIMEOUT : DMUL_ERR_INVALID);
     {
         std::lock_guard<std::mutex> g(self->mu_);
+        for (uint64_t t : s->tickets) {
+            Ticket &tk = self->tickets_[t];
+            tk.status = rc;
+            tk.done = true;
+        }
+        s->tickets.clear();
+        s->result = (int)st;
         s->finished = true;
     }
+    self->done_cv_.notify_all();
     self->cv_.notify_all();
 }
 
-// A finished slot: read its device status, complete its tickets, release its scratch.
+// A finished slot (its tickets already completed by on_done): clear its device status word if
+// the batch set it (on the slot's stream, ahead of the next batch there) and release its budget.
 void Server::retire(Slot &s, std::unique_lock<std::mutex> &g) {
-    std::vector<uint64_t> done;
-    done.swap(s.tickets);
     s.busy = false;
     s.finished = false;
     inflight_ -= s.bytes;
     s.bytes = 0;
-    g.unlock();
-    uint32_t st = 0;
-    int rc = DMUL_OK;
-    if (cudaMemcpyAsync(&st, s.status, 4, cudaMemcpyDeviceToHost, s.stream) != cudaSuccess ||
-        cudaStreamSynchronize(s.stream) != cudaSuccess) {
-        rc = DMUL_ERR_CUDA;
-    } else if (st) {
+    if (s.result) {
+        s.result = 0;
+        g.unlock();
         cudaMemsetAsync(s.status, 0, 4, s.stream);
-        rc = (st & kStatusTimeout) ? DMUL_ERR_TIMEOUT : DMUL_ERR_INVALID;
+        g.lock();
     }
-    g.lock();
-    for (uint64_t t : done) {
-        Ticket &tk = tickets_[t];
-        tk.status = rc;
-        tk.done = true;
-    }
-    done_cv_.notify_all();
 }
 
 // Admit pending requests into a free slot and launch them as one batch.
@@ -142,7 +145,10 @@ bool Server::launch(Slot &s, std::unique_lock<std::mutex> &g) {
         s.bs.arena_cap = 0;
     }
     if (arena) cudaFreeAsync(arena, s.stream);
-    if (rc == DMUL_OK && cudaLaunchHostFunc(s.stream, on_done, &s) != cudaSuccess) rc = DMUL_ERR_CUDA;
+    if (rc == DMUL_OK &&
+        (cudaMemcpyAsync(s.h_status, s.status, 4, cudaMemcpyDeviceToHost, s.stream) != cudaSuccess ||
+         cudaLaunchHostFunc(s.stream, on_done, &s) != cudaSuccess))
+        rc = DMUL_ERR_CUDA;
     g.lock();
     if (rc != DMUL_OK) {
         for (uint64_t t : s.tickets) {

@@ -54,6 +54,8 @@ class Server {
         BatchState bs;
         cudaStream_t stream = nullptr;
         uint32_t *status = nullptr;  // device status word of this slot's batches
+        uint32_t *h_status = nullptr;  // pinned copy, written on the stream before the callback
+        int result = 0;               // the finished batch's status (set by the callback)
         std::vector<uint64_t> tickets;
         size_t bytes = 0;
         void *arena = nullptr;

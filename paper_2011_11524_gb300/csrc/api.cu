@@ -476,8 +476,13 @@ int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, si
 
 int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
                        const uint32_t *y, size_t ny, bool square, cudaStream_t s, cudaEvent_t y_ready) {
-    const PlanDev &pd = pe->pd;
     if (!(c->cfg.flags & DMUL_FLAG_SIXSTEP)) {
+        // The row pass of a prime starts once that prime's forward columns are done (per-prime
+        // counters, running totals: this call adds operands x N2 columns to every prime's count).
+        PlanDev pd = pe->pd;
+        c->fwd_cols += (square ? 1u : 2u) * pd.N2;
+        pd.fsync = c->fwd_sync;
+        pd.ftarget = c->fwd_cols;
         if (y_ready && !square) {
             // x's forward pass first, then (once y is uploaded) y's
             Timed t(c, kStColFwd, s);
@@ -493,6 +498,7 @@ int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
         CK(launch_row_any(pd, c->X, c->Y, square, c->status, s));
         return DMUL_OK;
     }
+    const PlanDev &pd = pe->pd;
     // Six-step form (Sec. 7.2): [N1 x N2] -> transpose -> row DFTs of length N1 -> transpose
     // back -> (twiddle fused into the row DFT kernel) -> fused row pass -> and the mirror.
     if (y_ready) CK(cudaStreamWaitEvent(s, y_ready, 0));
@@ -516,7 +522,7 @@ int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
     }
     {
         Timed t(c, kStRowMul, s);
-        CK(launch_row_mul(pd, c->X, c->Y, square, s));
+        CK(launch_row_mul(pd, c->X, c->Y, square, s, c->status));
     }
     {
         Timed t(c, kStTranspose, s);
@@ -644,6 +650,9 @@ int dmul_init(dmul_ctx **out, const dmul_config *cfg) {
     int rc = dev_alloc(c.get(), (void **)&c->status, 256);
     if (rc) return rc;
     CK(cudaMemset(c->status, 0, 256));
+    rc = dev_alloc(c.get(), (void **)&c->fwd_sync, 256);
+    if (rc) return rc;
+    CK(cudaMemset(c->fwd_sync, 0, 256));
     CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
     *out = c.release();
     return DMUL_OK;
@@ -660,6 +669,7 @@ void dmul_destroy(dmul_ctx *c) {
     dev_free(c, c->spill, c->spill_cap * sizeof(uint2));
     dev_free(c, c->ctl, c->ctl_cap);
     dev_free(c, c->status, 256);
+    dev_free(c, c->fwd_sync, 256);
     destroy_batch_state(c);
 
     if (c->hx) { cudaFree(c->hx); cudaFree(c->hy); cudaFree(c->hz); cudaFree(c->hnz); }

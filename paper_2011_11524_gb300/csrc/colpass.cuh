@@ -229,13 +229,14 @@ __global__ void __launch_bounds__(512) k_col_fwd_ct(const PlanDev pd, const uint
     extern __shared__ __align__(16) uint32_t sm[];
     pdl_trigger();
     pdl_wait();
-    const int pi = blockIdx.x % kPrimes;
-    const uint32_t tile = blockIdx.x / kPrimes;
-    const bool second = blockIdx.y != 0;
+    uint32_t pi, tile;
+    bool second;
+    fwd_order(pi, tile, second);
     const uint32_t *src = second ? y : x;
     const uint64_t n = second ? ny : nx;
     uint32_t *dst = (second ? Y : X) + (uint64_t)pi * pd.N;
-    DMUL_PRIME_SWITCH(pi, (col_fwd_ct_body<PI, N1>(pd, sm, src, n, dst, tile, status)));
+    DMUL_PRIME_SWITCH((int)pi, (col_fwd_ct_body<PI, N1>(pd, sm, src, n, dst, tile, status)));
+    fwd_done(pd, pi, 32);
 }
 
 // the same for a batch of jobs of one transform length (job = blockIdx.z)
@@ -563,10 +564,12 @@ __global__ void __launch_bounds__(256, 3) k_col_fwd_h(const PlanDev pd, const ui
     extern __shared__ __align__(16) uint32_t sm[];
     pdl_trigger();
     pdl_wait();
-    const int pi = blockIdx.x % kPrimes;
-    const bool second = blockIdx.y != 0;
+    uint32_t pi, tile;
+    bool second;
+    fwd_order(pi, tile, second);
     col_fwd_h_run<N1>(pd, sm, second ? y : x, second ? ny : nx, (second ? Y : X) + (uint64_t)pi * pd.N,
-                      (blockIdx.x / kPrimes) * 16, pi, status);
+                      tile * 16, (int)pi, status);
+    fwd_done(pd, pi, 16);
 }
 
 // the same for a batch of jobs of one transform length (job = blockIdx.z)

@@ -83,6 +83,10 @@ struct dmul_ctx {
     void *ctl = nullptr;
     size_t ctl_cap = 0;
     uint32_t *status = nullptr;  // device status word
+    // per-prime hand-off counters from the forward column pass to the row pass (device, never
+    // reset) and the host's running total of the columns the plain path has sent through them
+    uint32_t *fwd_sync = nullptr;
+    uint32_t fwd_cols = 0;
     // host-buffer path staging
     uint32_t *hx = nullptr, *hy = nullptr, *hz = nullptr;
     uint64_t *hnz = nullptr;

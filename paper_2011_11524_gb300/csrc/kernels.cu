@@ -22,13 +22,14 @@ __global__ void __launch_bounds__(512) k_col_fwd(const PlanDev pd, const uint32_
     extern __shared__ uint32_t sm[];
     pdl_trigger();
     pdl_wait();
-    const int pi = blockIdx.x % kPrimes;
-    const uint32_t tile = blockIdx.x / kPrimes;
-    const bool second = blockIdx.y != 0;
+    uint32_t pi, tile;
+    bool second;
+    fwd_order(pi, tile, second);
     const uint32_t *src = second ? y : x;
     const uint64_t n = second ? ny : nx;
     uint32_t *dst = (second ? Y : X) + (uint64_t)pi * pd.N;
-    DMUL_PRIME_SWITCH(pi, (col_fwd_body<PI>(pd, sm, src, n, dst, tile, status)));
+    DMUL_PRIME_SWITCH((int)pi, (col_fwd_body<PI>(pd, sm, src, n, dst, tile, status)));
+    fwd_done(pd, pi, 32);
 }
 
 cudaError_t launch_col_fwd(const PlanDev &pd, const uint32_t *x, uint64_t nx, const uint32_t *y,
@@ -42,10 +43,11 @@ cudaError_t launch_col_fwd(const PlanDev &pd, const uint32_t *x, uint64_t nx, co
 }
 
 template <bool SQR>
-__global__ void __launch_bounds__(256) k_row_mul(const PlanDev pd, uint32_t *X, const uint32_t *Y) {
+__global__ void __launch_bounds__(256) k_row_mul(const PlanDev pd, uint32_t *X, const uint32_t *Y,
+                                                 uint32_t *status) {
     extern __shared__ uint32_t sm[];
     pdl_trigger();
-    pdl_wait();
+    row_wait_prime(pd, blockIdx.y, status);
     const uint32_t row = blockIdx.x;
     const int pi = blockIdx.y;
     uint32_t *xr = X + (uint64_t)pi * pd.N + (uint64_t)row * pd.N2;
@@ -58,7 +60,7 @@ __global__ void __launch_bounds__(256) k_row_mul_tma(const PlanDev pd, uint32_t 
                                                      uint32_t *status) {
     extern __shared__ __align__(16) uint32_t sm[];
     pdl_trigger();
-    pdl_wait();
+    row_wait_prime(pd, blockIdx.y, status);
     const int pi = blockIdx.y;
     DMUL_PRIME_SWITCH(pi, (row_mul_tma_body<PI, SQR>(pd, sm, X, Y, status)));
 }
@@ -76,15 +78,15 @@ cudaError_t launch_row_any(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bo
                            uint32_t *status, cudaStream_t s) {
     if (row_pass_specialized(pd)) return launch_row_pass_ct(pd, X, Y, square, status, s);
     if (pd.row_tma) return launch_row_mul_tma(pd, X, Y, square, status, s);
-    return launch_row_mul(pd, X, Y, square, s);
+    return launch_row_mul(pd, X, Y, square, s, status);
 }
 
 cudaError_t launch_row_mul(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
-                           cudaStream_t s) {
+                           cudaStream_t s, uint32_t *status) {
     dim3 grid(pd.N1, kPrimes);
     const size_t smem = (size_t)(square ? 1 : 2) * pd.N2 * sizeof(uint32_t);
-    if (square) return launch_pdl(k_row_mul<true>, grid, dim3(pd.row_threads), smem, s, 1, pd, X, Y);
-    return launch_pdl(k_row_mul<false>, grid, dim3(pd.row_threads), smem, s, 1, pd, X, Y);
+    if (square) return launch_pdl(k_row_mul<true>, grid, dim3(pd.row_threads), smem, s, 1, pd, X, Y, status);
+    return launch_pdl(k_row_mul<false>, grid, dim3(pd.row_threads), smem, s, 1, pd, X, Y, status);
 }
 
 template <int MODE>

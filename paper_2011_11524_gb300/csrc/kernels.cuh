@@ -78,7 +78,7 @@ cudaError_t launch_col_fwd(const PlanDev &pd, const uint32_t *x, uint64_t nx, co
 // Row pass: forward row transforms, pointwise product (or square), inverse row transforms,
 // result in X.
 cudaError_t launch_row_mul(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,
-                           cudaStream_t s);
+                           cudaStream_t s, uint32_t *status = nullptr);
 
 // The same row pass as a persistent kernel fed by bulk asynchronous copies (TMA), pd.row_grid
 // CTAs per prime, each prefetching its next row while computing the current one.

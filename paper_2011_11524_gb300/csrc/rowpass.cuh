@@ -182,10 +182,11 @@ __device__ __forceinline__ void row_core_ct(const PlanDev &pd, uint32_t *sx, uin
 }
 
 template <uint32_t N, bool SQR>
-__global__ void __launch_bounds__(256) k_row_ct(const PlanDev pd, uint32_t *X, const uint32_t *Y) {
+__global__ void __launch_bounds__(256) k_row_ct(const PlanDev pd, uint32_t *X, const uint32_t *Y,
+                                                uint32_t *status) {
     extern __shared__ uint32_t sm[];
     pdl_trigger();
-    pdl_wait();
+    row_wait_prime(pd, blockIdx.y, status);
     const uint32_t row = blockIdx.x;
     const int pi = blockIdx.y;
     uint32_t *xr = X + (uint64_t)pi * pd.N + (uint64_t)row * N;
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(256) k_row_tma_ct(const PlanDev pd, uint32_t *
                                                     uint32_t *status) {
     extern __shared__ __align__(16) uint32_t sm[];
     pdl_trigger();
-    pdl_wait();
+    row_wait_prime(pd, blockIdx.y, status);
     const int pi = blockIdx.y;
     DMUL_PRIME_SWITCH(pi, (row_tma_ct_body<PI, N, SQR>(pd, sm, X, Y, status)));
 }
@@ -291,8 +292,8 @@ static cudaError_t launch_ct(const PlanDev &pd, uint32_t *X, const uint32_t *Y, 
     } else {
         dim3 grid(pd.N1, kPrimes);
         const size_t smem = (size_t)(square ? 1 : 2) * RowPad<N>::NP * 4;
-        if (square) return launch_pdl(k_row_ct<N, true>, grid, dim3(pd.row_threads), smem, s, 1, pd, X, Y);
-        return launch_pdl(k_row_ct<N, false>, grid, dim3(pd.row_threads), smem, s, 1, pd, X, Y);
+        if (square) return launch_pdl(k_row_ct<N, true>, grid, dim3(pd.row_threads), smem, s, 1, pd, X, Y, status);
+        return launch_pdl(k_row_ct<N, false>, grid, dim3(pd.row_threads), smem, s, 1, pd, X, Y, status);
     }
     return cudaGetLastError();
 }

@@ -44,6 +44,52 @@ namespace dml {
 
 __device__ __forceinline__ uint2 ldtw(const uint2 *p) { return __ldg(p); }
 
+// ---- hand-off from the forward column pass to the row pass, per prime ------------------------
+// The forward column CTAs run prime by prime (CTA order lin = blockIdx.y * gridDim.x + blockIdx.x,
+// prime-major), so that the rows of a prime can start while later primes' columns still run.
+__device__ __forceinline__ void fwd_order(uint32_t &pi, uint32_t &tile, bool &second) {
+    const uint32_t nt = gridDim.x / kPrimes;  // tiles per prime and operand
+    const uint32_t per_prime = nt * gridDim.y;
+    const uint32_t lin = blockIdx.y * gridDim.x + blockIdx.x;
+    pi = lin / per_prime;
+    const uint32_t r = lin - pi * per_prime;
+    second = r >= nt;
+    tile = second ? r - nt : r;
+}
+__device__ __forceinline__ void fwd_sync_add(uint32_t *p, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t fwd_sync_ld(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+// end of a forward column CTA: its columns of prime pi are in memory
+__device__ __forceinline__ void fwd_done(const PlanDev &pd, uint32_t pi, uint32_t cols) {
+    if (!pd.fsync) return;
+    __syncthreads();
+    if (threadIdx.x == 0) fwd_sync_add(pd.fsync + pi, cols);
+}
+// start of a row CTA of prime pi: wait for the columns of its prime (bounded), or for the whole
+// previous grid when there is no per-prime hand-off
+__device__ __forceinline__ void row_wait_prime(const PlanDev &pd, uint32_t pi, uint32_t *status) {
+    if (!pd.fsync) {
+        pdl_wait();
+        return;
+    }
+    if (threadIdx.x == 0) {
+        uint32_t spins = 0;
+        while ((int32_t)(fwd_sync_ld(pd.fsync + pi) - pd.ftarget) < 0) {
+            if (++spins > (1u << 24)) {
+                if (status) atomicOr(status, kStatusTimeout);
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    __syncthreads();
+}
+
 // Grid-strided zeroing of n words (the next pipeline stage's control block; p may be null).
 __device__ __forceinline__ void zero_words(uint64_t *p, uint32_t n) {
     if (!p) return;

@@ -799,10 +799,11 @@ int dmul_mul_host(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, 
         cudaStreamSynchronize(c->copy_stream);
         return rc;
     }
-    CK(cudaMemcpyAsync(z, c->hz, L * 4, cudaMemcpyDeviceToHost, s));
-    // the normalized length and the status word into pinned memory: one synchronization
+    // the normalized length and the status word into pinned memory (ahead of the product, so that
+    // the product's copy ends the stream), then the product: one synchronization
     CK(cudaMemcpyAsync(&c->h_tail[0], c->hnz, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&c->h_tail[1], c->status, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(z, c->hz, L * 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (nz) *nz = (size_t)c->h_tail[0];
     const uint32_t st = (uint32_t)c->h_tail[1];

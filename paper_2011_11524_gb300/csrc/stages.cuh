@@ -64,11 +64,13 @@ __device__ __forceinline__ uint32_t fwd_sync_ld(const uint32_t *p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-// end of a forward column CTA: its columns of prime pi are in memory
+// end of a forward column CTA: its columns of prime pi are in memory.  Each warp posts its share
+// (cols / warps) once its own stores are ordered before the release (a warp barrier, then lane 0),
+// so no warp waits for the others' stores.
 __device__ __forceinline__ void fwd_done(const PlanDev &pd, uint32_t pi, uint32_t cols) {
     if (!pd.fsync) return;
-    __syncthreads();
-    if (threadIdx.x == 0) fwd_sync_add(pd.fsync + pi, cols);
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) fwd_sync_add(pd.fsync + pi, cols / (blockDim.x >> 5));
 }
 // start of a row CTA of prime pi: wait for the columns of its prime (bounded), or for the whole
 // previous grid when there is no per-prime hand-off

@@ -176,12 +176,22 @@ __device__ __forceinline__ void small_carry(const JobDev &J, const uint2 *spb, u
         if (k >= 33 && (k & 31) == 1) v += spb[(k >> 5) - 1].y;
         return v;
     };
-    uint32_t c0 = 0, c1 = 1, c2 = 2;
-    for (uint64_t k = b0; k < b1; ++k) {
-        uint32_t v = digit(k);
-        c0 = qdig(v + c0);
-        c1 = qdig(v + c1);
-        c2 = qdig(v + c2);
+    // the segment's map: constant when its last position's carry-out ignores its carry-in (the
+    // usual case), else the three carry chains
+    uint32_t c0 = 0, c1 = 0, c2 = 0;
+    const uint32_t vl = b1 > b0 ? digit(b1 - 1) : 0u;
+    const uint32_t ql = qdig(vl);
+    if (b1 > b0 && qdig(vl + 2u) == ql) {
+        c0 = c1 = c2 = ql;
+    } else {
+        c1 = 1;
+        c2 = 2;
+        for (uint64_t k = b0; k < b1; ++k) {
+            uint32_t v = digit(k);
+            c0 = qdig(v + c0);
+            c1 = qdig(v + c1);
+            c2 = qdig(v + c2);
+        }
     }
     uint32_t f = c0 | (c1 << 2) | (c2 << 4);
     uint32_t inc = f;

@@ -886,18 +886,25 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
         v[0] += sp.x;
         v[1] += sp.y;
     }
-    // map of this thread's PER positions: chains from carry 0 and 2 (and 1 only if they differ)
-    uint32_t c0 = 0, c2 = 2;
+    // map of this thread's PER positions.  When the last position's digit sum is not within 2 of
+    // a multiple of 10^9 its carry-out ignores its carry-in, so the map is constant: that carry-out
+    // (the usual case).  Otherwise follow the chains from carry 0 and 2 (and 1 if they differ).
+    const uint32_t ql = qdig(v[PER - 1]);
+    uint32_t c0 = ql, c1 = ql, c2 = ql;
+    if (qdig(v[PER - 1] + 2u) != ql) {
+        c0 = 0;
+        c2 = 2;
 #pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        c0 = qdig(v[i] + c0);
-        c2 = qdig(v[i] + c2);
-    }
-    uint32_t c1 = c0;
-    if (c2 != c0) {
-        c1 = 1;
+        for (int i = 0; i < PER; ++i) {
+            c0 = qdig(v[i] + c0);
+            c2 = qdig(v[i] + c2);
+        }
+        c1 = c0;
+        if (c2 != c0) {
+            c1 = 1;
 #pragma unroll
-        for (int i = 0; i < PER; ++i) c1 = qdig(v[i] + c1);
+            for (int i = 0; i < PER; ++i) c1 = qdig(v[i] + c1);
+        }
     }
     uint32_t f = c0 | (c1 << 2) | (c2 << 4);
     // The tile's map is the composition of its threads' maps; when the last thread's map is

@@ -63,6 +63,13 @@ typedef struct dmul_ctx dmul_ctx;
                                   /* half tiles (N1 in {512, 768, 1024, 1536}) instead of N1 x 32 */
 #define DMUL_FLAG_ROW_TMA 16u     /* with DMUL_FLAG_NO_AUTOTUNE: use the persistent row pass fed  */
                                   /* by bulk asynchronous copies (TMA) instead of one CTA per row */
+#define DMUL_FLAG_HOST_STAGED_IN 64u   /* dmul_mul_host: copy page-locked operands into device   */
+                                       /* staging buffers instead of reading them in place       */
+#define DMUL_FLAG_HOST_DIRECT_IN 256u  /* dmul_mul_host: read page-locked operands in place at   */
+                                       /* every length (default: only short products, see below) */
+#define DMUL_FLAG_HOST_STAGED_OUT 128u /* dmul_mul_host: write the product to a device buffer    */
+                                       /* and copy it out, instead of writing a page-locked z    */
+                                       /* in place                                               */
 
 typedef struct {
     int device;                /* CUDA device ordinal                                          */
@@ -103,11 +110,27 @@ int dmul_mul(dmul_ctx *ctx, const uint32_t *x, size_t nx, const uint32_t *y, siz
 int dmul_sqr(dmul_ctx *ctx, const uint32_t *x, size_t nx, uint32_t *z, size_t z_cap,
              uint64_t *nz, void *stream);
 
-/* Host-memory convenience: x, y, z and nz are HOST pointers.  Copies the operands to the device
- * through the context's pinned staging buffers, multiplies, copies z back and synchronizes.
- * x == y with nx == ny squares.  Returns the full status (including device-side errors). */
+/* Host-memory convenience: x, y, z and nz are HOST pointers; the call returns when z and *nz
+ * hold the product (it synchronizes).  x == y with nx == ny squares.  z must not overlap x or y.
+ * Returns the full status (including device-side errors).
+ *  - A page-locked z (cudaHostAlloc / cudaMallocHost / cudaHostRegister, both ends of the buffer
+ *    inside registered memory; a buffer must not straddle two registrations) is written in place
+ *    by the carry scan, so the limbs cross the host link while it runs.  Page-locked operands of a
+ *    short product (nx + ny <= DMUL_HOST_IN_PLACE_LIMBS) are read in place by the forward pass;
+ *    longer ones are copied, because every prime's column pass reads its operand tile again.
+ *    DMUL_FLAG_HOST_STAGED_IN / _OUT and DMUL_FLAG_HOST_DIRECT_IN override this.
+ *  - Pageable buffers are copied through device staging buffers (cudaMemcpyAsync; y's upload
+ *    overlaps x's forward pass).
+ * Device memory: nx + ny words for the digit sums, plus 2 (nx + ny) words of operand staging
+ * when the operands are copied; DMUL_ERR_NOMEM beyond the context's budget. */
 int dmul_mul_host(dmul_ctx *ctx, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny,
                   uint32_t *z, size_t z_cap, size_t *nz);
+
+#define DMUL_HOST_IN_PLACE_LIMBS 524288u
+
+/* 1 when the host buffer [p, p + bytes) is page-locked, so that dmul_mul_host can access it in
+ * place, else 0 (pageable memory, or a null / empty range). */
+int dmul_host_direct(dmul_ctx *ctx, const void *p, size_t bytes);
 
 /* ---- the batched form -------------------------------------------------------------------------- */
 typedef struct {

@@ -413,9 +413,11 @@ int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
     return DMUL_OK;
 }
 
+// z_out (optional, digits mode, four-step or six-step path): where the carry writes the limbs --
+// pinned host memory for the host-buffer entry point; z then only holds the digit sums.
 int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny,
                 uint32_t *z, size_t z_cap, uint64_t *nz, cudaStream_t s, InvMode mode,
-                uint32_t *mode_out, cudaEvent_t y_ready = nullptr) {
+                uint32_t *mode_out, cudaEvent_t y_ready = nullptr, uint32_t *z_out = nullptr) {
     uint64_t N;
     int rc = check_sizes(c, nx, ny, &N);
     if (rc) return rc;
@@ -445,6 +447,8 @@ int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, si
         if (y_ready) CK(cudaStreamWaitEvent(s, y_ready, 0));
         Timed t(c, kStSmall, s);
         CK(launch_small_mul_one(se->sp, jd, c->status, s));
+        // the fused kernel keeps its digit sums in z: its limbs are copied out afterwards
+        if (z_out) CK(cudaMemcpyAsync(z_out, z, L * 4, cudaMemcpyDefault, s));
         return DMUL_OK;
     }
     PlanEntry *pe;
@@ -469,7 +473,7 @@ int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, si
     }
     if (mode == kInvDigits) {
         Timed t(c, kStCarry, s);
-        CK(launch_carry(z, c->spill, L, (CarryCtl *)c->ctl, nz, c->status, s));
+        CK(launch_carry(z, c->spill, L, (CarryCtl *)c->ctl, nz, c->status, s, z_out));
     }
     return DMUL_OK;
 }
@@ -672,7 +676,8 @@ void dmul_destroy(dmul_ctx *c) {
     dev_free(c, c->fwd_sync, 256);
     destroy_batch_state(c);
 
-    if (c->hx) { cudaFree(c->hx); cudaFree(c->hy); cudaFree(c->hz); cudaFree(c->hnz); }
+    if (c->hx) { cudaFree(c->hx); cudaFree(c->hy); }
+    if (c->hz) { cudaFree(c->hz); cudaFree(c->hnz); }
     if (c->h_tail) {
         cudaFreeHost(c->h_tail);
         cudaStreamDestroy(c->copy_stream);
@@ -753,6 +758,30 @@ int dmul_transpose(dmul_ctx *c, uint32_t *a, size_t rows, size_t cols, void *str
     return DMUL_OK;
 }
 
+// The device address of the host buffer [p, p + bytes) when it is page-locked (cudaHostAlloc,
+// cudaMallocHost, cudaHostRegister: both ends inside registered memory), else nullptr.
+static void *pinned_view(const void *p, size_t bytes) {
+    cudaPointerAttributes a, b;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const char *last = (const char *)p + bytes - 1;
+    if (cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    if ((const char *)b.devicePointer != (const char *)a.devicePointer + (bytes - 1)) return nullptr;
+    return a.devicePointer;
+}
+
+int dmul_host_direct(dmul_ctx *c, const void *p, size_t bytes) {
+    if (!c || !p || !bytes) return 0;
+    if (set_device(c)) return 0;
+    return pinned_view(p, bytes) ? 1 : 0;
+}
+
 int dmul_mul_host(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny,
                   uint32_t *z, size_t z_cap, size_t *nz) {
     if (!c || !x || !y || !z) return DMUL_ERR_INVALID;
@@ -762,48 +791,76 @@ int dmul_mul_host(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, 
     if (rc) return rc;
     const size_t L = nx + ny;
     if (z_cap < L) return DMUL_ERR_CAPACITY;
+    if (overlaps(z, L * 4, x, nx * 4) || overlaps(z, L * 4, y, ny * 4)) return DMUL_ERR_INVALID;
     rc = set_device(c);
     if (rc) return rc;
     if (!c->h_tail) {
         CK(cudaMallocHost(&c->h_tail, 64));
+        CK(cudaHostGetDevicePointer((void **)&c->h_tail_dev, c->h_tail, 0));
         CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c->ev_y, cudaEventDisableTiming));
     }
+    // Page-locked buffers are read and written in place by the kernels (the operands by the
+    // forward pass, the limbs and their count by the carry scan): the bytes cross the host link
+    // while the kernels run, not in copies before and after them.  Pageable buffers (or the
+    // DMUL_FLAG_HOST_STAGED_* flags) go through device staging buffers with cudaMemcpyAsync.
+    // Operands in place only for short products (or on request): each prime's column pass reads
+    // the operand tile again, which over the host link costs more than one copy up front.
+    const bool in_place_in = !(c->cfg.flags & DMUL_FLAG_HOST_STAGED_IN) &&
+                             ((c->cfg.flags & DMUL_FLAG_HOST_DIRECT_IN) || L <= DMUL_HOST_IN_PLACE_LIMBS);
+    const uint32_t *xd = in_place_in ? (const uint32_t *)pinned_view(x, nx * 4) : nullptr;
+    const uint32_t *yd = square ? xd : in_place_in ? (const uint32_t *)pinned_view(y, ny * 4) : nullptr;
+    if (!xd || !yd) xd = yd = nullptr;  // both operands one way
+    uint32_t *zd = (c->cfg.flags & DMUL_FLAG_HOST_STAGED_OUT) ? nullptr : (uint32_t *)pinned_view(z, L * 4);
     if (c->h_cap < L) {
-        if (c->hx) { cudaFree(c->hx); cudaFree(c->hy); cudaFree(c->hz); cudaFree(c->hnz); c->used -= c->h_cap * 12 + 64; }
-        c->hx = c->hy = c->hz = nullptr;
+        if (c->hz) { cudaFree(c->hz); cudaFree(c->hnz); c->used -= c->h_cap * 4 + 64; }
+        c->hz = nullptr;
+        c->hnz = nullptr;
         c->h_cap = 0;
-        if (c->used + L * 12 + 64 > c->budget) return DMUL_ERR_NOMEM;
-        CK(cudaMalloc(&c->hx, L * 4));
-        CK(cudaMalloc(&c->hy, L * 4));
+        if (c->used + L * 4 + 64 > c->budget) return DMUL_ERR_NOMEM;
         CK(cudaMalloc(&c->hz, L * 4));
         CK(cudaMalloc(&c->hnz, 64));
-        c->used += L * 12 + 64;
+        c->used += L * 4 + 64;
         c->h_cap = L;
     }
-    cudaStream_t s = c->own_stream;
-    // x is uploaded on the compute stream; y on the copy stream, overlapping x's forward pass
-    CK(cudaMemcpyAsync(c->hx, x, nx * 4, cudaMemcpyHostToDevice, s));
-    cudaEvent_t y_ready = nullptr;
-    if (!square) {
-        CK(cudaEventRecord(c->ev_start, s));  // earlier work on s (readers of hy) is done first
-        CK(cudaStreamWaitEvent(c->copy_stream, c->ev_start, 0));
-        CK(cudaMemcpyAsync(c->hy, y, ny * 4, cudaMemcpyHostToDevice, c->copy_stream));
-        CK(cudaEventRecord(c->ev_y, c->copy_stream));
-        y_ready = c->ev_y;
+    if (!xd && c->h_in_cap < L) {
+        if (c->hx) { cudaFree(c->hx); cudaFree(c->hy); c->used -= c->h_in_cap * 8; }
+        c->hx = c->hy = nullptr;
+        c->h_in_cap = 0;
+        if (c->used + L * 8 > c->budget) return DMUL_ERR_NOMEM;
+        CK(cudaMalloc(&c->hx, L * 4));
+        CK(cudaMalloc(&c->hy, L * 4));
+        c->used += L * 8;
+        c->h_in_cap = L;
     }
-    rc = enqueue_mul(c, c->hx, nx, square ? c->hx : c->hy, ny, c->hz, L, c->hnz, s, kInvDigits, nullptr,
-                     y_ready);
+    cudaStream_t s = c->own_stream;
+    cudaEvent_t y_ready = nullptr;
+    const uint32_t *xa = xd, *ya = yd;
+    if (!xd) {
+        // x is uploaded on the compute stream; y on the copy stream, overlapping x's forward pass
+        CK(cudaMemcpyAsync(c->hx, x, nx * 4, cudaMemcpyHostToDevice, s));
+        xa = c->hx;
+        ya = square ? c->hx : c->hy;
+        if (!square) {
+            CK(cudaEventRecord(c->ev_start, s));  // earlier work on s (readers of hy) is done first
+            CK(cudaStreamWaitEvent(c->copy_stream, c->ev_start, 0));
+            CK(cudaMemcpyAsync(c->hy, y, ny * 4, cudaMemcpyHostToDevice, c->copy_stream));
+            CK(cudaEventRecord(c->ev_y, c->copy_stream));
+            y_ready = c->ev_y;
+        }
+    }
+    rc = enqueue_mul(c, xa, nx, ya, ny, c->hz, L, zd ? &c->h_tail_dev[0] : c->hnz, s, kInvDigits, nullptr,
+                     y_ready, zd);
     if (rc) {
         cudaStreamSynchronize(c->copy_stream);
         return rc;
     }
-    // the normalized length and the status word into pinned memory (ahead of the product, so that
-    // the product's copy ends the stream), then the product: one synchronization
-    CK(cudaMemcpyAsync(&c->h_tail[0], c->hnz, 8, cudaMemcpyDeviceToHost, s));
+    // the status word (and, staged, the normalized length) into pinned memory ahead of the
+    // product, so that the product's copy ends the stream: one synchronization
+    if (!zd) CK(cudaMemcpyAsync(&c->h_tail[0], c->hnz, 8, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(&c->h_tail[1], c->status, 4, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(z, c->hz, L * 4, cudaMemcpyDeviceToHost, s));
+    if (!zd) CK(cudaMemcpyAsync(z, c->hz, L * 4, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (nz) *nz = (size_t)c->h_tail[0];
     const uint32_t st = (uint32_t)c->h_tail[1];

@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(512) k_col_inv_b(const PlanDev pd, const JobDe
 __global__ void __launch_bounds__(256) k_carry_b(const JobDev *__restrict__ jobs, uint32_t *status) {
     const JobDev &J = jobs[blockIdx.y];
     if (blockIdx.x >= J.ntiles) return;
-    carry_tile<256, 8>(J.z, J.spill, J.L, J.ctl, J.nz, status, J.ntiles);
+    carry_tile<256, 8>(J.z, J.z, J.spill, J.L, J.ctl, J.nz, status, J.ntiles);
 }
 
 cudaError_t init_kernel_attributes_batch() {

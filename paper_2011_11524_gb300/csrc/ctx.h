@@ -88,9 +88,11 @@ struct dmul_ctx {
     uint32_t *fwd_sync = nullptr;
     uint32_t fwd_cols = 0;
     // host-buffer path staging
-    uint32_t *hx = nullptr, *hy = nullptr, *hz = nullptr;
+    uint32_t *hx = nullptr, *hy = nullptr;  // operand staging (pageable operands), h_in_cap words each
+    uint32_t *hz = nullptr;                 // digit sums (and, staged, the limbs), h_cap words
     uint64_t *hnz = nullptr;
-    size_t h_cap = 0;
+    size_t h_cap = 0, h_in_cap = 0;
+    uint64_t *h_tail_dev = nullptr;         // device address of h_tail
     uint64_t *h_tail = nullptr;            // pinned: [0] normalized length, [1] status word
     cudaStream_t copy_stream = nullptr;    // uploads of the second operand
     cudaEvent_t ev_start = nullptr, ev_y = nullptr;

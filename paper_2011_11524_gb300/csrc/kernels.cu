@@ -142,13 +142,13 @@ cudaError_t launch_triples_to_digits(const uint32_t *d, uint64_t L, uint32_t *ou
     return cudaGetLastError();
 }
 
-template <int NT, int PER>
-__global__ void __launch_bounds__(NT, 1536 / NT) k_carry(uint32_t *__restrict__ z, const uint2 *__restrict__ spill,
+template <int NT, int PER, bool OOP>
+__global__ void __launch_bounds__(NT, 1536 / NT) k_carry(const uint32_t *z, uint32_t *zo, const uint2 *__restrict__ spill,
                                               uint64_t L, CarryCtl *ctl, uint64_t *nz, uint32_t *status,
                                               uint32_t ntiles) {
     pdl_trigger();
     pdl_wait();
-    carry_tile<NT, PER>(z, spill, L, ctl, nz, status, ntiles);
+    carry_tile<NT, PER, OOP>(z, zo, spill, L, ctl, nz, status, ntiles);
 }
 
 // Long products take 8192-limb tiles (512 threads x 16), so that every tile of a product of a few
@@ -156,16 +156,19 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_carry(uint32_t *__restrict__ 
 // (256 x 8) for parallelism.  ctl holds flags for ceil(L / kCarryLimbs) tiles, enough for either;
 // it must be zero when the kernel starts.
 cudaError_t launch_carry(uint32_t *z, const uint2 *spill, uint64_t L, CarryCtl *ctl, uint64_t *nz,
-                         uint32_t *status, cudaStream_t s) {
+                         uint32_t *status, cudaStream_t s, uint32_t *zo) {
     constexpr uint64_t kBig = 512 * 16;
+    const uint32_t *zi = z;
+    const bool oop = zo && zo != z;
+    if (!zo) zo = z;
     if (L >= 256 * kBig) {
         const uint64_t ntiles = (L + kBig - 1) / kBig;
-        return launch_pdl(k_carry<512, 16>, dim3((unsigned)ntiles), dim3(512), 0, s, 1, z, spill, L, ctl, nz,
-                          status, (uint32_t)ntiles);
+        return launch_pdl(oop ? k_carry<512, 16, true> : k_carry<512, 16, false>, dim3((unsigned)ntiles),
+                          dim3(512), 0, s, 1, zi, zo, spill, L, ctl, nz, status, (uint32_t)ntiles);
     }
     const uint64_t ntiles = (L + kCarryLimbs - 1) / kCarryLimbs;
-    return launch_pdl(k_carry<256, 8>, dim3((unsigned)ntiles), dim3(256), 0, s, 1, z, spill, L, ctl, nz, status,
-                      (uint32_t)ntiles);
+    return launch_pdl(oop ? k_carry<256, 8, true> : k_carry<256, 8, false>, dim3((unsigned)ntiles), dim3(256), 0,
+                      s, 1, zi, zo, spill, L, ctl, nz, status, (uint32_t)ntiles);
 }
 
 // ---------------------------------------------------------------------------------------------

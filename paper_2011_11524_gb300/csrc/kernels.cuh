@@ -131,10 +131,12 @@ cudaError_t launch_col_inv(const PlanDev &pd, const uint32_t *X, uint64_t L, Inv
 cudaError_t launch_triples_to_digits(const uint32_t *d, uint64_t L, uint32_t *out, uint2 *spill,
                                      uint32_t *status, cudaStream_t s);
 
-// Decoupled-lookahead carry scan: z[0..L) (digit sums < 3*10^9) + spills -> base-10^9 limbs,
-// *nz (device, may be null).  ctl must be zeroed (carry_ctl_bytes(L)) before the launch.
+// Decoupled-lookahead carry scan: z[0..L) (digit sums < 3*10^9) + spills -> base-10^9 limbs in
+// zo[0..L) (zo == nullptr: in place in z; else a disjoint buffer, device or pinned host memory),
+// *nz (device or pinned host, may be null).  ctl must be zeroed (carry_ctl_bytes(L)) before the
+// launch.
 cudaError_t launch_carry(uint32_t *z, const uint2 *spill, uint64_t L, CarryCtl *ctl, uint64_t *nz,
-                         uint32_t *status, cudaStream_t s);
+                         uint32_t *status, cudaStream_t s, uint32_t *zo = nullptr);
 
 // Six-step pieces (Sec. 7.2, 7.6).
 cudaError_t launch_pack(const uint32_t *x, uint64_t nx, uint64_t N, uint32_t *X, uint32_t *status,

@@ -855,8 +855,12 @@ __device__ __forceinline__ void col_inv_crt(const PlanDev &pd, const uint32_t *_
 // unless every position of the run has a digit sum within 2 of a multiple of 10^9.  The per-thread
 // map therefore follows the carry chains from 0 and from 2; only when they end apart (never, for
 // random digits) is the chain from 1 followed too.
-template <int NT, int PER>
-__device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2 *__restrict__ spill,
+//
+// The digit sums are read from z and the limbs written to zo: the same buffer, or (OOP, the
+// host-buffer entry point) pinned host memory, so that the limbs cross the host link as the tiles
+// finish instead of in a copy after the kernel.
+template <int NT, int PER, bool OOP = false>
+__device__ __forceinline__ void carry_tile(const uint32_t *z, uint32_t *zo, const uint2 *__restrict__ spill,
                                            uint64_t L, CarryCtl *ctl, uint64_t *nz,
                                            uint32_t *status, uint32_t ntiles) {
     // every 32-limb chunk start (where a spill lands) is the first limb of some thread
@@ -1011,13 +1015,38 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
             if (base + i < L) cc = qdig(v[i] + cc);
         if (cc != 0) atomicOr(status, kStatusInvalid);
     }
-    if (vec) {
+    if constexpr (OOP) {
+        // out of place (pinned host memory across the host link, where a store of 16 bytes per
+        // lane at a 64-byte stride is as many transactions): the tile goes through shared memory
+        // and every warp store covers contiguous bytes.  Slot i of thread T sits at
+        // T * G + (i ^ (T mod G)), which halves the bank conflicts of the writes.
+        constexpr int G = PER / 4;
+        __shared__ uint4 s_out[NT * G];
 #pragma unroll
-        for (int i = 0; i < PER; i += 4) *(uint4 *)(z + base + i) = make_uint4(o[i], o[i + 1], o[i + 2], o[i + 3]);
+        for (int i = 0; i < G; ++i)
+            s_out[tid * G + (i ^ (tid & (G - 1)))] =
+                make_uint4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+        __syncthreads();
+        const uint64_t t0 = (uint64_t)tile * (NT * PER);
+        if ((((uintptr_t)zo) & 15) == 0 && t0 + NT * PER <= L) {
+            uint4 *dst = (uint4 *)(zo + t0);
+#pragma unroll
+            for (int j = tid; j < NT * G; j += NT) dst[j] = s_out[(j / G) * G + ((j % G) ^ ((j / G) & (G - 1)))];
+        } else {
+            const uint32_t *sw = (const uint32_t *)s_out;
+            for (int k = tid; k < NT * PER; k += NT) {
+                if (t0 + k >= L) break;
+                const int T = k / PER, r = k % PER;
+                zo[t0 + k] = sw[4 * (T * G + ((r / 4) ^ (T & (G - 1)))) + (r & 3)];
+            }
+        }
+    } else if (vec) {
+#pragma unroll
+        for (int i = 0; i < PER; i += 4) *(uint4 *)(zo + base + i) = make_uint4(o[i], o[i + 1], o[i + 2], o[i + 3]);
     } else {
 #pragma unroll
         for (int i = 0; i < PER; ++i)
-            if (base + i < L) z[base + i] = o[i];
+            if (base + i < L) zo[base + i] = o[i];
     }
     if (!nz) return;
     // The normalized length: the highest nonzero limb lies in the last tile that has one.  Every
@@ -1058,7 +1087,7 @@ __device__ __forceinline__ void carry_tile(uint32_t *__restrict__ z, const uint2
         if (hi) {
             const uint64_t t0 = (hi - 1) * (uint64_t)(NT * PER);
             for (uint64_t k = t0 + tid; k < t0 + (uint64_t)NT * PER; k += NT)
-                if (ld_relaxed_u32(z + k)) top = top > k + 1 ? top : k + 1;
+                if (ld_relaxed_u32(zo + k)) top = top > k + 1 ? top : k + 1;
             top = block_max_u64<NT>(top, s_top);
         }
     }

@@ -30,6 +30,10 @@ DMUL_FLAG_NO_SMALL = 4
 DMUL_FLAG_NO_AUTOTUNE = 8
 DMUL_FLAG_ROW_TMA = 16
 DMUL_FLAG_COL_HALF = 32
+DMUL_FLAG_HOST_STAGED_IN = 64
+DMUL_FLAG_HOST_STAGED_OUT = 128
+DMUL_FLAG_HOST_DIRECT_IN = 256
+DMUL_HOST_IN_PLACE_LIMBS = 524288
 
 # every symbol include/dmul.h declares
 EXPORTS = [
@@ -37,7 +41,7 @@ EXPORTS = [
     "dmul_mul_host", "dmul_batch", "dmul_submit", "dmul_poll", "dmul_wait", "dmul_conv_residues",
     "dmul_conv_coeffs", "dmul_carry", "dmul_transpose", "dmul_get_plan", "dmul_primes",
     "dmul_lambda", "dmul_max_min_limbs", "dmul_stage_times", "dmul_stage_timing", "dmul_probe_imad",
-    "dmul_carry_noalloc",
+    "dmul_carry_noalloc", "dmul_host_direct",
 ]
 
 
@@ -87,6 +91,7 @@ def load() -> ctypes.CDLL:
         "dmul_mul": ([vp, vp, sz, vp, sz, vp, sz, vp, vp], i32),
         "dmul_sqr": ([vp, vp, sz, vp, sz, vp, vp], i32),
         "dmul_mul_host": ([vp, vp, sz, vp, sz, vp, sz, ctypes.POINTER(sz)], i32),
+        "dmul_host_direct": ([vp, vp, sz], i32),
         "dmul_batch": ([vp, ctypes.POINTER(dmul_job), sz, vp], i32),
         "dmul_submit": ([vp, ctypes.POINTER(dmul_job), ctypes.POINTER(u64)], i32),
         "dmul_poll": ([vp, u64, ctypes.POINTER(i32)], i32),
@@ -170,6 +175,13 @@ def dmul_mul_host(ctx, x, nx, y, ny, z, z_cap) -> tuple[int, int]:
     rc = load().dmul_mul_host(ctx, _host_ptr(x), nx, _host_ptr(y), ny, _host_ptr(z), z_cap,
                               ctypes.byref(nz))
     return rc, nz.value
+
+
+def dmul_host_direct(ctx, a, nbytes=None) -> bool:
+    """Whether dmul_mul_host reads / writes the host buffer `a` in place (it is page-locked)."""
+    if nbytes is None:
+        nbytes = a.numel() * a.element_size() if hasattr(a, "numel") else a.nbytes
+    return load().dmul_host_direct(ctx, _host_ptr(a), nbytes) == 1
 
 
 def _host_ptr(a) -> int:

@@ -320,8 +320,8 @@ def test_argument_errors(d, ctx):
 
 @pytest.mark.parametrize("n,m", [(7777, 5555), (300000, 250001), (1 << 20, (1 << 20) - 3)])
 def test_host_buffer_entry_point(d, ctx, n, m):
-    """dmul_mul_host: host buffers in and out (y's upload overlaps x's forward pass on the
-    four-step path), the normalized length and the status word returned with the product."""
+    """dmul_mul_host on pageable buffers (staged copies; y's upload overlaps x's forward pass on
+    the four-step path), the normalized length and the status word returned with the product."""
     rng = _rng(7100 + n)
     x, y = _rand(rng, n), _rand(rng, m)
     z = np.zeros(len(x) + len(y), np.uint32)
@@ -339,6 +339,78 @@ def test_host_buffer_entry_point(d, ctx, n, m):
     assert rc == d.DMUL_ERR_INVALID
     rc, nz = d.dmul_mul_host(ctx.handle, x, len(x), y, len(y), z, len(z))
     assert rc == 0 and np.array_equal(z, ref)
+
+
+def _pinned(a):
+    t = torch.from_numpy(a.view(np.int32).copy()).pin_memory()
+    return t
+
+
+@pytest.fixture(scope="module")
+def ctx_staged(d):
+    c = d.Context(0, flags=d.DMUL_FLAG_HOST_STAGED_IN | d.DMUL_FLAG_HOST_STAGED_OUT)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx_direct_in(d):
+    c = d.Context(0, flags=d.DMUL_FLAG_HOST_DIRECT_IN)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("n,m", [(11112, 11112), (7777, 5555), (300000, 250001), (1 << 20, (1 << 20) - 3)])
+@pytest.mark.parametrize("kind", ["direct", "direct_in", "direct_out", "staged_flags", "forced_in"])
+def test_host_pinned_in_place(d, ctx, ctx_staged, ctx_direct_in, n, m, kind):
+    """dmul_mul_host on page-locked buffers: the forward pass reads x and y in place and the carry
+    scan writes z and its length in place (or, per buffer / per flag, the staged copies) -- every
+    combination gives the oracle's product."""
+    if n >= 1 << 20 and kind in ("direct_in", "direct_out"):
+        pytest.skip("the mixed cases run at the smaller sizes")
+    rng = _rng(7300 + n + m)
+    x, y = _rand(rng, n), _rand(rng, m)
+    L = n + m
+    px = _pinned(x) if kind in ("direct", "direct_in", "staged_flags", "forced_in") else x
+    py = _pinned(y) if kind in ("direct", "direct_in", "staged_flags", "forced_in") else y
+    pz = (torch.zeros(L + 3, dtype=torch.int32).pin_memory()
+          if kind in ("direct", "direct_out", "staged_flags", "forced_in") else np.zeros(L + 3, np.uint32))
+    c = {"staged_flags": ctx_staged, "forced_in": ctx_direct_in}.get(kind, ctx)
+    assert d.dmul_host_direct(c.handle, px) == (kind != "direct_out")
+    assert d.dmul_host_direct(c.handle, pz) == (kind != "direct_in")
+    ref = oracle.mul(x, y)
+    for _ in range(2):  # the second call reuses the staging / digit buffers
+        rc, nz = d.dmul_mul_host(c.handle, px, n, py, m, pz, L + 3)
+        assert rc == 0
+        zz = pz.numpy().view(np.uint32) if hasattr(pz, "numpy") else pz
+        assert np.array_equal(zz[:L], ref) and nz == len(oracle.normalize(ref))
+        assert not zz[L:].any()  # nothing written past nx + ny
+    # squaring in place
+    z2 = torch.zeros(2 * n, dtype=torch.int32).pin_memory()
+    rc, nz = d.dmul_mul_host(c.handle, px, n, px, n, z2, 2 * n)
+    assert rc == 0 and np.array_equal(z2.numpy().view(np.uint32), oracle.mul(x, x))
+    # an invalid limb read in place is reported, and the context stays usable
+    bad = y.copy()
+    bad[m // 2] = B
+    pb = _pinned(bad) if kind in ("direct", "direct_in", "staged_flags", "forced_in") else bad
+    rc, _ = d.dmul_mul_host(c.handle, px, n, pb, m, pz, L + 3)
+    assert rc == d.DMUL_ERR_INVALID
+    rc, nz = d.dmul_mul_host(c.handle, px, n, py, m, pz, L + 3)
+    zz = pz.numpy().view(np.uint32) if hasattr(pz, "numpy") else pz
+    assert rc == 0 and np.array_equal(zz[:L], ref)
+
+
+def test_host_pinned_zero_and_aliasing(d, ctx):
+    """In place: a zero product has length 1; z overlapping an operand is rejected."""
+    x = _pinned(np.zeros(5000, np.uint32))
+    y = _pinned(_rand(_rng(7400), 7000))
+    z = torch.full((12000,), -1, dtype=torch.int32).pin_memory()
+    rc, nz = d.dmul_mul_host(ctx.handle, x, 5000, y, 7000, z, 12000)
+    assert rc == 0 and nz == 1 and not z.numpy().any()
+    buf = torch.zeros(30000, dtype=torch.int32).pin_memory()
+    xs, zs = buf[:5000], buf[4000:16000]
+    rc, _ = d.dmul_mul_host(ctx.handle, xs, 5000, y, 7000, zs, 12000)
+    assert rc == d.DMUL_ERR_INVALID
 
 
 # ---- six-step form (Sec. 7.2) with the in-place transposes of Sec. 7.6 -------------------------

@@ -99,6 +99,8 @@ def _dft_mults(R: int) -> int:
     with the factor-1 butterflies peeled, Sec. 5.6; radix 3: one)."""
     if R == 3:
         return 1
+    if R == 5:
+        return 6
     n, h, total = R, R // 2, 0
     while h >= 1:
         total += (n // (2 * h)) * (h - 1)
@@ -376,6 +378,7 @@ def time_product(d, torch, dev, ctx, x_np, y_np, reps, flush, stream, square=Fal
 
 def run_other_configs(d, torch, dev, flush, stream) -> dict:
     """The other workload configurations, one product each (median of several runs)."""
+    import numpy as np
     from paper_2011_11524_gb300 import workloads as wl
     out = {}
     with d.Context(dev.index or 0) as ctx:
@@ -392,6 +395,18 @@ def run_other_configs(d, torch, dev, flush, stream) -> dict:
                                     (65_000_000, 48_000_000)):
             ms = time_product(d, torch, dev, ctx, a, b, 10, flush, stream)
             out[name] = {"ms": ms, "digits_per_s": nd / (ms * 1e-3)}
+        # a length in (2^22, 5 2^20]: N = 5 2^20 (radix-5 first column stage) instead of 3 2^21
+        rng = np.random.Generator(np.random.PCG64(6))
+        a5, b5 = wl.random_operand(19_000_000, rng), wl.random_operand(19_000_000, rng)
+        ms = time_product(d, torch, dev, ctx, a5, b5, 10, flush, stream)
+        out["len5_19M_x_19M"] = {"ms": ms, "digits_per_s": 38_000_000 / (ms * 1e-3),
+                                 "N": int(d.dmul_get_plan(ctx.handle, len(a5) + len(b5)).N)}
+    with d.Context(dev.index or 0, flags=d.DMUL_FLAG_NO_RADIX5) as ctx23:
+        ms = time_product(d, torch, dev, ctx23, a5, b5, 10, flush, stream)
+        out["len5_19M_x_19M_without_5x2k"] = {
+            "ms": ms, "digits_per_s": 38_000_000 / (ms * 1e-3),
+            "N": int(d.dmul_get_plan(ctx23.handle, len(a5) + len(b5)).N),
+            "note": "same product with lengths from {2^k, 3 2^k} only"}
     with d.Context(dev.index or 0, flags=d.DMUL_FLAG_SIXSTEP) as ctx6:
         x, y = wl.c2_random_pair()
         ms = time_product(d, torch, dev, ctx6, x, y, 5, flush, stream)
@@ -457,14 +472,14 @@ def run_served(d, torch, dev, count=2000, load=0.7, budget_gib=8, loads=(0.1, 0.
     budget = budget_gib << 30
     # one request of every transform length the stream uses: plans (twiddle tables, autotuned
     # splits) are built before the measurement and stay resident, as in a running server
-    def tlen(n):  # the smallest 2^k or 3 * 2^k >= n (>= 64): the transform length class
+    def tlen(n):  # the transform length classes: the one-cluster path's and the four-step plan's
         best, p = None, 1
         while best is None or p <= best:
             for c in (p, 3 * p):
                 if c >= max(n, 64) and (best is None or c < best):
                     best = c
             p *= 2
-        return best
+        return best, int(d.dmul_get_plan(None, n).N)
     warm, seen = [], set()
     for i, j in enumerate(jobs):
         nlen = tlen(len(j.x) + len(j.y))

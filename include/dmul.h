@@ -67,6 +67,8 @@ typedef struct dmul_ctx dmul_ctx;
                                        /* staging buffers instead of reading them in place       */
 #define DMUL_FLAG_HOST_DIRECT_IN 256u  /* dmul_mul_host: read page-locked operands in place at   */
                                        /* every length (default: only short products, see below) */
+#define DMUL_FLAG_NO_RADIX5 512u       /* transform lengths from {2^k, 3 2^k} only (default: also */
+                                       /* 5 2^k, with a radix-5 first column stage)              */
 #define DMUL_FLAG_HOST_STAGED_OUT 128u /* dmul_mul_host: write the product to a device buffer    */
                                        /* and copy it out, instead of writing a page-locked z    */
                                        /* in place                                               */

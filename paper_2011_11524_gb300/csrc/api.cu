@@ -336,7 +336,7 @@ int check_sizes(dmul_ctx *c, size_t nx, size_t ny, uint64_t *N) {
     uint64_t L = (uint64_t)nx + ny;
     if (std::min(nx, ny) > max_min_limbs()) return DMUL_ERR_TOO_LARGE;  // eq. product_inequality
     if (c->cfg.max_limbs && L > c->cfg.max_limbs) return DMUL_ERR_TOO_LARGE;
-    *N = (c->cfg.flags & DMUL_FLAG_SIXSTEP) ? choose_N_pow2(L) : choose_N(L);
+    *N = (c->cfg.flags & DMUL_FLAG_SIXSTEP) ? choose_N_pow2(L) : choose_N(L, !(c->cfg.flags & DMUL_FLAG_NO_RADIX5));
     if (*N == 0) return DMUL_ERR_TOO_LARGE;
     return DMUL_OK;
 }
@@ -593,7 +593,7 @@ uint64_t dmul_max_min_limbs(void) { return max_min_limbs(); }
 int dmul_get_plan(const dmul_ctx *ctx, uint64_t L, dmul_plan_info *out) {
     if (!out || L < 2) return DMUL_ERR_INVALID;
     const bool six = ctx && (ctx->cfg.flags & DMUL_FLAG_SIXSTEP);
-    uint64_t N = six ? choose_N_pow2(L) : choose_N(L);
+    uint64_t N = six ? choose_N_pow2(L) : choose_N(L, !(ctx && (ctx->cfg.flags & DMUL_FLAG_NO_RADIX5)));
     if (!N) return DMUL_ERR_TOO_LARGE;
     HostPlan hp;
     if (!(six ? make_host_plan_sixstep(N, &hp) : make_host_plan(N, &hp))) return DMUL_ERR_TOO_LARGE;

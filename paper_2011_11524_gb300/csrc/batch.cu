@@ -624,7 +624,7 @@ int run_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, cudaStream_t s) {
 size_t job_scratch_bytes(const dmul_ctx *c, const dmul_job &j) {
     const uint64_t L = j.nx + j.ny;
     if (choose_N_small(L) && !(c->cfg.flags & (DMUL_FLAG_SIXSTEP | DMUL_FLAG_NO_SMALL))) return 0;
-    const uint64_t N = choose_N(L);
+    const uint64_t N = choose_N(L, !(c->cfg.flags & DMUL_FLAG_NO_RADIX5));
     const bool sq = j.x == j.y && j.nx == j.ny;
     return align256((size_t)kPrimes * N * 4) * (sq ? 1 : 2) + align256(((L + 31) / 32 + 1) * sizeof(uint2)) +
            align256(carry_ctl_bytes(L));
@@ -651,7 +651,7 @@ int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count,
             it.small = true;
             it.N = Ns;
         } else {
-            it.N = (c->cfg.flags & DMUL_FLAG_SIXSTEP) ? 0 : choose_N(L);
+            it.N = (c->cfg.flags & DMUL_FLAG_SIXSTEP) ? 0 : choose_N(L, !(c->cfg.flags & DMUL_FLAG_NO_RADIX5));
             if (!it.N) return (c->cfg.flags & DMUL_FLAG_SIXSTEP) ? DMUL_ERR_INVALID : DMUL_ERR_TOO_LARGE;
         }
         items[i] = it;

@@ -7,7 +7,7 @@
 // Sec. 6 and the cluster CRT of Sec. 8.2.2), with N1 a template parameter so that each stage's
 // radix, span and stride are compile-time constants (group indices become shifts, shared-memory
 // addresses immediate offsets).  The dispatcher uses them only when the plan's column schedule is
-// the planner's (radix 3 first for 3*2^a, then a small power of two, then radix 16).
+// the planner's (radix 3 or 5 first for 3*2^a or 5*2^a, then a small power of two, then radix 16).
 #pragma once
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -23,13 +23,13 @@ namespace dml {
 
 template <uint32_t N1>
 struct ColSched {
-    static constexpr bool THREE = (N1 % 3) == 0;
-    static constexpr uint32_t P = THREE ? N1 / 3 : N1;
+    static constexpr uint32_t F = (N1 % 3) == 0 ? 3u : (N1 % 5) == 0 ? 5u : 1u;  // odd factor
+    static constexpr uint32_t P = N1 / F;
     static constexpr int A = ilog2c((int)P);
-    static constexpr int NS = (THREE ? 1 : 0) + (A % 4 ? 1 : 0) + A / 4;
+    static constexpr int NS = (F > 1 ? 1 : 0) + (A % 4 ? 1 : 0) + A / 4;
     static constexpr uint32_t radix(int t) {
-        if (THREE) {
-            if (t == 0) return 3;
+        if (F > 1) {
+            if (t == 0) return F;
             t -= 1;
         }
         return (A % 4 && t == 0) ? (1u << (A % 4)) : 16u;

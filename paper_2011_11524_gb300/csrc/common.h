@@ -24,6 +24,9 @@ struct PrimeConst {
     uint32_t w16[2][16];         // [dir][e] = xi_16^(+-e): dir 0 forward, 1 inverse
     uint32_t w16s[2][16];        // Shoup companions floor(w 2^32 / p)
     uint32_t w3[2], w3s[2];      // xi_3^(+-1) and companions
+    // radix 5, w = xi_5^(+-1): [dir][0] = -1/4, [1] = (w + w^4 - w^2 - w^3) / 4,
+    // [2] = (w - w^4) / 2, [3] = (w^2 - w^3) / 2 (mod p), and companions
+    uint32_t w5[2][4], w5s[2][4];
 };
 
 // Constants of the three-prime Garner CRT (Sec. 8.2.2 extended to l = 3) and of the base-10^9

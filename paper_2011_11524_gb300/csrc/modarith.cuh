@@ -91,10 +91,10 @@ __host__ __device__ constexpr int brev(int v, int bits) {
 }
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
 
-// Position of output k of an R-point DFT computed by dft<>: brev(k) for R = 2^a, k for R = 3.
+// Position of output k of an R-point DFT computed by dft<>: brev(k) for R = 2^a, k for R = 3, 5.
 template <int R>
 __device__ __forceinline__ constexpr int outpos(int k) {
-    if constexpr (R == 3) return k; else return brev(k, ilog2c(R));
+    if constexpr (R == 3 || R == 5) return k; else return brev(k, ilog2c(R));
 }
 
 // LAZY (last level only): 0 every output reduced to [0, 2p); 1 only output k = 0 (slot 0)
@@ -140,6 +140,30 @@ __device__ __forceinline__ void dft(uint32_t (&v)[R]) {
         uint32_t x1 = red2p<PI>(red2p<PI>(a - c + p2) + t);
         uint32_t x2 = red2p<PI>(red2p<PI>(a - b + p2) - t + p2);
         v[0] = x0; v[1] = x1; v[2] = x2;
+    } else if constexpr (R == 5) {
+        // With w = xi_5^(+-1), s1 = a1 + a4, d1 = a1 - a4, s2 = a2 + a3, d2 = a2 - a3:
+        //   X1, X4 = a0 + c1 s1 + c2 s2 +- (e1 d1 + e2 d2)
+        //   X2, X3 = a0 + c2 s1 + c1 s2 +- (e2 d1 - e1 d2)
+        // where c1 = (w + w^4)/2, c2 = (w^2 + w^3)/2, e1 = (w - w^4)/2, e2 = (w^2 - w^3)/2.  Since
+        // c1 + c2 = -1/2, the c-terms are b +- K2 (s1 - s2) with b = a0 - (s1 + s2)/4 and
+        // K2 = (c1 - c2)/2: six constant products instead of sixteen.
+        const uint32_t p2 = c_prime[PI].p2;
+        const uint32_t *k = c_prime[PI].w5[DIR], *ks = c_prime[PI].w5s[DIR];
+        const uint32_t a0 = v[0];
+        const uint32_t s1 = red2p<PI>(v[1] + v[4]), s2 = red2p<PI>(v[2] + v[3]);
+        const uint32_t d1 = v[1] - v[4] + p2, d2 = v[2] - v[3] + p2;  // (0, 4p): Shoup inputs
+        const uint32_t t1 = red2p<PI>(s1 + s2);
+        const uint32_t b = red2p<PI>(a0 + shoup<PI>(t1, k[0], ks[0]));
+        const uint32_t m2 = shoup<PI>(s1 - s2 + p2, k[1], ks[1]);
+        const uint32_t P = red2p<PI>(b + m2), Q = red2p<PI>(b - m2 + p2);
+        const uint32_t e11 = shoup<PI>(d1, k[2], ks[2]), e22 = shoup<PI>(d2, k[3], ks[3]);
+        const uint32_t e21 = shoup<PI>(d1, k[3], ks[3]), e12 = shoup<PI>(d2, k[2], ks[2]);
+        const uint32_t E1 = red2p<PI>(e11 + e22), E2 = red2p<PI>(e21 - e12 + p2);
+        v[0] = red2p<PI>(a0 + t1);
+        v[1] = red2p<PI>(P + E1);
+        v[4] = red2p<PI>(P - E1 + p2);
+        v[2] = red2p<PI>(Q + E2);
+        v[3] = red2p<PI>(Q - E2 + p2);
     } else {
         dft_levels<PI, DIR, R, R / 2, LAZY>(v);
     }

@@ -185,6 +185,21 @@ void make_prime_consts(PrimeConst out[kPrimes]) {
         c.w3[1] = (uint32_t)powmod64(w3, p - 2, p);
         c.w3s[0] = shoup_companion(c.w3[0], p);
         c.w3s[1] = shoup_companion(c.w3[1], p);
+        const uint64_t w5 = root_of_unity(p, 5);
+        const uint64_t inv2 = (p + 1) / 2, inv4 = mulmod64(inv2, inv2, p);
+        for (int dir = 0; dir < 2; ++dir) {
+            const uint64_t w = dir ? powmod64(w5, p - 2, p) : w5;
+            const uint64_t w2 = mulmod64(w, w, p), w3 = mulmod64(w2, w, p), w4 = mulmod64(w3, w, p);
+            uint64_t k[4];
+            k[0] = p - inv4;                                           // -1/4
+            k[1] = mulmod64((w + w4 + 2 * p - w2 - w3) % p, inv4, p);  // (c1 - c2) / 2
+            k[2] = mulmod64((w + p - w4) % p, inv2, p);                // e1
+            k[3] = mulmod64((w2 + p - w3) % p, inv2, p);               // e2
+            for (int i = 0; i < 4; ++i) {
+                c.w5[dir][i] = (uint32_t)k[i];
+                c.w5s[dir][i] = shoup_companion((uint32_t)k[i], p);
+            }
+        }
     }
 }
 
@@ -203,10 +218,10 @@ void make_crt_consts(CrtConst *o) {
 }
 
 // ---- transform lengths and schedules ------------------------------------------------------------
-uint64_t choose_N(uint64_t L) {
+uint64_t choose_N(uint64_t L, bool five) {
     uint64_t best = 0;
     for (uint64_t n = 1; n <= kMaxN; n <<= 1) {
-        for (uint64_t cand : {n, 3 * n}) {
+        for (uint64_t cand : {n, 3 * n, five ? 5 * n : n}) {
             if (cand >= L && cand >= kMinN && cand <= kMaxN && (best == 0 || cand < best)) best = cand;
         }
     }
@@ -225,14 +240,15 @@ static std::vector<uint32_t> pow2_schedule(uint32_t n) {
 
 bool make_host_plan(uint64_t N, HostPlan *hp, uint32_t n1_override) {
     if (N < kMinN || N > kMaxN) return false;
-    bool three = (N % 3 == 0);
-    uint64_t P = three ? N / 3 : N;
+    // N = f 2^k with f in {1, 3, 5}: the odd factor is the column pass's first radix
+    const uint32_t f = (N % 3 == 0) ? 3u : (N % 5 == 0) ? 5u : 1u;
+    uint64_t P = N / f;
     if (P & (P - 1)) return false;
     int k = 0;
     while ((1ull << k) < P) ++k;
     uint64_t N2 = 1ull << ((k + 1) / 2);
     uint64_t N1 = N / N2;
-    const uint64_t n1max = three ? kMaxN1 : 1024;
+    const uint64_t n1max = f == 3 ? kMaxN1 : f == 5 ? 1280 : 1024;
     while (N1 > n1max) { N1 /= 2; N2 *= 2; }
     while (N2 < (uint64_t)kTile) { N2 *= 2; N1 /= 2; }
     if (n1_override) {
@@ -246,16 +262,17 @@ bool make_host_plan(uint64_t N, HostPlan *hp, uint32_t n1_override) {
     hp->N1 = (uint32_t)N1;
     hp->N2 = (uint32_t)N2;
     hp->col_radix.clear();
-    if (three) hp->col_radix.push_back(3);
-    for (uint32_t r : pow2_schedule((uint32_t)(three ? N1 / 3 : N1))) hp->col_radix.push_back(r);
+    if (f > 1) hp->col_radix.push_back(f);
+    for (uint32_t r : pow2_schedule((uint32_t)(N1 / f))) hp->col_radix.push_back(r);
     hp->row_radix = pow2_schedule((uint32_t)N2);
     return (int)hp->col_radix.size() <= kMaxStages && (int)hp->row_radix.size() <= kMaxStages;
 }
 
 bool col_half_supported(const HostPlan &hp) {
     const uint32_t n1 = hp.N1;
-    const bool spec = n1 == 64 || n1 == 96 || n1 == 128 || n1 == 192 || n1 == 256 || n1 == 384 || n1 == 512 ||
-                      n1 == 768 || n1 == 1024 || n1 == 1536;
+    const bool spec = n1 == 64 || n1 == 80 || n1 == 96 || n1 == 128 || n1 == 160 || n1 == 192 || n1 == 256 ||
+                      n1 == 320 || n1 == 384 || n1 == 512 || n1 == 640 || n1 == 768 || n1 == 1024 ||
+                      n1 == 1280 || n1 == 1536;
     return spec && hp.N2 % 32 == 0 &&
            !hp.col_radix.empty() && hp.col_radix.back() == 16;
 }
@@ -263,7 +280,7 @@ bool col_half_supported(const HostPlan &hp) {
 std::vector<uint32_t> candidate_n1(uint64_t N) {
     std::vector<uint32_t> out;
     for (uint32_t n1 = 2; n1 <= kMaxN1; n1 *= 2) {
-        for (uint32_t cand : {n1, 3 * n1}) {
+        for (uint32_t cand : {n1, 3 * n1, 5 * n1}) {
             HostPlan hp;
             if (cand <= kMaxN1 && N % cand == 0 && make_host_plan(N, &hp, cand) && hp.N1 == cand &&
                 hp.N1 >= 32 && std::find(out.begin(), out.end(), cand) == out.end())

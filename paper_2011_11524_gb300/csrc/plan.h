@@ -30,8 +30,9 @@ void make_crt_consts(CrtConst *out);
 constexpr uint64_t kMaxN = 3ull << 22;
 constexpr uint64_t kMinN = 1024;
 
-// Smallest admissible transform length >= L: N in {2^k, 3*2^k} (Sec. 4.5 "smooth the stairs").
-uint64_t choose_N(uint64_t L);
+// Smallest admissible transform length >= L: N in {2^k, 3*2^k, 5*2^k} (Sec. 4.5 "smooth the
+// stairs", and the smoother set suggested in Sec. 9); five = false leaves out 5*2^k.
+uint64_t choose_N(uint64_t L, bool five = true);
 
 // Split N = N1 * N2 and the radix schedules.
 struct HostPlan {

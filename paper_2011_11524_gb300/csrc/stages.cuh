@@ -31,6 +31,7 @@ namespace dml {
         case 2: { constexpr int RR = 2; CALL; } break;   \
         case 3: { constexpr int RR = 3; CALL; } break;   \
         case 4: { constexpr int RR = 4; CALL; } break;   \
+        case 5: { constexpr int RR = 5; CALL; } break;   \
         case 8: { constexpr int RR = 8; CALL; } break;   \
         default: { constexpr int RR = 16; CALL; } break; \
     }

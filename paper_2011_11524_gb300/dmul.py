@@ -33,6 +33,7 @@ DMUL_FLAG_COL_HALF = 32
 DMUL_FLAG_HOST_STAGED_IN = 64
 DMUL_FLAG_HOST_STAGED_OUT = 128
 DMUL_FLAG_HOST_DIRECT_IN = 256
+DMUL_FLAG_NO_RADIX5 = 512
 DMUL_HOST_IN_PLACE_LIMBS = 524288
 
 # every symbol include/dmul.h declares

@@ -135,7 +135,8 @@ def test_served_mix_same_as_alone(d):
 @pytest.mark.parametrize("half", [False, True], ids=["full_tiles", "half_tiles"])
 def test_batch_specialized_splits(d, half):
     """Medium jobs whose default splits take the specialized passes (N = 2^19: 512 x 1024, both
-    column and row specialized; N = 3 * 2^17: 768 x 512, column specialized), with squarings, and
+    column and row specialized; N = 3 * 2^17: 768 x 512 and N = 5 * 2^16: 1280 x 256, column
+    specialized), with squarings, and
     a group holding an operand that is not 16-byte aligned (its column passes fall back to the
     generic kernels)."""
     flags = d.DMUL_FLAG_NO_AUTOTUNE | (d.DMUL_FLAG_COL_HALF if half else 0)

@@ -452,7 +452,7 @@ def test_c1_workload(d, ctx):
     assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))
 
 
-# ---- compile-time specialized column passes (N1 in {512, 768, 1024, 1536}) --------------------
+# ---- compile-time specialized column passes (N1 = 2^a, 3 2^a, 5 2^a from 64 to 1536) -----------
 @pytest.fixture(scope="module")
 def ctx_def(d):
     """Four-step path with the planner's default split and the one-CTA-per-row pass."""
@@ -470,10 +470,16 @@ SPECIALIZED_COLS = [((3000, 3000), 96, 64),           # N = 3 * 2^11
                     ((25000, 20000), 384, 128),       # N = 3 * 2^14
                     ((33000, 32000), 256, 256),       # N = 2^16 (row pass specialized too)
                     ((50001, 45000), 384, 256),       # N = 3 * 2^15 (row pass specialized too)
-                    ((150001, 150000), 768, 512),     # N = 3 * 2^17 (row pass specialized too)
+                    ((180000, 180000), 768, 512),     # N = 3 * 2^17 (row pass specialized too)
                     ((262143, 200000), 512, 1024),    # N = 2^19
-                    ((300000, 299999), 1536, 512),    # N = 3 * 2^18
-                    ((524287, 400003), 1024, 1024)]   # N = 2^20
+                    ((350000, 349999), 1536, 512),    # N = 3 * 2^18
+                    ((524287, 400003), 1024, 1024),   # N = 2^20
+                    ((1300, 1200), 80, 32),           # N = 5 * 2^9 (radix 5 first)
+                    ((2600, 2500), 160, 32),          # N = 5 * 2^10
+                    ((10000, 10000), 320, 64),        # N = 5 * 2^12
+                    ((40000, 40000), 640, 128),       # N = 5 * 2^14
+                    ((80001, 80000), 640, 256),       # N = 5 * 2^15 (row pass specialized too)
+                    ((330000, 320000), 1280, 512)]    # N = 5 * 2^17
 
 
 @pytest.fixture(scope="module")
@@ -509,3 +515,26 @@ def test_specialized_column_pass(d, request, half, shape, n1, n2):
         c = oracle.conv_at(x, y, k)
         assert dg[k, 0] + dg[k, 1] * B + dg[k, 2] * B * B == c, k
         assert [int(r[i, k]) for i in range(3)] == [c % p for p in primes], k
+
+
+
+@pytest.mark.parametrize("n,m", [(2097153, 2097152), (4194000, 1000)])
+def test_five_length_long(d, ctx, n, m):
+    """Long products on N = 5 2^k (here 5 2^20 = 5242880, split 1280 x 4096 or as autotuned):
+    bit-exact against the oracle, plus the squaring's closed form on all-nines operands."""
+    info = d.dmul_get_plan(ctx.handle, n + m)
+    assert info.N == 5 * 2**20
+    rng = _rng(11500 + m)
+    x, y = _rand(rng, n), _rand(rng, m)
+    z, nz = _gpu_mul(d, ctx, x, y)
+    ref = oracle.mul(x, y)
+    assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))
+    # (10^(9h) - 1)^2 = 10^(18h) - 2 10^(9h) + 1 for h limbs of nines
+    h = (n + m) // 2
+    nines = np.full(h, B - 1, np.uint32)
+    z2, nz2 = _gpu_mul(d, ctx, nines, nines, square=True)
+    expect = np.zeros(2 * h, np.uint32)
+    expect[0] = 1
+    expect[h] = B - 2
+    expect[h + 1:] = B - 1
+    assert np.array_equal(z2, expect) and nz2 == 2 * h

@@ -67,25 +67,41 @@ def test_product_bound():
     assert (10**9 - 1) ** 2 * 1864136 < P
 
 
-@pytest.mark.parametrize("L", [2, 3, 1000, 1024, 1025, 1536, 1537, 22224, 3728272, 5333334, 7222224,
-                               3 * 2**22])
+def _odd_part_admissible(n):
+    """n = f 2^k with f in {1, 3, 5} (the length set {2^k, 3 2^k, 5 2^k})."""
+    for f in (1, 3, 5):
+        if n % f == 0 and (n // f) & (n // f - 1) == 0:
+            return True
+    return False
+
+
+@pytest.mark.parametrize("L", [2, 3, 1000, 1024, 1025, 1280, 1281, 1536, 1537, 5000, 22224, 81920,
+                               3728272, 4194305, 5242880, 5333334, 7222224, 10485761, 3 * 2**22])
 def test_plan_invariants(L):
     info = d.dmul_get_plan(None, L)
     N = info.N
     assert N >= L and N >= 1024
-    k = N // 3 if N % 3 == 0 else N
-    assert k & (k - 1) == 0
+    assert _odd_part_admissible(N)
     # smallest admissible length
     for cand in range(L, N):
-        kk = cand // 3 if cand % 3 == 0 else cand
-        assert not (kk & (kk - 1) == 0 and cand >= 1024), cand
+        assert not (_odd_part_admissible(cand) and cand >= 1024), cand
     assert info.N1 * info.N2 == N
     cr = [r for r in info.col_radix if r]
     rr = [r for r in info.row_radix if r]
     assert math.prod(cr) == info.N1 and math.prod(rr) == info.N2
+    # the odd factor is the first column radix; then powers of two, radix 16 last
+    assert all(r in (2, 4, 8, 16) for r in cr[1:] + rr)
+    assert cr[0] in (2, 3, 4, 5, 8, 16)
     assert info.N2 % 32 == 0 and info.N2 <= 8192 and info.N1 <= 1536
     for p in info.primes:
         assert (p - 1) % N == 0
+
+
+def test_five_lengths_cut_the_staircase():
+    """Between 4 2^k and 5 2^k the length set picks 5 2^k, not 6 2^k (Sec. 4.5)."""
+    for k in range(9, 22):
+        L = 4 * 2**k + 1
+        assert d.dmul_get_plan(None, L).N == 5 * 2**k
 
 
 def test_too_large_rejected():

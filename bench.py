@@ -412,6 +412,11 @@ def run_other_configs(d, torch, dev, flush, stream) -> dict:
         ms = time_product(d, torch, dev, ctx6, x, y, 5, flush, stream)
         out["c2_2e24_mul_sixstep"] = {"ms": ms, "digits_per_s": 2 * DIGITS / (ms * 1e-3),
                                       "note": "six-step form with the in-place transposes (Sec. 7.2, 7.6)"}
+        a, b = wl.c3_pairs()[0]
+        ms = time_product(d, torch, dev, ctx6, a, b, 5, flush, stream)
+        out["c3a_64M_x_1M_sixstep"] = {"ms": ms, "digits_per_s": 65_000_000 / (ms * 1e-3),
+                                       "N": int(d.dmul_get_plan(ctx6.handle, len(a) + len(b)).N),
+                                       "note": "six-step form at N = 2^23 (odd power: n x 2n transposes)"}
     return out
 
 

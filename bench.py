@@ -504,25 +504,32 @@ def run_served(d, torch, dev, count=2000, load=0.7, budget_gib=8, loads=(0.1, 0.
         for ld in sorted(set(list(loads) + [load])):
             rate = ld * sat
             arrivals, _ = wl.c5_stream(rate, count)
-            # one thread: submit at each arrival time, and in between watch the oldest outstanding
-            # ticket (completion is observed in arrival order)
+            # one thread: submit at each arrival time, and in between poll every outstanding
+            # ticket, oldest first, so that each request's completion is seen when it happens, not
+            # when the requests before it complete
             tickets = [0] * count
             done_t = [0.0] * count
             start = time.perf_counter() + 0.05
-            i = head = 0
-            while head < count:
+            i = ndone = 0
+            pending = []
+            while ndone < count:
                 now = time.perf_counter()
                 if i < count and now >= start + float(arrivals[i]):
                     rc, tickets[i] = d.dmul_submit(srv.handle, arr[i])
                     assert rc == 0
+                    pending.append(i)
                     i += 1
                     continue
-                if head < i:
-                    rc, done = d.dmul_poll(srv.handle, tickets[head])
+                still = []
+                for k in pending:
+                    rc, done = d.dmul_poll(srv.handle, tickets[k])
                     assert rc == 0
                     if done:
-                        done_t[head] = now
-                        head += 1
+                        done_t[k] = time.perf_counter()
+                        ndone += 1
+                    else:
+                        still.append(k)
+                pending = still
             lat = sorted((done_t[i] - (start + float(arrivals[i]))) * 1e3 for i in range(count))
             wall = max(done_t) - start
             sweep.append({"load": ld, "offered_rate_per_s": rate, "mults_per_s": count / wall,

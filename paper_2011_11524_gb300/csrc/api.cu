@@ -351,12 +351,18 @@ int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
 
 // A lone short product can run as one cluster (the fused kernel: one launch, three SMs) or as the
 // four-step pipeline (four launches, many CTAs).  Which is faster depends on the length; the
-// first product of each short length times both on zero operands (identical results) and keeps
-// the faster.
-int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
+// first product of each short length times both on operands of nonzero limbs (the work of a real
+// product) and keeps the faster.
+int small_single_cached(const dmul_ctx *c, uint64_t Ns) {
+    std::lock_guard<std::mutex> g(c->small_mu);
     auto it = c->small_single.find(Ns);
-    if (it != c->small_single.end()) {
-        *use_small = it->second;
+    return it == c->small_single.end() ? -1 : (it->second ? 1 : 0);
+}
+
+int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
+    const int known = small_single_cached(c, Ns);
+    if (known >= 0) {
+        *use_small = known == 1;
         return DMUL_OK;
     }
     SmallPlanEntry *se;
@@ -409,6 +415,7 @@ int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
     dev_free(c, nzb, 64);
     if (cudaGetLastError() != cudaSuccess) return DMUL_ERR_CUDA;
     *use_small = t_small <= t_four;
+    std::lock_guard<std::mutex> g(c->small_mu);
     c->small_single[Ns] = *use_small;
     return DMUL_OK;
 }

@@ -17,6 +17,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <tuple>
 #include <vector>
 
@@ -339,11 +340,26 @@ cudaError_t launch_small_persistent(const SmallPlanDev *plans, uint32_t maxN, co
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    int clusters = 0;
-    cfg.gridDim = dim3(kPrimes, 1, 1);
-    if (cudaOccupancyMaxActiveClusters(&clusters, k_small_persist, &cfg) != cudaSuccess || clusters < 1) {
-        cudaGetLastError();
-        clusters = sms / kPrimes;
+    // resident clusters for this shared-memory size: queried once per size (the query costs tens
+    // of microseconds, a short product's whole run)
+    static std::mutex occ_mu;
+    static std::map<std::pair<int, size_t>, int> occ;  // (device, shared-memory bytes)
+    int clusters = 0, dev = 0;
+    cudaGetDevice(&dev);
+    const std::pair<int, size_t> key(dev, cfg.dynamicSmemBytes);
+    {
+        std::lock_guard<std::mutex> g(occ_mu);
+        auto it = occ.find(key);
+        if (it != occ.end()) {
+            clusters = it->second;
+        } else {
+            cfg.gridDim = dim3(kPrimes, 1, 1);
+            if (cudaOccupancyMaxActiveClusters(&clusters, k_small_persist, &cfg) != cudaSuccess || clusters < 1) {
+                cudaGetLastError();
+                clusters = sms / kPrimes;
+            }
+            occ[key] = clusters;
+        }
     }
     uint32_t n = std::min<uint32_t>(njobs, (uint32_t)std::max(1, clusters));
     cfg.gridDim = dim3(kPrimes * n, 1, 1);
@@ -621,9 +637,14 @@ int run_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, cudaStream_t s) {
     return run_batch_on(c, b, jobs, count, s, c->status, true);
 }
 
-size_t job_scratch_bytes(const dmul_ctx *c, const dmul_job &j) {
+size_t job_scratch_bytes(const dmul_ctx *c, const dmul_job &j, bool *four) {
     const uint64_t L = j.nx + j.ny;
-    if (choose_N_small(L) && !(c->cfg.flags & (DMUL_FLAG_SIXSTEP | DMUL_FLAG_NO_SMALL))) return 0;
+    if (four) *four = false;
+    const uint64_t Ns = choose_N_small(L);
+    if (Ns && !(c->cfg.flags & (DMUL_FLAG_SIXSTEP | DMUL_FLAG_NO_SMALL))) {
+        if (small_single_cached(c, Ns) != 0) return 0;
+        if (four) *four = true;  // may run as a four-step group (see run_batch_on)
+    }
     const uint64_t N = choose_N(L, !(c->cfg.flags & DMUL_FLAG_NO_RADIX5));
     const bool sq = j.x == j.y && j.nx == j.ny;
     return align256((size_t)kPrimes * N * 4) * (sq ? 1 : 2) + align256(((L + 31) / 32 + 1) * sizeof(uint2)) +
@@ -631,7 +652,7 @@ size_t job_scratch_bytes(const dmul_ctx *c, const dmul_job &j) {
 }
 
 int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count, cudaStream_t s,
-                 uint32_t *status, bool use_graph) {
+                 uint32_t *status, bool use_graph, const uint8_t *four_ok) {
     if (count == 0) return DMUL_OK;
     int rc = DMUL_OK;
     // validate and classify
@@ -655,6 +676,42 @@ int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count,
             if (!it.N) return (c->cfg.flags & DMUL_FLAG_SIXSTEP) ? DMUL_ERR_INVALID : DMUL_ERR_TOO_LARGE;
         }
         items[i] = it;
+    }
+    // Size classes with too few short jobs to fill the GPU with clusters: where the plain form
+    // measured the four-step pipeline faster for a lone product of that length, those jobs run as
+    // four-step groups (a lone short job waits on one cluster's three SMs otherwise).
+    {
+        static int sms = 0;
+        if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        size_t per_class[kSmallClasses] = {0, 0, 0};
+        for (const Item &it : items)
+            if (it.small) per_class[small_class(it.N)]++;
+        for (Item &it : items) {
+            if (!it.small || per_class[small_class(it.N)] * kPrimes >= (size_t)std::max(sms, 1)) continue;
+            bool use_small = true;
+            if (four_ok) {
+                // the serving loop: its scratch was admitted at submission
+                if (!four_ok[it.idx]) {
+                    if (small_single_cached(c, it.N) < 0) {
+                        const dmul_job &j = jobs[it.idx];
+                        const uint64_t N4 = choose_N(j.nx + j.ny, !(c->cfg.flags & DMUL_FLAG_NO_RADIX5));
+                        if ((rc = prefer_small_single(c, it.N, N4, &use_small))) return rc;  // for later
+                    }
+                    continue;
+                }
+                use_small = false;
+            } else {
+                const dmul_job &j = jobs[it.idx];
+                const uint64_t N4 = choose_N(j.nx + j.ny, !(c->cfg.flags & DMUL_FLAG_NO_RADIX5));
+                if ((rc = prefer_small_single(c, it.N, N4, &use_small))) return rc;
+            }
+            if (!use_small) {
+                const dmul_job &j = jobs[it.idx];
+                it.small = false;
+                it.N = choose_N(j.nx + j.ny, !(c->cfg.flags & DMUL_FLAG_NO_RADIX5));
+                if (!it.N) return DMUL_ERR_TOO_LARGE;
+            }
+        }
     }
     // group by (kind, N): the largest transforms first
     std::sort(items.begin(), items.end(), [](const Item &a, const Item &b) {

@@ -75,6 +75,7 @@ struct dmul_ctx {
     std::map<uint64_t, std::unique_ptr<dml::PlanEntry>> plans;
     std::map<uint64_t, std::unique_ptr<dml::SmallPlanEntry>> small_plans;
     std::map<uint64_t, bool> small_single;  // per short length: fused kernel faster than four-step
+    mutable std::mutex small_mu;            // guards small_single (read by dmul_submit callers)
     // scratch of the plain form (one set, used by one call at a time)
     uint32_t *X = nullptr, *Y = nullptr;
     size_t res_words = 0;  // capacity of X and of Y, in words
@@ -140,9 +141,20 @@ void free_batch_state(dmul_ctx *c, BatchState *b);
 // One batch on a given state (arena, descriptors); device errors go to *status.  use_graph:
 // capture/replay per batch shape with groups forked over the state's streams; otherwise plain
 // launches on s.
+//
+// A size class of short products with fewer jobs than it would take to fill the GPU with clusters
+// runs as four-step groups instead when a lone product of that length is faster there (the
+// plain form's measured choice, prefer_small_single).  four_ok (null: every job) marks the jobs
+// whose scratch allows that: the serving loop admits a short job's four-step scratch only when the
+// choice was already known at submission.
 int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count, cudaStream_t s,
-                 uint32_t *status, bool use_graph);
-// Library scratch a job needs on the four-step path (0 for the fused short path).
-size_t job_scratch_bytes(const dmul_ctx *c, const dmul_job &j);
+                 uint32_t *status, bool use_graph, const uint8_t *four_ok = nullptr);
+// Library scratch a job needs on the four-step path: 0 for a short product, unless the measured
+// choice for its length is the four-step pipeline (then *four = true, when four is non-null).
+size_t job_scratch_bytes(const dmul_ctx *c, const dmul_job &j, bool *four = nullptr);
+// The measured choice for lone short products of transform length Ns: 1 fused kernel, 0 four-step,
+// -1 not measured yet.
+int small_single_cached(const dmul_ctx *c, uint64_t Ns);
+int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small);
 
 }  // namespace dml

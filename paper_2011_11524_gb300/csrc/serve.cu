@@ -10,6 +10,23 @@ Server::Server(dmul_ctx *c) : ctx_(c) {
     // admission budget for in-flight scratch: what the context's HBM budget leaves free now
     budget_ = c->budget > c->used ? (c->budget - c->used) : 0;
     init_ok_ = true;
+    // A stream-ordered pool of its own that keeps up to the admission budget mapped between
+    // batches.  The default pool returns freed memory to the driver at every synchronization, so
+    // each large batch would map its scratch afresh (hundreds of microseconds for tens of MB).
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&pool_, &props) != cudaSuccess) {
+        pool_ = nullptr;
+        init_ok_ = false;
+    } else {
+        uint64_t keep = budget_;
+        if (cudaMemPoolSetAttribute(pool_, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess)
+            init_ok_ = false;
+    }
     for (int i = 0; i < kSlots; ++i) {
         auto s = std::make_unique<Slot>();
         s->owner = this;
@@ -38,6 +55,7 @@ Server::~Server() {
         if (s->h_status) cudaFreeHost(s->h_status);
         if (s->stream) cudaStreamDestroy(s->stream);
     }
+    if (pool_) cudaMemPoolDestroy(pool_);
 }
 
 int Server::submit(const dmul_job &job, uint64_t *ticket) {
@@ -46,13 +64,15 @@ int Server::submit(const dmul_job &job, uint64_t *ticket) {
     const uint64_t L = job.nx + job.ny;
     if (job.z_cap < L) return DMUL_ERR_CAPACITY;
     if (!choose_N_small(L) && !choose_N(L)) return DMUL_ERR_TOO_LARGE;
-    const size_t bytes = job_scratch_bytes(ctx_, job);
+    bool four = false;
+    const size_t bytes = job_scratch_bytes(ctx_, job, &four);
     if (bytes > budget_) return DMUL_ERR_NOMEM;
     std::lock_guard<std::mutex> g(mu_);
     uint64_t t = next_++;
     Ticket &tk = tickets_[t];
     tk.job = job;
     tk.bytes = bytes;
+    tk.four = four;
     queue_.push_back(t);
     *ticket = t;
     cv_.notify_all();
@@ -117,12 +137,14 @@ void Server::retire(Slot &s, std::unique_lock<std::mutex> &g) {
 // Admit pending requests into a free slot and launch them as one batch.
 bool Server::launch(Slot &s, std::unique_lock<std::mutex> &g) {
     std::vector<dmul_job> jobs;
+    std::vector<uint8_t> four;
     size_t bytes = 0;
     while (!queue_.empty() && jobs.size() < kMaxBatch) {
         Ticket &tk = tickets_[queue_.front()];
         if (inflight_ + bytes + tk.bytes > budget_) break;  // wait for memory to free up
         bytes += tk.bytes;
         jobs.push_back(tk.job);
+        four.push_back(tk.four ? 1 : 0);
         s.tickets.push_back(queue_.front());
         queue_.pop_front();
     }
@@ -134,13 +156,13 @@ bool Server::launch(Slot &s, std::unique_lock<std::mutex> &g) {
     int rc = DMUL_OK;
     void *arena = nullptr;
     if (bytes) {
-        if (cudaMallocAsync(&arena, bytes, s.stream) != cudaSuccess) rc = DMUL_ERR_NOMEM;
+        if (cudaMallocFromPoolAsync(&arena, bytes, pool_, s.stream) != cudaSuccess) rc = DMUL_ERR_NOMEM;
     }
     if (rc == DMUL_OK) {
         // the scratch of this batch is the pool allocation; the state never reallocates it
         s.bs.arena = (uint8_t *)arena;
         s.bs.arena_cap = bytes;
-        rc = run_batch_on(ctx_, &s.bs, jobs.data(), jobs.size(), s.stream, s.status, false);
+        rc = run_batch_on(ctx_, &s.bs, jobs.data(), jobs.size(), s.stream, s.status, false, four.data());
         s.bs.arena = nullptr;
         s.bs.arena_cap = 0;
     }

@@ -28,7 +28,7 @@ int run_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, cudaStream_t s);
 // stream with its own scratch.  Whenever a slot is free it takes every pending request (FIFO) whose
 // scratch still fits the admission budget, launches them as one batch (grouped by transform
 // length, see batch.cu) and returns to the queue; requests that arrive while batches run join the
-// next one.  Scratch comes from a stream-ordered memory pool (cudaMallocAsync / cudaFreeAsync on
+// next one.  Scratch comes from the server's stream-ordered memory pool (allocated and freed on
 // the slot's stream), so admitting and retiring batches never synchronizes the device.  A slot's
 // completion is signalled by a host callback on its stream.
 class Server {
@@ -46,6 +46,7 @@ class Server {
     struct Ticket {
         dmul_job job;
         size_t bytes = 0;
+        bool four = false;  // its scratch covers the four-step path (a short job; see run_batch_on)
         int status = DMUL_OK;
         bool done = false;
     };
@@ -78,6 +79,7 @@ class Server {
     bool mem_blocked_ = false;  // the head request waits for in-flight scratch to be released
     std::vector<std::unique_ptr<Slot>> slots_;
     size_t budget_ = 0, inflight_ = 0;
+    cudaMemPool_t pool_ = nullptr;  // in-flight scratch (stream-ordered, kept mapped up to budget_)
     std::thread worker_;
 };
 

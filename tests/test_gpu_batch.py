@@ -167,3 +167,36 @@ def test_batch_specialized_splits(d, half):
         for nx, ny, sq in shapes[:1]:
             info = d.dmul_get_plan(c.handle, nx + ny)
             assert (info.N1, info.N2, info.col_half) == (512, 1024, int(half))
+
+
+def test_few_short_jobs_take_the_measured_path(d):
+    """A short job alone (or a handful of one size class) runs as a four-step group when the plain
+    form measured that faster for a lone product of its length; batched and served, alone and
+    again once the choice is known, the results equal the oracle's."""
+    rng = np.random.Generator(np.random.PCG64(71))
+
+    def rand(n):
+        a = rng.integers(0, 10**9, size=n, dtype=np.uint64).astype(np.uint32)
+        a[-1] = max(1, int(a[-1]))
+        return a
+
+    # transform lengths 24576, 16384, 8192 (size class 2) and 3072 (class 1), one squaring
+    jobs = [wl.Job(rand(11112), rand(11112), False), wl.Job(rand(7000), rand(6000), False),
+            wl.Job(rand(3500), rand(3000), False), wl.Job(rand(1500), rand(1200), False)]
+    x = rand(9000)
+    jobs.append(wl.Job(x, x, True))
+    with d.Context(0) as c:
+        for _ in range(2):  # first: the choices get measured; then they are known
+            for k in range(1, len(jobs) + 1):
+                dev = _prep(d, jobs[:k])
+                assert d.dmul_batch(c.handle, d.make_jobs(dev), len(dev)) == 0
+                assert d.dmul_sync(c.handle) == 0
+                _check(d, jobs[:k], dev)
+    with d.Context(0) as srv:
+        for _ in range(2):
+            dev = _prep(d, jobs)
+            arr = d.make_jobs(dev)
+            for i in range(len(jobs)):  # one at a time: every batch holds one job
+                rc, t = d.dmul_submit(srv.handle, arr[i])
+                assert rc == 0 and d.dmul_wait(srv.handle, t) == 0
+            _check(d, jobs, dev)

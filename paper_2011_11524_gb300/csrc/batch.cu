@@ -42,6 +42,10 @@ DMUL_DEFINE_UPLOAD(upload_constants_batch)
 // 16 consecutive rows at 17b + u.
 __device__ __forceinline__ uint32_t spidx(uint32_t a) { return a + (a >> 4); }
 __host__ __device__ constexpr uint32_t small_np(uint32_t N) { return N + N / 16; }
+// CTA size of the one-cluster kernels: one CTA per SM holds a product from N = 8192 up (its shared
+// memory), so it takes the most warps the register file allows (1024 threads at 64 registers) to
+// hide the latency of its twiddle loads and cluster exchanges.
+__host__ __device__ constexpr uint32_t small_threads(uint32_t N) { return N >= 8192 ? 1024u : 256u; }
 
 // forward stage t < ns-1 (twiddled: outputs k > 0 go to their twiddle products unreduced)
 template <int PI, int R>
@@ -241,7 +245,7 @@ __device__ __forceinline__ void small_carry(const JobDev &J, const uint2 *spb, u
 }
 
 // jobs == null: the single job `one` (passed by value, so a lone product needs no descriptor copy)
-__global__ void __launch_bounds__(512) k_small_mul(const SmallPlanDev sp, const JobDev *__restrict__ jobs,
+__global__ void __launch_bounds__(1024) k_small_mul(const SmallPlanDev sp, const JobDev *__restrict__ jobs,
                                                    const JobDev one, uint32_t *status) {
     extern __shared__ uint32_t sm[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -276,7 +280,7 @@ __global__ void __launch_bounds__(512) k_small_mul(const SmallPlanDev sp, const 
 // Persistent form: the cluster's rank-0 CTA draws the next job from the counter and hands it to
 // the other two through distributed shared memory; all three then run the job as k_small_mul
 // does.  The loop ends when the counter passes the job count.
-__global__ void __launch_bounds__(512) k_small_persist(const SmallPlanDev *__restrict__ plans,
+__global__ void __launch_bounds__(1024) k_small_persist(const SmallPlanDev *__restrict__ plans,
                                                        const JobDev *__restrict__ jobs, uint32_t njobs,
                                                        uint32_t maxN, uint32_t *counter,
                                                        uint32_t *status) {
@@ -330,7 +334,7 @@ cudaError_t launch_small_persistent(const SmallPlanDev *plans, uint32_t maxN, co
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.blockDim = dim3(maxN >= 8192 ? 512 : 256, 1, 1);
+    cfg.blockDim = dim3(small_threads(maxN), 1, 1);
     cfg.dynamicSmemBytes = (size_t)2 * small_np(maxN) * 4 + (size_t)(maxN / 32) * sizeof(uint2);
     cfg.stream = s;
     cudaLaunchAttribute at[1];
@@ -372,7 +376,7 @@ static cudaError_t small_launch(const SmallPlanDev &sp, const JobDev *jobs, int 
                                 uint32_t *status, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kPrimes, (unsigned)njobs, 1);
-    cfg.blockDim = dim3(sp.N >= 8192 ? 512 : 256, 1, 1);
+    cfg.blockDim = dim3(small_threads(sp.N), 1, 1);
     cfg.dynamicSmemBytes = small_smem(sp.N);
     cfg.stream = s;
     cudaLaunchAttribute at[1];

@@ -570,7 +570,8 @@ struct SmallLaunch {
 };
 
 static int launch_work(dmul_ctx *c, BatchState *b, const std::vector<GroupLaunch> &groups,
-                       const SmallLaunch &sl, cudaStream_t *streams, int nstreams, uint32_t *status) {
+                       const SmallLaunch &sl, cudaStream_t *streams, int nstreams, uint32_t *status,
+                       bool rows) {
     int si = 0;
     for (int k = 0; k < kSmallClasses; ++k) {
         const SmallClass &sc = sl.cls[k];
@@ -593,7 +594,7 @@ static int launch_work(dmul_ctx *c, BatchState *b, const std::vector<GroupLaunch
         if ((cs ? launch_col_fwd_bs(pd, jd, (int)G.count, status, st)
                 : launch_col_fwd_b(pd, jd, (int)G.count, status, st)) != cudaSuccess)
             return DMUL_ERR_CUDA;
-        if ((rs ? launch_row_pass_ct_b(pd, jd, (int)G.count, st) : launch_row_mul_b(pd, jd, (int)G.count, st)) !=
+        if ((rs ? launch_row_pass_ct_b(pd, jd, (int)G.count, st, rows) : launch_row_mul_b(pd, jd, (int)G.count, st)) !=
             cudaSuccess)
             return DMUL_ERR_CUDA;
         if ((col_pass_specialized(pd) ? launch_col_inv_bs(pd, jd, (int)G.count, st)
@@ -617,11 +618,12 @@ static int upload_and_launch(dmul_ctx *c, BatchState *b, const std::vector<Group
             return DMUL_ERR_CUDA;
     }
     if (ctl_bytes && cudaMemsetAsync(b->arena + ctl_off, 0, ctl_bytes, s) != cudaSuccess) return DMUL_ERR_CUDA;
-    if (!fork) return launch_work(c, b, groups, sl, &s, 1, status);
+    // the serving loop (no fork) keeps one row per CTA; a whole batch takes several (rowpass.cuh)
+    if (!fork) return launch_work(c, b, groups, sl, &s, 1, status, false);
     if (cudaEventRecord(b->fork, s) != cudaSuccess) return DMUL_ERR_CUDA;
     for (int i = 0; i < kBatchStreams; ++i)
         if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) return DMUL_ERR_CUDA;
-    int rc = launch_work(c, b, groups, sl, b->streams, kBatchStreams, status);
+    int rc = launch_work(c, b, groups, sl, b->streams, kBatchStreams, status, true);
     if (rc) return rc;
     for (int i = 0; i < kBatchStreams; ++i) {
         if (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess) return DMUL_ERR_CUDA;

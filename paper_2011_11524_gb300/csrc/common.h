@@ -57,6 +57,7 @@ struct PlanDev {
     uint32_t row_tma;                   // 1: persistent TMA-fed row pass with row_grid CTAs/prime
     uint32_t row_grid;
     uint32_t col_half;                  // 1: column passes on N1 x 16 half tiles (colpass.cu)
+    uint32_t row_rows;                  // rows per CTA of the specialized row pass (set per launch; 0: 1)
     // Per-prime hand-off from the forward column pass to the row pass (null: the row pass waits
     // for the whole column grid instead).  Column CTAs add their column count to fsync[prime] when
     // done; the row pass of a prime starts once fsync[prime] reaches ftarget (a running total).

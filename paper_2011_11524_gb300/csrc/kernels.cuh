@@ -110,7 +110,9 @@ cudaError_t init_kernel_attributes_colpass();
 cudaError_t upload_constants_colpass(const PrimeConst pc[kPrimes], const CrtConst &crt);
 // The specialized row pass for a batch of medium products of one transform length (plain form;
 // squarings per job).
-cudaError_t launch_row_pass_ct_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s);
+// rows: several short rows per CTA where the batch is large enough (dmul_batch; see rowpass.cuh)
+cudaError_t launch_row_pass_ct_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s,
+                                 bool rows = false);
 cudaError_t upload_constants_colpass(const PrimeConst pc[kPrimes], const CrtConst &crt);
 
 // The row pass the plan asks for: specialized when available, else the generic plain or TMA form.

@@ -12,7 +12,8 @@ namespace dml {
     bool rowpass_##TAG##_matches(const PlanDev &pd);                                                   \
     cudaError_t rowpass_##TAG##_run(const PlanDev &pd, uint32_t *X, const uint32_t *Y, bool square,   \
                                    uint32_t *status, cudaStream_t s);                                  \
-    cudaError_t rowpass_##TAG##_run_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s); \
+    cudaError_t rowpass_##TAG##_run_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s, \
+                                     bool rows);                                                       \
     cudaError_t rowpass_##TAG##_attrs();
 DMUL_ROWPASS_DECL(big)
 DMUL_ROWPASS_DECL(small)
@@ -29,8 +30,8 @@ cudaError_t launch_row_pass_ct(const PlanDev &pd, uint32_t *X, const uint32_t *Y
                          : rowpass_small_run(pd, X, Y, square, status, s);
 }
 
-cudaError_t launch_row_pass_ct_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s) {
-    return is_big(pd.N2) ? rowpass_big_run_b(pd, jobs, njobs, s) : rowpass_small_run_b(pd, jobs, njobs, s);
+cudaError_t launch_row_pass_ct_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s, bool rows) {
+    return is_big(pd.N2) ? rowpass_big_run_b(pd, jobs, njobs, s, rows) : rowpass_small_run_b(pd, jobs, njobs, s, rows);
 }
 
 cudaError_t init_kernel_attributes_rowpass() {

@@ -11,7 +11,7 @@ Server::Server(dmul_ctx *c) : ctx_(c) {
     budget_ = c->budget > c->used ? (c->budget - c->used) : 0;
     init_ok_ = true;
     // A stream-ordered pool of its own that keeps up to the admission budget mapped between
-    // batches.  The default pool returns freed memory to the driver at every synchronization, so
+    // batches.  The default pool returns freed memory to the CUDA driver at every synchronization, so
     // each large batch would map its scratch afresh (hundreds of microseconds for tens of MB).
     int dev = 0;
     cudaGetDevice(&dev);

@@ -23,6 +23,9 @@
  * Threading: a context is not thread-safe.  Its device scratch is shared by the calls made on it,
  * so calls on one context must be issued on one stream (or be otherwise serialized), except the
  * served entry points dmul_submit / dmul_poll / dmul_wait, which may be called from any thread.
+ * While the serving loop has work (between the first dmul_submit and the last completion) the
+ * context is its own: the loop plans new lengths and times short ones on the context's plans and
+ * scratch, so the other entry points must not be called on it meanwhile.
  *
  * Errors: every int-returning function returns one of the DMUL_* codes below.
  */

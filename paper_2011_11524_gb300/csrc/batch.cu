@@ -327,12 +327,7 @@ __global__ void __launch_bounds__(1024) k_small_persist(const SmallPlanDev *__re
 
 cudaError_t launch_small_persistent(const SmallPlanDev *plans, uint32_t maxN, const JobDev *jobs,
                                     uint32_t njobs, uint32_t *counter, uint32_t *status, cudaStream_t s) {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
+    const int sms = current_device_sms();
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(small_threads(maxN), 1, 1);
     cfg.dynamicSmemBytes = (size_t)2 * small_np(maxN) * 4 + (size_t)(maxN / 32) * sizeof(uint2);
@@ -687,8 +682,7 @@ int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count,
     // measured the four-step pipeline faster for a lone product of that length, those jobs run as
     // four-step groups (a lone short job waits on one cluster's three SMs otherwise).
     {
-        static int sms = 0;
-        if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        const int sms = current_device_sms();
         size_t per_class[kSmallClasses] = {0, 0, 0};
         for (const Item &it : items)
             if (it.small) per_class[small_class(it.N)]++;

@@ -2,10 +2,32 @@
 #pragma once
 #include <utility>
 #include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
 #include <stdint.h>
 #include "common.h"
 
 namespace dml {
+
+// SM count of the current device, cached per device ordinal (thread-safe: launches come from the
+// caller's threads and the serving loop's).
+inline int current_device_sms() {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        sms = 1;
+    }
+    cache[dev] = sms;
+    return sms;
+}
 
 // Device-side status bits (accumulated in a context word, read by dmul_sync).
 constexpr uint32_t kStatusInvalid = 1u;   // an input limb >= 10^9, or the result overflowed

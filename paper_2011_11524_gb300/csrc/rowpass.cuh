@@ -53,13 +53,7 @@ __device__ __forceinline__ uint32_t pidx(uint32_t a) { return a + (a >> 4); }
 // longer row whose blocks never straddle two rows.
 template <uint32_t N>
 static uint32_t row_rows(uint32_t n1, uint64_t rows_total) {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms < 1) sms = 1;
-    }
+    const int sms = current_device_sms();
     uint32_t r = N >= 4096 ? 1u : 4096u / N;
     while (r > 1 && ((n1 % r) || rows_total / r < 2 * (uint64_t)sms)) r >>= 1;
     return r;

@@ -111,8 +111,12 @@ static int autotune_plan(dmul_ctx *c, uint64_t N, std::unique_ptr<PlanEntry> *be
     HostPlan def;
     if (!make_host_plan(N, &def)) return DMUL_ERR_TOO_LARGE;
     if (n1s.empty()) n1s.push_back(def.N1);
-    // the timing runs reuse the plain form's scratch: earlier work on any stream must be done
+    // the timing runs reuse the plain form's scratch: earlier work on any stream must be done.
+    // The status word is kept as earlier calls left it (an error they set is still reported by
+    // the next dmul_sync); whatever the timing runs set is discarded.
     CK(cudaDeviceSynchronize());
+    uint32_t saved_status = 0;
+    CK(cudaMemcpy(&saved_status, c->status, 4, cudaMemcpyDeviceToHost));
     int rc = ensure_scratch(c, N, N, true);
     if (rc) return rc;
     uint32_t *in = nullptr, *zt = nullptr;
@@ -206,8 +210,7 @@ static int autotune_plan(dmul_ctx *c, uint64_t N, std::unique_ptr<PlanEntry> *be
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(s);
-    uint32_t zero = 0;
-    cudaMemcpy(c->status, &zero, 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(c->status, &saved_status, 4, cudaMemcpyHostToDevice);
     dev_free(c, in, N * 4);
     dev_free(c, zt, N * 4);
     dev_free(c, sp, nsp * sizeof(uint2));
@@ -371,6 +374,8 @@ int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
     if (!rc) rc = get_plan(c, N, &pe);
     if (rc) return rc;
     CK(cudaDeviceSynchronize());
+    uint32_t saved_status = 0;  // kept for the next dmul_sync, as in autotune_plan
+    CK(cudaMemcpy(&saved_status, c->status, 4, cudaMemcpyDeviceToHost));
     const uint64_t Lt = Ns;  // a full-length product: L = N of the short plan
     rc = ensure_scratch(c, N, Lt, true);
     if (rc) return rc;
@@ -409,8 +414,7 @@ int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(s);
-    uint32_t zero = 0;
-    cudaMemcpy(c->status, &zero, 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(c->status, &saved_status, 4, cudaMemcpyHostToDevice);
     dev_free(c, buf, 2 * Lt * 4);
     dev_free(c, nzb, 64);
     if (cudaGetLastError() != cudaSuccess) return DMUL_ERR_CUDA;

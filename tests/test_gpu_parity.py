@@ -308,6 +308,26 @@ def test_invalid_limb_flagged(d, ctx):
     zz, nz = _gpu_mul(d, ctx, x, _rand(_rng(7001), 10))
 
 
+def test_error_survives_first_use_timing(d):
+    """A device-side error of an asynchronous call is still reported by the next dmul_sync when a
+    later call on the context first times a new length (the autotuners' timing runs keep the
+    status word as they found it)."""
+    rng = _rng(7050)
+    with d.Context(0) as c:
+        x = _rand(rng, 5000)
+        x[77] = B  # not a base-10^9 digit
+        tx, ty = d.to_device(x), d.to_device(_rand(rng, 100))
+        z = torch.empty(5100, dtype=torch.int32, device="cuda")
+        assert d.dmul_mul(c.handle, tx, 5000, ty, 100, z, 5100, None) == 0
+        # new lengths: a short one (fused kernel against four-step) and a long one (split search)
+        for n in (6000, 150000):
+            a = d.to_device(_rand(rng, n))
+            zz = torch.empty(2 * n, dtype=torch.int32, device="cuda")
+            assert d.dmul_mul(c.handle, a, n, a, n, zz, 2 * n, None) == 0
+        assert d.dmul_sync(c.handle) == d.DMUL_ERR_INVALID
+        assert d.dmul_sync(c.handle) == 0  # reported once, then cleared
+
+
 def test_argument_errors(d, ctx):
     t = d.to_device(np.ones(10, np.uint32))
     z = torch.empty(30, dtype=torch.int32, device="cuda")
@@ -398,6 +418,22 @@ def test_host_pinned_in_place(d, ctx, ctx_staged, ctx_direct_in, n, m, kind):
     rc, nz = d.dmul_mul_host(c.handle, px, n, py, m, pz, L + 3)
     zz = pz.numpy().view(np.uint32) if hasattr(pz, "numpy") else pz
     assert rc == 0 and np.array_equal(zz[:L], ref)
+
+
+@pytest.mark.parametrize("n,m", [(5000, 7001), (1 << 20, 12345)])
+def test_host_pinned_unaligned_product(d, ctx, n, m):
+    """A page-locked z that starts 4 bytes past a 16-byte boundary: the carry scan writes it in
+    place word by word (the 16-byte stores need alignment)."""
+    rng = _rng(7450 + m)
+    x, y = _pinned(_rand(rng, n)), _pinned(_rand(rng, m))
+    L = n + m
+    buf = torch.zeros(L + 4, dtype=torch.int32).pin_memory()
+    z = buf[1:L + 1]
+    assert z.data_ptr() % 16 == 4 and d.dmul_host_direct(ctx.handle, z)
+    rc, nz = d.dmul_mul_host(ctx.handle, x, n, y, m, z, L)
+    ref = oracle.mul(x.numpy().view(np.uint32), y.numpy().view(np.uint32))
+    assert rc == 0 and np.array_equal(z.numpy().view(np.uint32), ref) and nz == len(oracle.normalize(ref))
+    assert buf[0].item() == 0 and buf[L + 1:].abs().sum().item() == 0  # nothing outside z
 
 
 def test_host_pinned_zero_and_aliasing(d, ctx):

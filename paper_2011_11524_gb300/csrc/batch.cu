@@ -4,7 +4,10 @@
 // prime: limbs -> residues in shared memory, forward transform of x (and y), pointwise product
 // fused with the first inverse stage, inverse transform with the 2^32 N^-1 scale (Sec. 6), then
 // the cluster's CRT through distributed shared memory (Sec. 8.2.2) and the carry recurrence as
-// a block-wide scan of carry maps (Sec. 3.2) in the rank-0 CTA.  One launch, no HBM round trips.
+// a block-wide scan of carry maps (Sec. 3.2) in the rank-0 CTA.  One launch; the residues never
+// leave shared memory (only the digit sums pass through z on their way to the carry).  A size
+// class with too few short jobs to fill the GPU runs them as four-step groups instead, where that
+// measured faster for a lone product of their length (run_batch_on).
 //
 // Larger products run the four-step pipeline (column pass, fused row pass, inverse column pass
 // with CRT, lookahead carry) with a job index in the grid: one launch per stage serves every job of
@@ -545,13 +548,12 @@ static int batch_state(dmul_ctx *c, BatchState **out) {
     return DMUL_OK;
 }
 
-// Enqueue the launches of every group (on the fork/join streams).
-// Every short product of the batch runs in one persistent launch; each group of longer products
-// of one transform length runs as the four batched pipeline launches.  Work items are spread over
-// the given streams.
-// The short products run in up to three persistent launches by size class (transform length up to
-// 1536, 6144, 24576): each launch sizes its shared memory for its class, so that clusters of short
-// jobs pack several to an SM instead of each holding the room of the largest job in the batch.
+// Enqueue the launches of every group (on the fork/join streams).  The short products run in up
+// to three persistent launches by size class (transform length up to 1536, 6144, 24576): each
+// launch sizes its shared memory for its class, so that clusters of short jobs pack several to an
+// SM instead of each holding the room of the largest job in the batch.  Each group of longer
+// products of one transform length runs as the four batched pipeline launches.  Work items are
+// spread over the given streams.
 constexpr int kSmallClasses = 3;
 inline int small_class(uint64_t N) { return N <= 1536 ? 0 : (N <= 6144 ? 1 : 2); }
 struct SmallClass {

@@ -222,7 +222,7 @@ int dmul_transpose(dmul_ctx *ctx, uint32_t *a, size_t rows, size_t cols, void *s
 /* ---- host-side information (no GPU work; usable without a device) ---------------------------- */
 typedef struct {
     uint32_t primes[3];   /* ascending                                                     */
-    uint64_t N;           /* transform length: smallest 2^k or 3*2^k >= L the plan supports */
+    uint64_t N;           /* transform length: smallest 2^k, 3*2^k or 5*2^k >= L (see DMUL_FLAG_NO_RADIX5) */
     uint32_t N1, N2;      /* N = N1 * N2: column length, row length                         */
     uint32_t col_radix[8];/* radix of each column stage, first to last (0 ends the list)   */
     uint32_t row_radix[8];/* radix of each row stage                                        */

@@ -1,7 +1,7 @@
 """GPU parity: every result of libdmul (through its C ABI) against the CPU oracle, bit-exact.
 
-Shapes span every transform class from the smallest (N = 1024) up to 2^17, both length families
-(2^k and 3*2^k), ragged tails (lengths that are not multiples of any tile), unbalanced operands,
+Shapes span every transform class from the smallest (N = 1024) up to 2^17, the length families
+(2^k, 3*2^k and 5*2^k), ragged tails (lengths that are not multiples of any tile), unbalanced operands,
 leading zero limbs, zero, the all-nines worst case and squarings.  Each step of the path is also
 checked on its own through the stage entry points: convolution residues mod each prime (forward
 transforms, pointwise product, inverse transforms), exact coefficients after CRT, the carry scan

@@ -112,3 +112,36 @@ def test_too_large_rejected():
 def test_strerror():
     for st in range(8):
         assert isinstance(d.dmul_strerror(st), str) and d.dmul_strerror(st)
+
+
+def _admissible_lengths():
+    out = set()
+    for k in range(0, 24):
+        for f in (1, 3, 5):
+            n = f << k
+            if 1024 <= n <= 3 * 2**22:
+                out.add(n)
+    return sorted(out)
+
+
+@pytest.mark.parametrize("N", _admissible_lengths())
+def test_every_admissible_length_plans(N):
+    """Every admissible length (1024 .. 3 2^22) plans as itself: N1 N2 = N, the odd factor as the
+    first column radix, power-of-two row schedules ending in radix 16, N2 in [32, 8192], N1 within
+    the shared-memory tile, and N | p - 1 for every prime."""
+    info = d.dmul_get_plan(None, N)
+    assert info.N == N
+    cr = [r for r in info.col_radix if r]
+    rr = [r for r in info.row_radix if r]
+    assert info.N1 * info.N2 == N and math.prod(cr) == info.N1 and math.prod(rr) == info.N2
+    odd = N // (N & -N)
+    assert (cr[0] == odd) if odd > 1 else cr[0] in (2, 4, 8, 16)
+    assert all(r in (2, 4, 8, 16) for r in cr[1:]) and all(r in (2, 4, 8, 16) for r in rr)
+    assert rr[-1] == 16 or info.N2 < 16
+    assert 32 <= info.N2 <= 8192 and info.N1 <= 1536
+    for p in info.primes:
+        assert (p - 1) % N == 0
+    # one less than the length is planned on the same N, one more on a longer one
+    assert d.dmul_get_plan(None, N - 1).N == N
+    if N < 3 * 2**22:
+        assert d.dmul_get_plan(None, N + 1).N > N

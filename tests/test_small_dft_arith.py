@@ -1,5 +1,6 @@
-"""The odd-radix DFTs of the column pass (radix 3 and radix 5, modarith.cuh), emulated on the CPU
-in the kernels' exact 32-bit arithmetic and checked against the DFT's definition (Sec. 3.3):
+"""The kernels' modular arithmetic (modarith.cuh) emulated on the CPU in exact 32-bit steps: the
+Shoup and Montgomery products with their output ranges, and the odd-radix DFTs of the column pass
+(radix 3 and radix 5) checked against the DFT's definition (Sec. 3.3):
 every output congruent to sum_j a_j w^(jk) mod p and inside [0, 2p), for every prime, both
 directions and inputs anywhere in [0, 2p) (including the extremes).  This pins the algebra of the
 radix-5 decomposition (six constant products) and its range bounds, independently of the GPU."""
@@ -103,3 +104,34 @@ def test_radix5_uses_six_products():
         g = smallest_generator(p)
         w = pow(g, (p - 1) // 5, p)
         assert (w + pow(w, 2, p) + pow(w, 3, p) + pow(w, 4, p)) % p == p - 1
+
+
+def mont(a, b, p, pinv):
+    """Subtractive Montgomery: hi(ab) - hi(m p) + p with m = lo(ab) p^-1 mod 2^32."""
+    ab = a * b
+    lo, hi = ab & M32, ab >> 32
+    m = (lo * pinv) & M32
+    t = (m * p) >> 32
+    return (hi - t + p) & M32
+
+
+def test_shoup_and_montgomery_bounds():
+    """Shoup's product takes any 32-bit input and returns a w mod p in [0, 2p) (which is what lets
+    unreduced [0, 4p) sums feed it); the Montgomery product of inputs in [0, 2p) returns
+    a b 2^-32 mod p in (0, 2p) with no correction step (p < 2^30)."""
+    rng = np.random.Generator(np.random.PCG64(36))
+    for p in d.dmul_primes():
+        assert p < 1 << 30
+        pinv = pow(p, -1, 1 << 32)
+        r_inv = pow(1 << 32, -1, p)
+        ws = [int(x) for x in rng.integers(1, p, 40)] + [1, p - 1]
+        edges = [0, 1, p - 1, p, 2 * p - 1, 4 * p - 1, M32]
+        for w in ws:
+            wc = companion(w, p)
+            for a in edges + [int(x) for x in rng.integers(0, 1 << 32, 200, dtype=np.uint64)]:
+                r = shoup(a, w, wc, p)  # asserts r < 2p
+                assert r % p == a * w % p
+        for a in [0, 1, p, 2 * p - 1] + [int(x) for x in rng.integers(0, 2 * p, 300)]:
+            for b in [0, 1, 2 * p - 1] + [int(x) for x in rng.integers(0, 2 * p, 20)]:
+                r = mont(a, b, p, pinv)
+                assert 0 < r < 2 * p and r % p == a * b * r_inv % p

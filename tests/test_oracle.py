@@ -85,6 +85,70 @@ def test_conv_coefficients_vs_definition_tiny():
         assert max(c) <= (B - 1) ** 2 * min(n, m)
 
 
+def test_conv_at_every_k_vs_schoolbook_and_double_loop():
+    """One coefficient c_k = sum_{i+j=k} x_i y_j (Sec. 3.2), the checker of sampled c_k: at every
+    k of several shapes against the schoolbook column sums, and on tiny shapes against a Python
+    double loop.  Both the i-range bounds and both ends (k = 0, k = n+m-1, where c_k = 0) are hit."""
+    rng = _rng(110)
+    for n, m in ((1, 1), (3, 5), (5, 3), (7, 2), (300, 17), (17, 300), (1000, 1000)):
+        x, y = _rand_limbs(rng, n), _rand_limbs(rng, m)
+        c = oracle.conv_schoolbook(x, y, nthreads=1)
+        for k in range(n + m):
+            assert oracle.conv_at(x, y, k) == c[k], (n, m, k)
+        if n * m <= 64:
+            for k in range(n + m):
+                ref = sum(int(x[i]) * int(y[k - i]) for i in range(n) if 0 <= k - i < m)
+                assert oracle.conv_at(x, y, k) == ref
+    # all-nines: every c_k is (B-1)^2 times the number of index pairs, a closed form
+    n, m = 40, 25
+    x, y = np.full(n, B - 1, np.uint32), np.full(m, B - 1, np.uint32)
+    for k in range(n + m):
+        pairs = max(0, min(k, n - 1) - max(0, k - m + 1) + 1)
+        assert oracle.conv_at(x, y, k) == (B - 1) ** 2 * pairs
+
+
+def test_residues_vs_python_mod():
+    """c_k mod p from 128-bit (lo, hi) words, against Python's int %, on hand-built words that
+    exercise each half: 0, 1, 2^64 - 1, 2^64, 2^127 - 1, 2^128 - 1, multiples of p and
+    neighbours."""
+    ps = [377487361, 754974721, 880803841, 2**61 - 1, 3]
+    vals = [0, 1, 2**32, 2**64 - 1, 2**64, 2**64 + 1, 2**96 + 12345, 2**127 - 1, 2**128 - 1,
+            (10**9 - 1) ** 2 * 1864136]
+    for p in ps:
+        vv = vals + [p, p - 1, p + 1, p * (2**64 + 3), p * (2**64 + 3) - 1]
+        vv = [v for v in vv if v < 2**128]
+        words = np.array([[v & (2**64 - 1), v >> 64] for v in vv], dtype=np.uint64)
+        r = oracle.residues(words, p)
+        assert [int(t) for t in r] == [v % p for v in vv]
+
+
+def test_normalize_cases():
+    """Normalized length: strip leading zero limbs, keep at least one (zero is one limb 0)."""
+    z = oracle.normalize(np.zeros(7, np.uint32))
+    assert z.tolist() == [0]
+    z = oracle.normalize(np.zeros(1, np.uint32))
+    assert z.tolist() == [0]
+    a = np.zeros(9, np.uint32)
+    a[8] = 5
+    assert oracle.normalize(a).tolist() == [0] * 8 + [5]
+    a = np.array([3, 0, 7, 0, 0, 0], np.uint32)
+    assert oracle.normalize(a).tolist() == [3, 0, 7]
+    a = np.array([0, 0, 0, 1], np.uint32)
+    assert len(oracle.normalize(a)) == 4
+    a = np.array([B - 1], np.uint32)
+    assert oracle.normalize(a).tolist() == [B - 1]
+    # against Python's int: the normalized limbs are the decimal digits of the value
+    rng = _rng(111)
+    for n in (1, 2, 10, 100):
+        for lead in (0, 1, 5):
+            v = _rand_limbs(rng, n)
+            w = np.concatenate([v, np.zeros(lead, np.uint32)])
+            zn = oracle.normalize(w)
+            assert to_int(zn) == to_int(w)
+            assert zn[-1] != 0 or len(zn) == 1
+            assert len(zn) == max(1, (len(str(to_int(w))) + 8) // 9) if to_int(w) else len(zn) == 1
+
+
 def test_carry_vs_python_int():
     """The carry recurrence against Python's int -> decimal conversion, near-maximal c_k."""
     rng = random.Random(103)

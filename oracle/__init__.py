@@ -81,6 +81,8 @@ def _load():
         lib.or_cyclic_conv_mod.restype = None
         lib.or_fingerprint.argtypes = [u32p, sz, ctypes.c_uint64]
         lib.or_fingerprint.restype = ctypes.c_uint64
+        lib.or_fingerprint_many.argtypes = [u64p, u64p, sz, u64p, sz, u64p, ctypes.c_int]
+        lib.or_fingerprint_many.restype = None
         lib.or_transpose.argtypes = [u32p, sz, sz, u32p]
         lib.or_transpose.restype = None
         lib.or_permute_rows_rho.argtypes = [u32p, sz, sz, u32p]
@@ -195,6 +197,21 @@ def fingerprint(limbs, q: int) -> int:
     lib = _load()
     a = _u32(limbs)
     return int(lib.or_fingerprint(_p32(a), len(a), q))
+
+
+def fingerprint_many(vectors, qs, nthreads: int | None = None) -> np.ndarray:
+    """fingerprint(v, q) for every vector v and modulus q: a (len(vectors), len(qs)) array, the
+    vectors spread over threads (each Horner chain stays on one thread)."""
+    lib = _load()
+    vecs = [_u32(v) for v in vectors]
+    ptrs = np.array([v.ctypes.data for v in vecs], dtype=np.uint64)
+    lens = np.array([len(v) for v in vecs], dtype=np.uint64)
+    qa = np.array([int(q) for q in qs], dtype=np.uint64)
+    out = np.zeros((len(vecs), len(qa)), dtype=np.uint64)
+    if len(vecs) and len(qa):
+        lib.or_fingerprint_many(_p64(ptrs), _p64(lens), len(vecs), _p64(qa), len(qa), _p64(out),
+                                nthreads or default_threads())
+    return out
 
 
 def powmod(a: int, e: int, p: int) -> int:

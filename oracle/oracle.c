@@ -20,7 +20,8 @@
  *                            (no Montgomery, no matrix decomposition), the two-prime CRT formula of
  *                            Sec. 8.2.2 and the carry recurrence.
  *   - or_dft_naive         : the DFT by its definition (Sec. 3.3, eq. dft), O(n^2).
- *   - or_fingerprint       : X mod q of a base-10^9 limb vector by Horner's rule.
+ *   - or_fingerprint       : X mod q of a base-10^9 limb vector by Horner's rule (and
+ *                            or_fingerprint_many: the same for many vectors, threaded by vector).
  *   - or_is_prime_mr       : Miller-Rabin with the first 12 primes as bases (Sec. 4.5).
  *   - or_find_primes       : FindPrimesForN / FindPrimes of Sec. 4.5.
  *   - or_transpose         : the out-of-place transpose (definition; Sec. 7.5 row-major order).
@@ -383,6 +384,42 @@ uint64_t or_fingerprint(const uint32_t *limbs, size_t n, uint64_t q)
     u128 acc = 0;
     for (size_t i = n; i-- > 0;) acc = (acc * OR_BASE + limbs[i]) % q;
     return (uint64_t)acc;
+}
+
+/* The same fingerprint for many limb vectors and moduli: out[v * nq + j] = X_v mod q_j.  Each   */
+/* thread takes whole vectors (the work is split by vector, never inside one Horner chain).     */
+typedef struct {
+    const uint64_t *ptrs, *lens, *qs;
+    size_t count, nq, next;
+    uint64_t *out;
+    pthread_mutex_t *mu;
+} fp_job;
+
+static void *fp_worker(void *arg)
+{
+    fp_job *J = (fp_job *)arg;
+    for (;;) {
+        pthread_mutex_lock(J->mu);
+        size_t v = J->next++;
+        pthread_mutex_unlock(J->mu);
+        if (v >= J->count) break;
+        const uint32_t *limbs = (const uint32_t *)(uintptr_t)J->ptrs[v];
+        for (size_t j = 0; j < J->nq; ++j) J->out[v * J->nq + j] = or_fingerprint(limbs, J->lens[v], J->qs[j]);
+    }
+    return NULL;
+}
+
+void or_fingerprint_many(const uint64_t *ptrs, const uint64_t *lens, size_t count, const uint64_t *qs,
+                         size_t nq, uint64_t *out, int nthreads)
+{
+    pthread_mutex_t mu = PTHREAD_MUTEX_INITIALIZER;
+    fp_job J = {ptrs, lens, qs, count, nq, 0, out, &mu};
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    pthread_t th[256];
+    for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, fp_worker, &J);
+    fp_worker(&J);
+    for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
 }
 
 /* Out-of-place transpose of a rows x cols row-major matrix (Sec. 7: row-major convention). */

@@ -229,6 +229,20 @@ def test_fingerprint_identity_on_products():
             assert oracle.fingerprint(z, q) == oracle.fingerprint(x, q) * oracle.fingerprint(y, q) % q
 
 
+def test_fingerprint_many_vs_python_mod():
+    """The threaded many-vector form against Python's int %, vector by vector and modulus by
+    modulus (a swapped index or a thread writing another vector's slot fails here)."""
+    rng = _rng(108)
+    qs = _fp_moduli()
+    vecs = [_rand_limbs(rng, n) for n in (1, 7, 64, 999, 5000, 2, 31)] + [np.array([B - 1] * 40, np.uint32)]
+    for nt in (1, 3, 8):
+        out = oracle.fingerprint_many(vecs, qs, nthreads=nt)
+        assert out.shape == (len(vecs), len(qs))
+        for v, row in zip(vecs, out):
+            vi = to_int(v)
+            assert [int(t) for t in row] == [vi % q for q in qs]
+
+
 # ----------------------------------------------------------------------------------------------
 # the independent slow NTT route
 # ----------------------------------------------------------------------------------------------

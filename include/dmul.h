@@ -48,7 +48,9 @@ extern "C" {
 #define DMUL_ERR_TIMEOUT 4   /* a bounded device-side wait expired (the result is not valid)    */
 #define DMUL_ERR_CUDA 5      /* a CUDA runtime call failed                                      */
 #define DMUL_ERR_CAPACITY 6  /* z_cap < nx + ny                                                 */
-#define DMUL_ERR_UNKNOWN_TICKET 7 /* dmul_poll / dmul_wait on a ticket that was never issued    */
+#define DMUL_ERR_UNKNOWN_TICKET 7 /* dmul_poll / dmul_wait on a ticket that was never issued,   */
+                                  /* or whose result was already returned (see dmul_wait)        */
+#define DMUL_PENDING (-1)         /* dmul_job.status of a job whose batch has not been checked yet */
 
 /* ---- context ------------------------------------------------------------------------------- */
 typedef struct dmul_ctx dmul_ctx;
@@ -75,6 +77,15 @@ typedef struct dmul_ctx dmul_ctx;
 #define DMUL_FLAG_HOST_STAGED_OUT 128u /* dmul_mul_host: write the product to a device buffer    */
                                        /* and copy it out, instead of writing a page-locked z    */
                                        /* in place                                               */
+#define DMUL_FLAG_SHORT_WAITS 1024u    /* bound every device-side wait (carry look-back, column-  */
+                                       /* to-row hand-off, bulk-copy barriers) by 2^13 polls, a  */
+                                       /* few milliseconds, instead of seconds: an expired wait  */
+                                       /* reports DMUL_ERR_TIMEOUT soon (for tests of that path) */
+#define DMUL_FLAG_TEST_STALL_CARRY 2048u /* fault injection for tests, on the host side:        */
+                                       /* dmul_carry starts its tile ticket at 1, so that tile 0 */
+                                       /* never runs and tile 1's bounded look-back wait expires */
+                                       /* (DMUL_ERR_TIMEOUT at the next dmul_sync); the kernels  */
+                                       /* end normally and the context stays usable              */
 
 typedef struct {
     int device;                /* CUDA device ordinal                                          */
@@ -98,7 +109,9 @@ const char *dmul_strerror(int status);
 
 /* Synchronize `stream` and return the device-side status accumulated by the work enqueued on
  * this context since the previous dmul_sync (DMUL_OK, DMUL_ERR_INVALID, DMUL_ERR_TIMEOUT), then
- * clear it.  Returns DMUL_ERR_CUDA if the synchronization itself fails. */
+ * clear it.  It also fills the status field of every job of the last dmul_batch (see there); a
+ * failed batch job makes this return that job's error too.  Returns DMUL_ERR_CUDA if the
+ * synchronization itself fails. */
 int dmul_sync(dmul_ctx *ctx, void *stream);
 
 /* ---- the plain form -------------------------------------------------------------------------- */
@@ -146,13 +159,24 @@ typedef struct {
     uint32_t *z;       /* device pointer, z_cap >= nx + ny                                */
     uint64_t z_cap;
     uint64_t *nz;      /* device pointer or NULL                                          */
+    int status;        /* out (dmul_batch): this job's own status, see dmul_batch          */
 } dmul_job;
 
 /* Run `count` independent multiplications (jobs: HOST array of descriptors holding device
  * pointers).  Jobs are grouped by transform length; each group runs as batched launches that
  * process all of its jobs at once, and a repeated batch shape replays a captured CUDA graph.
- * Results are identical to calling dmul_mul on each job.  Asynchronous on `stream`. */
-int dmul_batch(dmul_ctx *ctx, const dmul_job *jobs, size_t count, void *stream);
+ * Results are identical to calling dmul_mul on each job.  Asynchronous on `stream`.
+ *
+ * Every job has its own status, so one bad job does not fail the others:
+ *  - a job the host rejects (null pointer, nx or ny = 0, z_cap < nx + ny, z overlapping x or y,
+ *    too large) gets that code in jobs[i].status at once and is not run;
+ *  - every other job gets DMUL_PENDING, replaced by its final status (DMUL_OK, DMUL_ERR_INVALID
+ *    for a limb >= 10^9, DMUL_ERR_TIMEOUT) by the next dmul_sync or dmul_batch on the context,
+ *    so `jobs` must stay valid until then.
+ * Returns DMUL_OK when the accepted jobs (possibly none) were enqueued; any other code is a
+ * failure of the call itself (bad context or array, budget, CUDA), with every job's status set
+ * to it and nothing run. */
+int dmul_batch(dmul_ctx *ctx, dmul_job *jobs, size_t count, void *stream);
 
 /* ---- the served form ------------------------------------------------------------------------- */
 /* Enqueue one job for the context's serving loop (a host thread that continuously batches
@@ -162,11 +186,29 @@ int dmul_batch(dmul_ctx *ctx, const dmul_job *jobs, size_t count, void *stream);
  * dmul_wait.  Thread-safe. */
 int dmul_submit(dmul_ctx *ctx, const dmul_job *job, uint64_t *ticket);
 
-/* *done = 1 when the ticket's result is in z (and *nz), else 0.  Thread-safe. */
+/* *done = 1 when the ticket's result is in z (and *nz), else 0.  With *done = 1 the return value
+ * is the ticket's own status (a request is never failed by another request of its batch) and the
+ * ticket is released: later calls on it return DMUL_ERR_UNKNOWN_TICKET.  Thread-safe. */
 int dmul_poll(dmul_ctx *ctx, uint64_t ticket, int *done);
 
-/* Block until the ticket completes; returns its status.  Thread-safe. */
+/* Block until the ticket completes; returns its own status and releases the ticket (each
+ * ticket's result is returned once, by dmul_wait or by the dmul_poll that reports it done; a
+ * later or concurrent second call gets DMUL_ERR_UNKNOWN_TICKET).  Thread-safe. */
 int dmul_wait(dmul_ctx *ctx, uint64_t ticket);
+
+/* Serving-loop counters, a snapshot (thread-safe; all zero before the first dmul_submit). */
+typedef struct {
+    uint64_t queued;             /* submitted requests not yet launched                          */
+    uint64_t running;            /* requests in batches on the GPU                                */
+    uint64_t held;               /* tickets issued and not yet released by dmul_wait / dmul_poll  */
+                                 /* (queued + running + completed but not yet claimed)            */
+    uint64_t peak_running;       /* the most requests on the GPU at once so far                   */
+    uint64_t admit_budget_bytes; /* device memory the loop may give to in-flight requests: the   */
+                                 /* context's HBM budget minus what the context held when the    */
+                                 /* loop started                                                  */
+    uint64_t inflight_bytes;     /* of which in use now                                           */
+} dmul_serve_info;
+int dmul_serve_stats(dmul_ctx *ctx, dmul_serve_info *out);
 
 /* ---- stage-level entry points (each step of the path on its own, for checking) --------------- */
 /* The convolution residues c_k mod p_i (Sec. 3.2 + Sec. 3.3 eq. conv_theorem + Sec. 6) for
@@ -200,13 +242,16 @@ int dmul_carry(dmul_ctx *ctx, const uint32_t *d, size_t L, uint32_t *z, size_t z
  * Arguments as dmul_carry: d holds L base-10^9 digit triples (device), z receives L limbs (device,
  * z_cap >= L, not overlapping d), nz (device pointer or NULL) the normalized length.  L may be at
  * most DMUL_NOALLOC_MAX_LIMBS; longer inputs return DMUL_ERR_TOO_LARGE without touching the GPU.
- * Device-side errors (the sum does not fit L limbs, an expired bounded wait) set *nz to 0, a value
- * no valid result has; pass nz to see them.  Asynchronous on `stream`, on the current device.
+ * Return value: DMUL_OK once the work is enqueued, or a host-side error (arguments, size, CUDA)
+ * with nothing enqueued.  It never reports device-side errors (the sum does not fit L limbs, an
+ * expired bounded wait): those set *nz to 0, a value no valid result has, so a caller who needs
+ * to see them must pass nz; with nz = NULL they are not observable.  Asynchronous on `stream`, on
+ * the current device.
  *
- * The first call on a device looks up the array's device address (once per device); make that
- * first call before any stream capture.  All calls share the one array and the next call
- * overwrites it: calls whose work overlaps on the GPU (different streams, or several host threads)
- * race and must be serialized by the caller. */
+ * The first call on a device (and again after a device reset, which creates a new context) looks
+ * up the array's device address; make that first call before any stream capture.  All calls
+ * share the one array and the next call overwrites it: calls whose work overlaps on the GPU
+ * (different streams, or several host threads) race and must be serialized by the caller. */
 #define DMUL_NOALLOC_MAX_LIMBS (1ull << 22)
 int dmul_carry_noalloc(const uint32_t *d, size_t L, uint32_t *z, size_t z_cap, uint64_t *nz,
                        void *stream);

@@ -24,6 +24,10 @@ using namespace dml;
 
 namespace dml {
 
+// Bound of every device-side wait under DMUL_FLAG_SHORT_WAITS: a few milliseconds of polling,
+// long enough for any legitimate wait of a product.
+constexpr uint32_t kShortWaitPolls = 1u << 13;
+
 static int cuda_fail(cudaError_t e) {
     (void)e;
     return DMUL_ERR_CUDA;
@@ -484,7 +488,7 @@ int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, si
     }
     if (mode == kInvDigits) {
         Timed t(c, kStCarry, s);
-        CK(launch_carry(z, c->spill, L, (CarryCtl *)c->ctl, nz, c->status, s, z_out));
+        CK(launch_carry(z, c->spill, L, (CarryCtl *)c->ctl, nz, c->status, s, z_out, c->spin_limit));
     }
     return DMUL_OK;
 }
@@ -494,21 +498,42 @@ int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
     if (!(c->cfg.flags & DMUL_FLAG_SIXSTEP)) {
         // The row pass of a prime starts once that prime's forward columns are done (per-prime
         // counters, running totals: this call adds operands x N2 columns to every prime's count).
+        // The counters are never reset: a row CTA may start, through the chain of early
+        // (programmatic) launches, while the previous call's kernels still run, and a total that
+        // only grows can never be met by that call's columns.  The host's total therefore counts
+        // only launches that were accepted.  Inside a stream capture the hand-off is off (the row
+        // pass waits for the whole column grid): a replayed graph would move the device counters
+        // without the host's total.
         PlanDev pd = pe->pd;
-        c->fwd_cols += (square ? 1u : 2u) * pd.N2;
-        pd.fsync = c->fwd_sync;
-        pd.ftarget = c->fwd_cols;
+        pd.spin = c->spin_limit;
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        CK(cudaStreamIsCapturing(s, &cap));
+        const bool handoff = cap == cudaStreamCaptureStatusNone;
+        const uint32_t before = c->fwd_cols;
+        if (handoff) {
+            pd.fsync = c->fwd_sync;
+            pd.ftarget = before + (square ? 1u : 2u) * pd.N2;
+        } else {
+            pd.fsync = nullptr;
+        }
+        cudaError_t e;
         if (y_ready && !square) {
             // x's forward pass first, then (once y is uploaded) y's
             Timed t(c, kStColFwd, s);
-            CK(launch_col_fwd(pd, x, nx, nullptr, 0, c->X, nullptr, c->status, s));
-            CK(cudaStreamWaitEvent(s, y_ready, 0));
-            CK(launch_col_fwd(pd, y, ny, nullptr, 0, c->Y, nullptr, c->status, s));
+            e = launch_col_fwd(pd, x, nx, nullptr, 0, c->X, nullptr, c->status, s);
+            if (e == cudaSuccess) {
+                if (handoff) c->fwd_cols += pd.N2;
+                e = cudaStreamWaitEvent(s, y_ready, 0);
+                if (e == cudaSuccess) e = launch_col_fwd(pd, y, ny, nullptr, 0, c->Y, nullptr, c->status, s);
+                if (e == cudaSuccess && handoff) c->fwd_cols += pd.N2;
+            }
         } else {
-            if (y_ready) CK(cudaStreamWaitEvent(s, y_ready, 0));
+            e = y_ready ? cudaStreamWaitEvent(s, y_ready, 0) : cudaSuccess;
             Timed t(c, kStColFwd, s);
-            CK(launch_col_fwd(pd, x, nx, square ? nullptr : y, ny, c->X, c->Y, c->status, s));
+            if (e == cudaSuccess) e = launch_col_fwd(pd, x, nx, square ? nullptr : y, ny, c->X, c->Y, c->status, s);
+            if (e == cudaSuccess && handoff) c->fwd_cols += (square ? 1u : 2u) * pd.N2;
         }
+        if (e != cudaSuccess) return DMUL_ERR_CUDA;
         Timed t(c, kStRowMul, s);
         CK(launch_row_any(pd, c->X, c->Y, square, c->status, s));
         return DMUL_OK;
@@ -583,6 +608,7 @@ const char *dmul_strerror(int st) {
         case DMUL_ERR_CUDA: return "CUDA runtime error";
         case DMUL_ERR_CAPACITY: return "output capacity too small";
         case DMUL_ERR_UNKNOWN_TICKET: return "unknown ticket";
+        case DMUL_PENDING: return "pending";
         default: return "unknown status";
     }
 }
@@ -641,6 +667,7 @@ int dmul_init(dmul_ctx **out, const dmul_config *cfg) {
     c->device = c->cfg.device;
     c->budget = c->cfg.hbm_budget_bytes ? c->cfg.hbm_budget_bytes : (16ull << 30);
     c->timing = (c->cfg.flags & DMUL_FLAG_STAGE_TIMING) != 0;
+    if (c->cfg.flags & DMUL_FLAG_SHORT_WAITS) c->spin_limit = kShortWaitPolls;
     for (int i = 0; i < kNumStages; ++i) c->timers.push_back(StageTimer{kStageNames[i]});
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || c->device < 0 || c->device >= ndev) {
@@ -709,9 +736,14 @@ int dmul_sync(dmul_ctx *c, void *stream) {
     uint32_t st = 0;
     CK(cudaMemcpy(&st, c->status, 4, cudaMemcpyDeviceToHost));
     if (st) CK(cudaMemset(c->status, 0, 4));
-    if (st & kStatusTimeout) return DMUL_ERR_TIMEOUT;
+    // the last dmul_batch's jobs get their own statuses; a failed one is reported here too
+    int jb = c->batch ? flush_batch_status(c->batch.get()) : DMUL_OK;
+    if (c->batch_err && jb != DMUL_ERR_TIMEOUT) jb = jb ? jb : c->batch_err;
+    if (c->batch_err == DMUL_ERR_TIMEOUT) jb = DMUL_ERR_TIMEOUT;
+    c->batch_err = DMUL_OK;
+    if ((st & kStatusTimeout) || jb == DMUL_ERR_TIMEOUT) return DMUL_ERR_TIMEOUT;
     if (st & kStatusInvalid) return DMUL_ERR_INVALID;
-    return DMUL_OK;
+    return jb;
 }
 
 int dmul_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny, uint32_t *z,
@@ -751,8 +783,14 @@ int dmul_carry(dmul_ctx *c, const uint32_t *d, size_t L, uint32_t *z, size_t z_c
     c->last_stream = s;
     CK(launch_triples_to_digits(d, L, z, c->spill, c->status, s));
     CK(cudaMemsetAsync(c->ctl, 0, carry_ctl_bytes(L), s));
+    if (c->cfg.flags & DMUL_FLAG_TEST_STALL_CARRY) {
+        // fault injection on the host side: the scan's tile ticket starts at 1, so no CTA becomes
+        // tile 0 and tile 1 waits for a publication that never comes (bounded by spin_limit)
+        static const uint32_t one = 1;
+        CK(cudaMemcpyAsync(c->ctl, &one, 4, cudaMemcpyHostToDevice, s));
+    }
     Timed t(c, kStCarry, s);
-    CK(launch_carry(z, c->spill, L, (CarryCtl *)c->ctl, nz, c->status, s));
+    CK(launch_carry(z, c->spill, L, (CarryCtl *)c->ctl, nz, c->status, s, nullptr, c->spin_limit));
     return DMUL_OK;
 }
 
@@ -884,8 +922,12 @@ int dmul_mul_host(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, 
     return DMUL_OK;
 }
 
-int dmul_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, void *stream) {
-    if (!c || (!jobs && count)) return DMUL_ERR_INVALID;
+int dmul_batch(dmul_ctx *c, dmul_job *jobs, size_t count, void *stream) {
+    if (!c) {
+        for (size_t i = 0; jobs && i < count; ++i) jobs[i].status = DMUL_ERR_INVALID;
+        return DMUL_ERR_INVALID;
+    }
+    if (!jobs && count) return DMUL_ERR_INVALID;
     return dml::run_batch(c, jobs, count, (cudaStream_t)stream);
 }
 
@@ -912,6 +954,14 @@ int dmul_wait(dmul_ctx *c, uint64_t ticket) {
     dml::Server *s = server_of(c, false);
     if (!s) return DMUL_ERR_UNKNOWN_TICKET;
     return s->wait(ticket);
+}
+
+int dmul_serve_stats(dmul_ctx *c, dmul_serve_info *out) {
+    if (!c || !out) return DMUL_ERR_INVALID;
+    memset(out, 0, sizeof(*out));
+    dml::Server *s = server_of(c, false);
+    if (s) s->stats(out);
+    return DMUL_OK;
 }
 
 int dmul_stage_times(dmul_ctx *c, const char **names, double *ms, uint64_t *launches, int *n) {

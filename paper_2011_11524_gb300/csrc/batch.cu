@@ -254,6 +254,7 @@ __global__ void __launch_bounds__(1024) k_small_mul(const SmallPlanDev sp, const
     cg::cluster_group cluster = cg::this_cluster();
     const int pi = (int)cluster.block_rank();
     const JobDev J = jobs ? jobs[blockIdx.y] : one;
+    status = job_status(J, status);
     uint32_t *sx = sm, *sy = sm + small_np(sp.N);
     uint2 *spb = (uint2 *)(sm + 2 * small_np(sp.N));
     DMUL_PRIME_SWITCH(pi, (small_transform<PI>(sp, J, sx, sy, status)));
@@ -304,7 +305,8 @@ __global__ void __launch_bounds__(1024) k_small_persist(const SmallPlanDev *__re
         if (j >= njobs) break;
         const JobDev J = jobs[j];
         const SmallPlanDev &sp = plans[J.plan];
-        DMUL_PRIME_SWITCH(pi, (small_transform<PI>(sp, J, sx, sy, status)));
+        uint32_t *jst = job_status(J, status);
+        DMUL_PRIME_SWITCH(pi, (small_transform<PI>(sp, J, sx, sy, jst)));
         cluster.sync();
         const uint32_t *s0 = cluster.map_shared_rank(sx, 0);
         const uint32_t *s1 = cluster.map_shared_rank(sx, 1);
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(1024) k_small_persist(const SmallPlanDev *__re
         }
         __threadfence();
         cluster.sync();
-        if (pi == 0) small_carry(J, spb, status);
+        if (pi == 0) small_carry(J, spb, jst);
         cluster.sync();  // shared memory is reused by the next job
     }
 }
@@ -413,7 +415,7 @@ __global__ void __launch_bounds__(512) k_col_fwd_b(const PlanDev pd, const JobDe
     const uint32_t *src = second ? J.y : J.x;
     const uint64_t n = second ? J.ny : J.nx;
     uint32_t *dst = (second ? J.Y : J.X) + (uint64_t)pi * pd.N;
-    DMUL_PRIME_SWITCH(pi, (col_fwd_body<PI>(pd, sm, src, n, dst, tile, status)));
+    DMUL_PRIME_SWITCH(pi, (col_fwd_body<PI>(pd, sm, src, n, dst, tile, job_status(J, status))));
 }
 
 __global__ void __launch_bounds__(256) k_row_mul_b(const PlanDev pd, const JobDev *__restrict__ jobs) {
@@ -439,7 +441,7 @@ __global__ void __launch_bounds__(512) k_col_inv_b(const PlanDev pd, const JobDe
 __global__ void __launch_bounds__(256) k_carry_b(const JobDev *__restrict__ jobs, uint32_t *status) {
     const JobDev &J = jobs[blockIdx.y];
     if (blockIdx.x >= J.ntiles) return;
-    carry_tile<256, 8>(J.z, J.z, J.spill, J.L, J.ctl, J.nz, status, J.ntiles);
+    carry_tile<256, 8>(J.z, J.z, J.spill, J.L, J.ctl, J.nz, job_status(J, status), J.ntiles);
 }
 
 cudaError_t init_kernel_attributes_batch() {
@@ -517,10 +519,16 @@ void free_batch_state(dmul_ctx *c, BatchState *b) {
     b->graphs.clear();
     if (b->arena) dev_free(c, b->arena, b->arena_cap);
     if (b->djobs) dev_free(c, b->djobs, b->jobs_cap * sizeof(JobDev));
+    if (b->dstat) dev_free(c, b->dstat, b->jobs_cap * sizeof(uint32_t));
     if (b->hjobs) cudaFreeHost(b->hjobs);
+    if (b->hstat) cudaFreeHost(b->hstat);
     b->arena = nullptr;
     b->djobs = nullptr;
+    b->dstat = nullptr;
     b->hjobs = nullptr;
+    b->hstat = nullptr;
+    b->pending = false;
+    b->pend_jobs = nullptr;
     for (int i = 0; i < kBatchStreams; ++i) {
         if (b->streams[i]) cudaStreamDestroy(b->streams[i]);
         if (b->join[i]) cudaEventDestroy(b->join[i]);
@@ -606,7 +614,8 @@ static int launch_work(dmul_ctx *c, BatchState *b, const std::vector<GroupLaunch
 static int upload_and_launch(dmul_ctx *c, BatchState *b, const std::vector<GroupLaunch> &groups,
                              const SmallLaunch &sl, cudaStream_t s, size_t njobs, size_t ctl_off,
                              size_t ctl_bytes, uint32_t *status, bool fork) {
-    if (cudaMemcpyAsync(b->djobs, b->hjobs, njobs * sizeof(JobDev), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    if (cudaMemcpyAsync(b->djobs, b->hjobs, njobs * sizeof(JobDev), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(b->dstat, 0, njobs * sizeof(uint32_t), s) != cudaSuccess)
         return DMUL_ERR_CUDA;
     if (sl.count) {
         if (cudaMemcpyAsync(b->dplans, b->hplans, sl.nplans * sizeof(SmallPlanDev), cudaMemcpyHostToDevice, s) !=
@@ -616,28 +625,65 @@ static int upload_and_launch(dmul_ctx *c, BatchState *b, const std::vector<Group
     }
     if (ctl_bytes && cudaMemsetAsync(b->arena + ctl_off, 0, ctl_bytes, s) != cudaSuccess) return DMUL_ERR_CUDA;
     // the serving loop (no fork) keeps one row per CTA; a whole batch takes several (rowpass.cuh)
-    if (!fork) return launch_work(c, b, groups, sl, &s, 1, status, false);
-    if (cudaEventRecord(b->fork, s) != cudaSuccess) return DMUL_ERR_CUDA;
-    for (int i = 0; i < kBatchStreams; ++i)
-        if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) return DMUL_ERR_CUDA;
-    int rc = launch_work(c, b, groups, sl, b->streams, kBatchStreams, status, true);
-    if (rc) return rc;
-    for (int i = 0; i < kBatchStreams; ++i) {
-        if (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess) return DMUL_ERR_CUDA;
-        if (cudaStreamWaitEvent(s, b->join[i], 0) != cudaSuccess) return DMUL_ERR_CUDA;
+    if (!fork) {
+        int rc = launch_work(c, b, groups, sl, &s, 1, status, false);
+        if (rc) return rc;
+    } else {
+        if (cudaEventRecord(b->fork, s) != cudaSuccess) return DMUL_ERR_CUDA;
+        for (int i = 0; i < kBatchStreams; ++i)
+            if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) return DMUL_ERR_CUDA;
+        int rc = launch_work(c, b, groups, sl, b->streams, kBatchStreams, status, true);
+        if (rc) return rc;
+        for (int i = 0; i < kBatchStreams; ++i) {
+            if (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess) return DMUL_ERR_CUDA;
+            if (cudaStreamWaitEvent(s, b->join[i], 0) != cudaSuccess) return DMUL_ERR_CUDA;
+        }
     }
+    // every job's own status word, for the caller (dmul_batch) or the serving loop's tickets
+    if (cudaMemcpyAsync(b->hstat, b->dstat, njobs * sizeof(uint32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return DMUL_ERR_CUDA;
     return DMUL_OK;
 }
 
-int run_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, cudaStream_t s) {
+int flush_batch_status(BatchState *b) {
+    if (!b->pending) return DMUL_OK;
+    b->pending = false;
+    if (b->done_recorded && cudaEventSynchronize(b->done) != cudaSuccess) return DMUL_ERR_CUDA;
+    int agg = DMUL_OK;
+    for (size_t i = 0; i < b->launched; ++i) {
+        const int rc = device_code(b->hstat[i]);
+        b->pend_jobs[b->order[i]].status = rc;
+        if (rc == DMUL_ERR_TIMEOUT || (rc && !agg)) agg = rc;
+    }
+    b->pend_jobs = nullptr;
+    return agg;
+}
+
+int run_batch(dmul_ctx *c, dmul_job *jobs, size_t count, cudaStream_t s) {
     BatchState *b;
+    auto fail_all = [&](int rc) {
+        for (size_t i = 0; i < count; ++i) jobs[i].status = rc;
+        return rc;
+    };
     int rc = set_device(c);
-    if (rc) return rc;
+    if (rc) return fail_all(rc);
     rc = batch_state(c, &b);
-    if (rc) return rc;
+    if (rc) return fail_all(rc);
+    // the previous batch's jobs get their statuses before this batch reuses the state; an error
+    // among them is kept for the next dmul_sync
+    const int prev = flush_batch_status(b);
+    if (prev && c->batch_err != DMUL_ERR_TIMEOUT) c->batch_err = prev;
     c->last_stream = s;
-    Timed t(c, kStBatch, s);
-    return run_batch_on(c, b, jobs, count, s, c->status, true);
+    std::vector<int> hs(count, DMUL_OK);
+    {
+        Timed t(c, kStBatch, s);
+        rc = run_batch_on(c, b, jobs, count, s, c->status, true, hs.data());
+    }
+    if (rc) return fail_all(rc);
+    for (size_t i = 0; i < count; ++i) jobs[i].status = hs[i] ? hs[i] : DMUL_PENDING;
+    b->pend_jobs = jobs;
+    b->pending = true;
+    return DMUL_OK;
 }
 
 size_t job_scratch_bytes(const dmul_ctx *c, const dmul_job &j, bool *four) {
@@ -654,32 +700,46 @@ size_t job_scratch_bytes(const dmul_ctx *c, const dmul_job &j, bool *four) {
            align256(carry_ctl_bytes(L));
 }
 
-int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count, cudaStream_t s,
-                 uint32_t *status, bool use_graph, const uint8_t *four_ok) {
-    if (count == 0) return DMUL_OK;
+// The host-side verdict on one job: DMUL_OK, or the code that keeps it out of the launch.
+static int check_job(const dmul_ctx *c, const dmul_job &j) {
+    if (!j.x || !j.y || !j.z || j.nx == 0 || j.ny == 0) return DMUL_ERR_INVALID;
+    const uint64_t L = j.nx + j.ny;
+    if (j.z_cap < L) return DMUL_ERR_CAPACITY;
+    if (overlaps(j.z, L * 4, j.x, j.nx * 4) || overlaps(j.z, L * 4, j.y, j.ny * 4)) return DMUL_ERR_INVALID;
+    if (std::min(j.nx, j.ny) > max_min_limbs()) return DMUL_ERR_TOO_LARGE;
+    if (c->cfg.max_limbs && L > c->cfg.max_limbs) return DMUL_ERR_TOO_LARGE;
+    if (c->cfg.flags & DMUL_FLAG_SIXSTEP) return DMUL_ERR_INVALID;  // the batched form is four-step only
+    if (!choose_N_small(L) && !choose_N(L, !(c->cfg.flags & DMUL_FLAG_NO_RADIX5))) {
+        return DMUL_ERR_TOO_LARGE;
+    }
+    return DMUL_OK;
+}
+
+int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count_in, cudaStream_t s,
+                 uint32_t *status, bool use_graph, int *host_status, const uint8_t *four_ok) {
     int rc = DMUL_OK;
-    // validate and classify
+    b->launched = 0;
+    // validate (per job: a rejected job is left out, the others run) and classify
     struct Item { size_t idx; bool small; uint64_t N; bool square; };
-    std::vector<Item> items(count);
-    for (size_t i = 0; i < count; ++i) {
+    std::vector<Item> items;
+    items.reserve(count_in);
+    for (size_t i = 0; i < count_in; ++i) {
         const dmul_job &j = jobs[i];
-        if (!j.x || !j.y || !j.z || j.nx == 0 || j.ny == 0) return DMUL_ERR_INVALID;
+        host_status[i] = check_job(c, j);
+        if (host_status[i]) continue;
         const uint64_t L = j.nx + j.ny;
-        if (j.z_cap < L) return DMUL_ERR_CAPACITY;
-        if (overlaps(j.z, L * 4, j.x, j.nx * 4) || overlaps(j.z, L * 4, j.y, j.ny * 4)) return DMUL_ERR_INVALID;
-        if (std::min(j.nx, j.ny) > max_min_limbs()) return DMUL_ERR_TOO_LARGE;
-        if (c->cfg.max_limbs && L > c->cfg.max_limbs) return DMUL_ERR_TOO_LARGE;
         Item it{i, false, 0, j.x == j.y && j.nx == j.ny};
         uint64_t Ns = choose_N_small(L);
         if (Ns && !(c->cfg.flags & (DMUL_FLAG_SIXSTEP | DMUL_FLAG_NO_SMALL))) {
             it.small = true;
             it.N = Ns;
         } else {
-            it.N = (c->cfg.flags & DMUL_FLAG_SIXSTEP) ? 0 : choose_N(L, !(c->cfg.flags & DMUL_FLAG_NO_RADIX5));
-            if (!it.N) return (c->cfg.flags & DMUL_FLAG_SIXSTEP) ? DMUL_ERR_INVALID : DMUL_ERR_TOO_LARGE;
+            it.N = choose_N(L, !(c->cfg.flags & DMUL_FLAG_NO_RADIX5));
         }
-        items[i] = it;
+        items.push_back(it);
     }
+    const size_t count = items.size();
+    if (count == 0) return DMUL_OK;
     // Size classes with too few short jobs to fill the GPU with clusters: where the plain form
     // measured the four-step pipeline faster for a lone product of that length, those jobs run as
     // four-step groups (a lone short job waits on one cluster's three SMs otherwise).
@@ -767,13 +827,20 @@ int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count,
         b->graphs.clear();
         if (b->done_recorded && cudaEventSynchronize(b->done) != cudaSuccess) return DMUL_ERR_CUDA;
         if (b->djobs) dev_free(c, b->djobs, b->jobs_cap * sizeof(JobDev));
+        if (b->dstat) dev_free(c, b->dstat, b->jobs_cap * sizeof(uint32_t));
         if (b->hjobs) cudaFreeHost(b->hjobs);
+        if (b->hstat) cudaFreeHost(b->hstat);
         b->djobs = nullptr;
+        b->dstat = nullptr;
         b->hjobs = nullptr;
+        b->hstat = nullptr;
         b->jobs_cap = 0;
         rc = dev_alloc(c, (void **)&b->djobs, count * sizeof(JobDev));
         if (rc) return rc;
+        rc = dev_alloc(c, (void **)&b->dstat, count * sizeof(uint32_t));
+        if (rc) return rc;
         if (cudaMallocHost(&b->hjobs, count * sizeof(JobDev)) != cudaSuccess) return DMUL_ERR_NOMEM;
+        if (cudaMallocHost(&b->hstat, count * sizeof(uint32_t)) != cudaSuccess) return DMUL_ERR_NOMEM;
         b->jobs_cap = count;
     }
     // the previous batch on this state may still read its descriptors (hjobs) and arena
@@ -791,6 +858,7 @@ int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count,
         d.ny = j.ny;
         d.L = j.nx + j.ny;
         d.square = it.square ? 1u : 0u;
+        d.stat = b->dstat + i;
         if (!it.small) {
             d.X = (uint32_t *)(b->arena + offX[i]);
             d.Y = it.square ? nullptr : (uint32_t *)(b->arena + offY[i]);
@@ -849,6 +917,9 @@ int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count,
         }
         sl.nplans = ns.size();
     }
+    b->order.resize(count);
+    for (size_t i = 0; i < count; ++i) b->order[i] = items[i].idx;
+    b->launched = count;
     if (!use_graph) {
         // plain launches on one stream (the serving loop's slots: shapes vary, slots overlap)
         rc = upload_and_launch(c, b, groups, sl, s, count, ctl_off, ctl_bytes, status, false);

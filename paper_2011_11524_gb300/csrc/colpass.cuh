@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(512) k_col_fwd_ct_b(const PlanDev pd, const Jo
     const uint32_t tile = blockIdx.x / kPrimes;
     uint32_t *dst = (second ? J.Y : J.X) + (uint64_t)pi * pd.N;
     DMUL_PRIME_SWITCH(pi, (col_fwd_ct_body<PI, N1>(pd, sm, second ? J.y : J.x, second ? J.ny : J.nx, dst,
-                                                   tile, status)));
+                                                   tile, job_status(J, status))));
 }
 
 // cluster of three CTAs (rank = prime) per 32-column tile, then the CRT epilogue
@@ -582,7 +582,8 @@ __global__ void __launch_bounds__(256, 3) k_col_fwd_h_b(const PlanDev pd, const 
     if (second && J.square) return;
     const int pi = blockIdx.x % kPrimes;
     col_fwd_h_run<N1>(pd, sm, second ? J.y : J.x, second ? J.ny : J.nx,
-                      (second ? J.Y : J.X) + (uint64_t)pi * pd.N, (blockIdx.x / kPrimes) * 16, pi, status);
+                      (second ? J.Y : J.X) + (uint64_t)pi * pd.N, (blockIdx.x / kPrimes) * 16, pi,
+                      job_status(J, status));
 }
 
 template <int PI, uint32_t N1>

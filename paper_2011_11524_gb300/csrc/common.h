@@ -63,6 +63,7 @@ struct PlanDev {
     // done; the row pass of a prime starts once fsync[prime] reaches ftarget (a running total).
     uint32_t *fsync;
     uint32_t ftarget;
+    uint32_t spin;                      // bound of the device-side waits (polls); 0: the defaults
     uint64_t offA, offQ, offAi, offQi;  // four-step twiddle tables (uint2 offsets)
     const uint2 *tw[kPrimes];           // per-prime table buffers (device)
 };

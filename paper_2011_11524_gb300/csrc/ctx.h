@@ -59,6 +59,14 @@ struct BatchState {
     SmallPlanDev *dplans = nullptr, *hplans = nullptr;  // plans of the short products (device, pinned)
     uint32_t *dcounter = nullptr;                       // job counter of the persistent launch
     bool done_recorded = false;
+    // per-job status: one device word per descriptor (zeroed with the descriptor upload), copied
+    // to the pinned hstat at the end of the batch; order[i] = the caller's index of descriptor i
+    uint32_t *dstat = nullptr, *hstat = nullptr;
+    std::vector<size_t> order;
+    size_t launched = 0;  // descriptors of the last batch launched on this state
+    // dmul_batch: the caller's job array whose status fields the next flush fills
+    dmul_job *pend_jobs = nullptr;
+    bool pending = false;
     // graph cache keyed by the batch shape
     std::map<std::vector<std::tuple<int, uint64_t, size_t>>, cudaGraphExec_t> graphs;
     };
@@ -88,6 +96,9 @@ struct dmul_ctx {
     // reset) and the host's running total of the columns the plain path has sent through them
     uint32_t *fwd_sync = nullptr;
     uint32_t fwd_cols = 0;
+    // bound of every device-side wait of this context's kernels, in polls (0: the defaults;
+    // DMUL_FLAG_SHORT_WAITS makes it short, so that tests can make a wait run out quickly)
+    uint32_t spin_limit = 0;
     // host-buffer path staging
     uint32_t *hx = nullptr, *hy = nullptr;  // operand staging (pageable operands), h_in_cap words each
     uint32_t *hz = nullptr;                 // digit sums (and, staged, the limbs), h_cap words
@@ -107,6 +118,7 @@ struct dmul_ctx {
     std::vector<dml::StageTimer> timers;
     // batched form
     std::unique_ptr<dml::BatchState> batch;
+    int batch_err = DMUL_OK;  // a batch job's device error found before the next dmul_sync
     // serving (created on the first dmul_submit, under server_mu)
     std::mutex server_mu;
     std::unique_ptr<dml::Server> server;
@@ -147,8 +159,21 @@ void free_batch_state(dmul_ctx *c, BatchState *b);
 // plain form's measured choice, prefer_small_single).  four_ok (null: every job) marks the jobs
 // whose scratch allows that: the serving loop admits a short job's four-step scratch only when the
 // choice was already known at submission.
+//
+// Per job: host_status[i] (every entry written) receives the job's host-side verdict -- DMUL_OK
+// for a job that was launched, else the code that rejected it (bad pointers or sizes, capacity,
+// aliasing, too large); rejected jobs are left out of the launch.  The device-side status of each
+// launched job lands in b->hstat[i] for descriptor i (job b->order[i]) once the stream has
+// passed the batch (b->done).
 int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count, cudaStream_t s,
-                 uint32_t *status, bool use_graph, const uint8_t *four_ok = nullptr);
+                 uint32_t *status, bool use_graph, int *host_status, const uint8_t *four_ok = nullptr);
+// DMUL_OK, DMUL_ERR_TIMEOUT or DMUL_ERR_INVALID for a device status word.
+inline int device_code(uint32_t st) {
+    return !st ? DMUL_OK : ((st & kStatusTimeout) ? DMUL_ERR_TIMEOUT : DMUL_ERR_INVALID);
+}
+// Waits for the last dmul_batch on b, writes each launched job's final status into the caller's
+// array and returns the first device-side error among them (DMUL_OK if none, or nothing pending).
+int flush_batch_status(BatchState *b);
 // Library scratch a job needs on the four-step path: 0 for a short product, unless the measured
 // choice for its length is the four-step pipeline (then *four = true, when four is non-null).
 size_t job_scratch_bytes(const dmul_ctx *c, const dmul_job &j, bool *four = nullptr);

@@ -145,10 +145,10 @@ cudaError_t launch_triples_to_digits(const uint32_t *d, uint64_t L, uint32_t *ou
 template <int NT, int PER, bool OOP>
 __global__ void __launch_bounds__(NT, 1536 / NT) k_carry(const uint32_t *z, uint32_t *zo, const uint2 *__restrict__ spill,
                                               uint64_t L, CarryCtl *ctl, uint64_t *nz, uint32_t *status,
-                                              uint32_t ntiles) {
+                                              uint32_t ntiles, uint32_t spin) {
     pdl_trigger();
     pdl_wait();
-    carry_tile<NT, PER, OOP>(z, zo, spill, L, ctl, nz, status, ntiles);
+    carry_tile<NT, PER, OOP>(z, zo, spill, L, ctl, nz, status, ntiles, spin);
 }
 
 // Long products take 8192-limb tiles (512 threads x 16), so that every tile of a product of a few
@@ -156,19 +156,20 @@ __global__ void __launch_bounds__(NT, 1536 / NT) k_carry(const uint32_t *z, uint
 // (256 x 8) for parallelism.  ctl holds flags for ceil(L / kCarryLimbs) tiles, enough for either;
 // it must be zero when the kernel starts.
 cudaError_t launch_carry(uint32_t *z, const uint2 *spill, uint64_t L, CarryCtl *ctl, uint64_t *nz,
-                         uint32_t *status, cudaStream_t s, uint32_t *zo) {
+                         uint32_t *status, cudaStream_t s, uint32_t *zo, uint32_t spin) {
     constexpr uint64_t kBig = 512 * 16;
+    if (!spin) spin = kSpinLimit;
     const uint32_t *zi = z;
     const bool oop = zo && zo != z;
     if (!zo) zo = z;
     if (L >= 256 * kBig) {
         const uint64_t ntiles = (L + kBig - 1) / kBig;
         return launch_pdl(oop ? k_carry<512, 16, true> : k_carry<512, 16, false>, dim3((unsigned)ntiles),
-                          dim3(512), 0, s, 1, zi, zo, spill, L, ctl, nz, status, (uint32_t)ntiles);
+                          dim3(512), 0, s, 1, zi, zo, spill, L, ctl, nz, status, (uint32_t)ntiles, spin);
     }
     const uint64_t ntiles = (L + kCarryLimbs - 1) / kCarryLimbs;
     return launch_pdl(oop ? k_carry<256, 8, true> : k_carry<256, 8, false>, dim3((unsigned)ntiles), dim3(256), 0,
-                      s, 1, zi, zo, spill, L, ctl, nz, status, (uint32_t)ntiles);
+                      s, 1, zi, zo, spill, L, ctl, nz, status, (uint32_t)ntiles, spin);
 }
 
 // ---------------------------------------------------------------------------------------------

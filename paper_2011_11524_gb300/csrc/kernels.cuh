@@ -84,7 +84,13 @@ struct JobDev {
     uint32_t square, ntiles;
     uint32_t plan;          // index of the job's small plan (persistent small-job launch)
     uint32_t pad;
+    uint32_t *stat;         // the job's own device status word (batched form), or null: the launch's
 };
+
+// The status word a job's device-side errors go to: its own (batched form) or the launch's.
+__host__ __device__ inline uint32_t *job_status(const JobDev &J, uint32_t *launch_status) {
+    return J.stat ? J.stat : launch_status;
+}
 
 // Inverse column pass output modes.
 enum InvMode { kInvDigits = 0, kInvTriples = 1, kInvResidues = 2 };
@@ -159,8 +165,9 @@ cudaError_t launch_triples_to_digits(const uint32_t *d, uint64_t L, uint32_t *ou
 // zo[0..L) (zo == nullptr: in place in z; else a disjoint buffer, device or pinned host memory),
 // *nz (device or pinned host, may be null).  ctl must be zeroed (carry_ctl_bytes(L)) before the
 // launch.
+// spin (0: the default) bounds each device-side wait of the scan, in polls.
 cudaError_t launch_carry(uint32_t *z, const uint2 *spill, uint64_t L, CarryCtl *ctl, uint64_t *nz,
-                         uint32_t *status, cudaStream_t s, uint32_t *zo = nullptr);
+                         uint32_t *status, cudaStream_t s, uint32_t *zo = nullptr, uint32_t spin = 0);
 
 // Six-step pieces (Sec. 7.2, 7.6).
 cudaError_t launch_pack(const uint32_t *x, uint64_t nx, uint64_t N, uint32_t *X, uint32_t *status,

@@ -6,6 +6,7 @@
 // context (dmul_init itself allocates).  For them this entry point runs the same two kernels as
 // dmul_carry (digit sums + chunk spills, then the lookahead carry scan) but takes every byte of
 // scratch from one file-scope __device__ array of fixed size, so it calls no allocation routine.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -32,16 +33,33 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};
+CUcontext g_owner[kMaxDevices] = {};  // the context the cached address belongs to
+CUresult (*g_ctx_current)(CUcontext *) = nullptr;
 
-// Device address of the scratch on the current device, looked up once per device.
+// Device address of the scratch on the current device, looked up once per device and CUDA
+// context (the set-up step: a device reset or a new primary context loads the module again, and
+// the array may move, so the address is looked up again for the new context).
 int scratch_address(unsigned char **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DMUL_ERR_CUDA;
     std::lock_guard<std::mutex> g(g_mu);
-    if (!g_addr[dev]) {
+    if (!g_ctx_current) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return DMUL_ERR_CUDA;
+        g_ctx_current = (CUresult(*)(CUcontext *))fn;
+    }
+    // the runtime makes the device's primary context current (cudaFree(0) creates it if needed)
+    if (cudaFree(nullptr) != cudaSuccess) return DMUL_ERR_CUDA;
+    CUcontext cur = nullptr;
+    if (g_ctx_current(&cur) != CUDA_SUCCESS || !cur) return DMUL_ERR_CUDA;
+    if (!g_addr[dev] || g_owner[dev] != cur) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return DMUL_ERR_CUDA;
         g_addr[dev] = p;
+        g_owner[dev] = cur;
     }
     *out = (unsigned char *)g_addr[dev];
     return DMUL_OK;

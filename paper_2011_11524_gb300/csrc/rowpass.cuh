@@ -264,7 +264,7 @@ __device__ __forceinline__ void row_tma_ct_body(const PlanDev &pd, uint32_t *sm,
             tma_load_1d(dst, X + base + (uint64_t)rn * N, bytes, &bar[b ^ 1u]);
             if (!SQR) tma_load_1d(dst + N, Y + base + (uint64_t)rn * N, bytes, &bar[b ^ 1u]);
         }
-        const int ok = __syncthreads_and(mbar_wait(&bar[b], (it >> 1) & 1u) ? 1 : 0);
+        const int ok = __syncthreads_and(mbar_wait(&bar[b], (it >> 1) & 1u, pd.spin) ? 1 : 0);
         if (!ok) {
             if (threadIdx.x == 0) {
                 atomicOr(status, kStatusTimeout);

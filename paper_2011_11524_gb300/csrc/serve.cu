@@ -33,7 +33,6 @@ Server::Server(dmul_ctx *c) : ctx_(c) {
         if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) init_ok_ = false;
         if (cudaMalloc(&s->status, 64) != cudaSuccess || cudaMemset(s->status, 0, 64) != cudaSuccess)
             init_ok_ = false;
-        if (cudaMallocHost(&s->h_status, 64) != cudaSuccess) init_ok_ = false;
         if (init_batch_state(&s->bs) != DMUL_OK) init_ok_ = false;
         slots_.push_back(std::move(s));
     }
@@ -52,7 +51,6 @@ Server::~Server() {
         if (s->stream) cudaStreamSynchronize(s->stream);
         free_batch_state(ctx_, &s->bs);
         if (s->status) cudaFree(s->status);
-        if (s->h_status) cudaFreeHost(s->h_status);
         if (s->stream) cudaStreamDestroy(s->stream);
     }
     if (pool_) cudaMemPoolDestroy(pool_);
@@ -79,59 +77,77 @@ int Server::submit(const dmul_job &job, uint64_t *ticket) {
     return DMUL_OK;
 }
 
+// A ticket's result is handed out once: the dmul_poll that sees it done, or dmul_wait, releases
+// it, so the table holds only tickets that are queued, running or completed and unclaimed.
 int Server::poll(uint64_t ticket, int *done) {
     std::lock_guard<std::mutex> g(mu_);
     auto it = tickets_.find(ticket);
     if (it == tickets_.end()) return DMUL_ERR_UNKNOWN_TICKET;
-    *done = it->second.done ? 1 : 0;
-    return it->second.done ? it->second.status : DMUL_OK;
+    if (!it->second.done) {
+        *done = 0;
+        return DMUL_OK;
+    }
+    *done = 1;
+    const int rc = it->second.status;
+    tickets_.erase(it);
+    return rc;
 }
 
 int Server::wait(uint64_t ticket) {
     std::unique_lock<std::mutex> g(mu_);
+    if (tickets_.find(ticket) == tickets_.end()) return DMUL_ERR_UNKNOWN_TICKET;
+    // looked up on every wake-up: another thread may release the ticket meanwhile
+    done_cv_.wait(g, [&] {
+        auto it = tickets_.find(ticket);
+        return it == tickets_.end() || it->second.done;
+    });
     auto it = tickets_.find(ticket);
     if (it == tickets_.end()) return DMUL_ERR_UNKNOWN_TICKET;
-    Ticket *tk = &it->second;  // element references survive rehashing; iterators do not
-    done_cv_.wait(g, [&] { return tk->done; });
-    return tk->status;
+    const int rc = it->second.status;
+    tickets_.erase(it);
+    return rc;
 }
 
-// Runs on CUDA's callback thread once the slot's batch and the copy of its status word are done:
-// completes the batch's tickets at once (no CUDA calls are allowed here); the worker recycles the
-// slot afterwards.
+void Server::stats(dmul_serve_info *out) {
+    std::lock_guard<std::mutex> g(mu_);
+    out->queued = queue_.size();
+    out->running = running_;
+    out->held = tickets_.size();
+    out->peak_running = peak_running_;
+    out->admit_budget_bytes = budget_;
+    out->inflight_bytes = inflight_;
+}
+
+// Runs on CUDA's callback thread once the slot's batch, and the copy of its jobs' status words,
+// are done: completes each launched ticket with its own job's status (no CUDA calls are allowed
+// here); the worker recycles the slot afterwards.
 void CUDART_CB Server::on_done(void *p) {
     Slot *s = (Slot *)p;
     Server *self = s->owner;
-    const uint32_t st = *(volatile uint32_t *)s->h_status;
-    const int rc = !st ? DMUL_OK : ((st & kStatusTimeout) ? DMUL_ERR_TIMEOUT : DMUL_ERR_INVALID);
     {
         std::lock_guard<std::mutex> g(self->mu_);
-        for (uint64_t t : s->tickets) {
-            Ticket &tk = self->tickets_[t];
-            tk.status = rc;
-            tk.done = true;
+        const BatchState &b = s->bs;
+        for (size_t i = 0; i < b.launched; ++i) {
+            auto it = self->tickets_.find(s->tickets[b.order[i]]);
+            if (it == self->tickets_.end()) continue;
+            it->second.status = device_code(((volatile uint32_t *)b.hstat)[i]);
+            it->second.done = true;
         }
+        self->running_ -= b.launched;
         s->tickets.clear();
-        s->result = (int)st;
         s->finished = true;
     }
     self->done_cv_.notify_all();
     self->cv_.notify_all();
 }
 
-// A finished slot (its tickets already completed by on_done): clear its device status word if
-// the batch set it (on the slot's stream, ahead of the next batch there) and release its budget.
+// A finished slot (its tickets already completed by on_done): release its budget.
 void Server::retire(Slot &s, std::unique_lock<std::mutex> &g) {
+    (void)g;
     s.busy = false;
     s.finished = false;
     inflight_ -= s.bytes;
     s.bytes = 0;
-    if (s.result) {
-        s.result = 0;
-        g.unlock();
-        cudaMemsetAsync(s.status, 0, 4, s.stream);
-        g.lock();
-    }
 }
 
 // Admit pending requests into a free slot and launch them as one batch.
@@ -149,9 +165,14 @@ bool Server::launch(Slot &s, std::unique_lock<std::mutex> &g) {
         queue_.pop_front();
     }
     if (jobs.empty()) return false;
+    std::vector<int> hs(jobs.size(), DMUL_OK);
+    // on_done may run (and clear s.tickets) before this thread takes the lock again
+    const std::vector<uint64_t> tick = s.tickets;
     s.busy = true;
     s.bytes = bytes;
     inflight_ += bytes;
+    running_ += jobs.size();
+    peak_running_ = std::max(peak_running_, running_);
     g.unlock();
     int rc = DMUL_OK;
     void *arena = nullptr;
@@ -162,26 +183,37 @@ bool Server::launch(Slot &s, std::unique_lock<std::mutex> &g) {
         // the scratch of this batch is the pool allocation; the state never reallocates it
         s.bs.arena = (uint8_t *)arena;
         s.bs.arena_cap = bytes;
-        rc = run_batch_on(ctx_, &s.bs, jobs.data(), jobs.size(), s.stream, s.status, false, four.data());
+        rc = run_batch_on(ctx_, &s.bs, jobs.data(), jobs.size(), s.stream, s.status, false, hs.data(), four.data());
         s.bs.arena = nullptr;
         s.bs.arena_cap = 0;
     }
     if (arena) cudaFreeAsync(arena, s.stream);
-    if (rc == DMUL_OK &&
-        (cudaMemcpyAsync(s.h_status, s.status, 4, cudaMemcpyDeviceToHost, s.stream) != cudaSuccess ||
-         cudaLaunchHostFunc(s.stream, on_done, &s) != cudaSuccess))
-        rc = DMUL_ERR_CUDA;
+    if (rc == DMUL_OK && cudaLaunchHostFunc(s.stream, on_done, &s) != cudaSuccess) rc = DMUL_ERR_CUDA;
     g.lock();
     if (rc != DMUL_OK) {
-        for (uint64_t t : s.tickets) {
+        // nothing of this batch will complete on the stream (no callback was enqueued)
+        for (uint64_t t : tick) {
             tickets_[t].status = rc;
             tickets_[t].done = true;
         }
+        running_ -= tick.size();
         s.tickets.clear();
         s.busy = false;
         inflight_ -= s.bytes;
         s.bytes = 0;
         done_cv_.notify_all();
+    } else {
+        // requests the host checks rejected were left out of the launch: they complete now, with
+        // their own code; the launched ones complete in on_done
+        bool any = false;
+        for (size_t k = 0; k < hs.size(); ++k)
+            if (hs[k]) {
+                tickets_[tick[k]].status = hs[k];
+                tickets_[tick[k]].done = true;
+                --running_;
+                any = true;
+            }
+        if (any) done_cv_.notify_all();
     }
     return true;
 }

@@ -20,7 +20,7 @@ namespace dml {
 int ctx_enqueue_mul(dmul_ctx *c, const dmul_job &j, cudaStream_t s);
 
 // dmul_batch implementation (batch.cu).
-int run_batch(dmul_ctx *c, const dmul_job *jobs, size_t count, cudaStream_t s);
+int run_batch(dmul_ctx *c, dmul_job *jobs, size_t count, cudaStream_t s);
 
 // The serving loop behind dmul_submit / dmul_poll / dmul_wait (serve.cu).
 //
@@ -38,6 +38,7 @@ class Server {
     int submit(const dmul_job &job, uint64_t *ticket);
     int poll(uint64_t ticket, int *done);
     int wait(uint64_t ticket);
+    void stats(dmul_serve_info *out);
 
     static constexpr int kSlots = 4;
     static constexpr size_t kMaxBatch = 1024;
@@ -54,10 +55,9 @@ class Server {
         Server *owner = nullptr;
         BatchState bs;
         cudaStream_t stream = nullptr;
-        uint32_t *status = nullptr;  // device status word of this slot's batches
-        uint32_t *h_status = nullptr;  // pinned copy, written on the stream before the callback
-        int result = 0;               // the finished batch's status (set by the callback)
-        std::vector<uint64_t> tickets;
+        uint32_t *status = nullptr;  // launch status word of this slot's batches (every job also
+                                     // has its own, in the batch state: bs.hstat / bs.order)
+        std::vector<uint64_t> tickets;  // the batch's requests, in the order they were passed
         size_t bytes = 0;
         void *arena = nullptr;
         bool busy = false;
@@ -72,8 +72,10 @@ class Server {
     std::mutex mu_;
     std::condition_variable cv_, done_cv_;
     std::deque<uint64_t> queue_;
-    std::unordered_map<uint64_t, Ticket> tickets_;
+    std::unordered_map<uint64_t, Ticket> tickets_;  // issued and not yet released
     uint64_t next_ = 1;
+    uint64_t running_ = 0;  // requests in launched batches
+    uint64_t peak_running_ = 0;
     bool stop_ = false;
     bool init_ok_ = false;
     bool mem_blocked_ = false;  // the head request waits for in-flight scratch to be released

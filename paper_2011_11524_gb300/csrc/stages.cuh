@@ -82,8 +82,9 @@ __device__ __forceinline__ void row_wait_prime(const PlanDev &pd, uint32_t pi, u
     }
     if (threadIdx.x == 0) {
         uint32_t spins = 0;
+        const uint32_t limit = pd.spin ? pd.spin : (1u << 24);
         while ((int32_t)(fwd_sync_ld(pd.fsync + pi) - pd.ftarget) < 0) {
-            if (++spins > (1u << 24)) {
+            if (++spins > limit) {
                 if (status) atomicOr(status, kStatusTimeout);
                 break;
             }
@@ -547,8 +548,9 @@ __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 // Bounded wait for the mbarrier phase with the given parity; false when the bound runs out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    for (uint32_t i = 0; i < (1u << 20); ++i) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = 0) {
+    if (!limit) limit = 1u << 20;
+    for (uint32_t i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -599,7 +601,7 @@ __device__ __forceinline__ void row_mul_tma_body(const PlanDev &pd, uint32_t *sm
             if (!SQR) tma_load_1d(dst + n, Y + base + (uint64_t)rn * n, bytes, &bar[b ^ 1u]);
         }
         // every thread polls; the outcome is agreed on so that the CTA leaves (or not) as a whole
-        const int ok = __syncthreads_and(mbar_wait(&bar[b], (it >> 1) & 1u) ? 1 : 0);
+        const int ok = __syncthreads_and(mbar_wait(&bar[b], (it >> 1) & 1u, pd.spin) ? 1 : 0);
         if (!ok) {
             if (threadIdx.x == 0) {
                 atomicOr(status, kStatusTimeout);
@@ -860,10 +862,13 @@ __device__ __forceinline__ void col_inv_crt(const PlanDev &pd, const uint32_t *_
 // The digit sums are read from z and the limbs written to zo: the same buffer, or (OOP, the
 // host-buffer entry point) pinned host memory, so that the limbs cross the host link as the tiles
 // finish instead of in a copy after the kernel.
+//
+// spin_limit bounds every wait of the tile (polls of a predecessor's flag, of the done count); an
+// expired wait sets kStatusTimeout and the tile goes on with carry 0, so the kernel always ends.
 template <int NT, int PER, bool OOP = false>
 __device__ __forceinline__ void carry_tile(const uint32_t *z, uint32_t *zo, const uint2 *__restrict__ spill,
                                            uint64_t L, CarryCtl *ctl, uint64_t *nz,
-                                           uint32_t *status, uint32_t ntiles) {
+                                           uint32_t *status, uint32_t ntiles, uint32_t spin_limit = kSpinLimit) {
     // every 32-limb chunk start (where a spill lands) is the first limb of some thread
     static_assert(NT % 32 == 0 && NT <= 1024 && PER % 4 == 0 && 32 % PER == 0, "tile shape");
     constexpr int NW = NT / 32;
@@ -873,6 +878,7 @@ __device__ __forceinline__ void carry_tile(const uint32_t *z, uint32_t *zo, cons
     if (tid == 0) s_tile = atomicAdd(&ctl->ticket, 1u);
     __syncthreads();
     const uint32_t tile = s_tile;
+    if (tile >= ntiles) return;  // more CTAs than tiles (a ticket that did not start at 0)
     const uint64_t base = (uint64_t)tile * (NT * PER) + (uint64_t)tid * PER;
     const bool vec = ((((uintptr_t)z) & 15) == 0) && (base + PER <= L);
     uint32_t v[PER];
@@ -966,7 +972,7 @@ __device__ __forceinline__ void carry_tile(const uint32_t *z, uint32_t *zo, cons
                     first = incl ? __ffs(incl) - 1 : 32;
                     const unsigned need = first == 32 ? 0xffffffffu : (2u << first) - 1u;  // lanes 0..first
                     if ((ready & need) == need) break;
-                    if (spins >= kSpinLimit) { late = true; break; }
+                    if (spins >= spin_limit) { late = true; break; }
                 }
                 if (late) {
                     if (lane == 0) atomicOr(status, kStatusTimeout);
@@ -1076,7 +1082,7 @@ __device__ __forceinline__ void carry_tile(const uint32_t *z, uint32_t *zo, cons
         if (tid == 0) {
             uint32_t spins = 0;
             while (ld_acquire_u32(&ctl->done) != ntiles - 1) {
-                if (++spins > kSpinLimit) { atomicOr(status, kStatusTimeout); break; }
+                if (++spins > spin_limit) { atomicOr(status, kStatusTimeout); break; }
             }
         }
         __syncthreads();

@@ -23,6 +23,7 @@ DMUL_ERR_TIMEOUT = 4
 DMUL_ERR_CUDA = 5
 DMUL_ERR_CAPACITY = 6
 DMUL_ERR_UNKNOWN_TICKET = 7
+DMUL_PENDING = -1
 
 DMUL_FLAG_SIXSTEP = 1
 DMUL_FLAG_STAGE_TIMING = 2
@@ -34,6 +35,8 @@ DMUL_FLAG_HOST_STAGED_IN = 64
 DMUL_FLAG_HOST_STAGED_OUT = 128
 DMUL_FLAG_HOST_DIRECT_IN = 256
 DMUL_FLAG_NO_RADIX5 = 512
+DMUL_FLAG_SHORT_WAITS = 1024
+DMUL_FLAG_TEST_STALL_CARRY = 2048
 DMUL_HOST_IN_PLACE_LIMBS = 524288
 
 # every symbol include/dmul.h declares
@@ -42,7 +45,7 @@ EXPORTS = [
     "dmul_mul_host", "dmul_batch", "dmul_submit", "dmul_poll", "dmul_wait", "dmul_conv_residues",
     "dmul_conv_coeffs", "dmul_carry", "dmul_transpose", "dmul_get_plan", "dmul_primes",
     "dmul_lambda", "dmul_max_min_limbs", "dmul_stage_times", "dmul_stage_timing", "dmul_probe_imad",
-    "dmul_carry_noalloc", "dmul_host_direct",
+    "dmul_carry_noalloc", "dmul_host_direct", "dmul_serve_stats",
 ]
 
 
@@ -60,7 +63,13 @@ class dmul_config(ctypes.Structure):
 class dmul_job(ctypes.Structure):
     _fields_ = [("x", ctypes.c_void_p), ("nx", ctypes.c_uint64), ("y", ctypes.c_void_p),
                 ("ny", ctypes.c_uint64), ("z", ctypes.c_void_p), ("z_cap", ctypes.c_uint64),
-                ("nz", ctypes.c_void_p)]
+                ("nz", ctypes.c_void_p), ("status", ctypes.c_int)]
+
+
+class dmul_serve_info(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_uint64), ("running", ctypes.c_uint64), ("held", ctypes.c_uint64),
+                ("peak_running", ctypes.c_uint64), ("admit_budget_bytes", ctypes.c_uint64),
+                ("inflight_bytes", ctypes.c_uint64)]
 
 
 class dmul_plan_info(ctypes.Structure):
@@ -97,6 +106,7 @@ def load() -> ctypes.CDLL:
         "dmul_submit": ([vp, ctypes.POINTER(dmul_job), ctypes.POINTER(u64)], i32),
         "dmul_poll": ([vp, u64, ctypes.POINTER(i32)], i32),
         "dmul_wait": ([vp, u64], i32),
+        "dmul_serve_stats": ([vp, ctypes.POINTER(dmul_serve_info)], i32),
         "dmul_conv_residues": ([vp, vp, sz, vp, sz, vp, vp], i32),
         "dmul_conv_coeffs": ([vp, vp, sz, vp, sz, vp, vp], i32),
         "dmul_carry": ([vp, vp, sz, vp, sz, vp, vp], i32),
@@ -196,8 +206,13 @@ def make_jobs(jobs) -> ctypes.Array:
     jobs = list(jobs)
     arr = (dmul_job * max(1, len(jobs)))()
     for i, (x, nx, y, ny, z, zc, nz) in enumerate(jobs):
-        arr[i] = dmul_job(_ptr(x), nx, _ptr(y), ny, _ptr(z), zc, _ptr(nz))
+        arr[i] = dmul_job(_ptr(x), nx, _ptr(y), ny, _ptr(z), zc, _ptr(nz), DMUL_PENDING)
     return arr
+
+
+def job_statuses(jobs_array, count) -> list[int]:
+    """The status field of the first `count` descriptors (filled by dmul_batch / dmul_sync)."""
+    return [int(jobs_array[i].status) for i in range(count)]
 
 
 def dmul_batch(ctx, jobs_array, count, stream=None) -> int:
@@ -218,6 +233,15 @@ def dmul_poll(ctx, ticket) -> tuple[int, bool]:
 
 def dmul_wait(ctx, ticket) -> int:
     return load().dmul_wait(ctx, ticket)
+
+
+def dmul_serve_stats(ctx) -> dict:
+    """The serving loop's counters as a dict (raises on error)."""
+    info = dmul_serve_info()
+    rc = load().dmul_serve_stats(ctx, ctypes.byref(info))
+    if rc:
+        raise DmulError(rc, "dmul_serve_stats")
+    return {k: int(getattr(info, k)) for k, _ in dmul_serve_info._fields_}
 
 
 def dmul_conv_residues(ctx, x, nx, y, ny, r, stream=None) -> int:

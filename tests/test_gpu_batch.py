@@ -92,12 +92,90 @@ def test_batch_same_as_alone(d, ctx):
         assert torch.equal(alone, z) and nza == int(nz.item())
 
 
-def test_batch_rejects_bad_job(d, ctx):
+def test_batch_rejects_bad_job_alone(d, ctx):
+    """A job the host checks reject gets its own code at once and is not run; the others run."""
     jobs = wl.c4_jobs(3, 2.0, 3.0, 0.0, seed=41)
     dev = _prep(d, jobs)
     tx, nx, ty, ny, z, L, nz = dev[1]
     dev[1] = (tx, nx, ty, ny, z, L - 1, nz)  # capacity too small
-    assert d.dmul_batch(ctx.handle, d.make_jobs(dev), len(dev)) == d.DMUL_ERR_CAPACITY
+    arr = d.make_jobs(dev)
+    assert d.dmul_batch(ctx.handle, arr, len(dev)) == d.DMUL_OK
+    st = d.job_statuses(arr, 3)
+    assert st == [d.DMUL_PENDING, d.DMUL_ERR_CAPACITY, d.DMUL_PENDING]
+    assert d.dmul_sync(ctx.handle) == d.DMUL_OK
+    assert d.job_statuses(arr, 3) == [d.DMUL_OK, d.DMUL_ERR_CAPACITY, d.DMUL_OK]
+    assert torch.all(dev[1][4] == -1)  # never written
+    _check(d, [jobs[0], jobs[2]], [dev[0], dev[2]])
+
+
+def _with_bad_limb(jobs, where, rng):
+    """A copy of jobs[where] whose x has one limb equal to 10^9 (an invalid base-10^9 limb)."""
+    j = jobs[where]
+    x = j.x.copy()
+    x[int(rng.integers(0, len(x)))] = 10**9
+    return wl.Job(x, x if j.square else j.y, j.square)
+
+
+@pytest.mark.parametrize("bad_kind", ["short", "four_step"])
+def test_batch_bad_limb_fails_only_its_job(d, ctx, bad_kind):
+    """50 valid jobs and one with a limb = 10^9 in one dmul_batch: only that job reports
+    DMUL_ERR_INVALID; the 50 match the oracle and their products computed alone."""
+    rng = np.random.Generator(np.random.PCG64(42))
+    jobs = wl.c4_jobs(50, 2.0, 5.0, 0.2, seed=43)
+    lo, hi = (2.0, 3.0) if bad_kind == "short" else (5.2, 5.4)
+    extra = wl.c4_jobs(1, lo, hi, 0.0, seed=44)
+    bad = _with_bad_limb(extra, 0, rng)
+    where = 17
+    jobs = jobs[:where] + [bad] + jobs[where:]
+    dev = _prep(d, jobs)
+    arr = d.make_jobs(dev)
+    assert d.dmul_batch(ctx.handle, arr, len(dev)) == d.DMUL_OK
+    assert d.dmul_sync(ctx.handle) == d.DMUL_ERR_INVALID
+    st = d.job_statuses(arr, len(dev))
+    assert st[where] == d.DMUL_ERR_INVALID
+    assert all(v == d.DMUL_OK for i, v in enumerate(st) if i != where)
+    good = [i for i in range(len(jobs)) if i != where]
+    _check(d, [jobs[i] for i in good], [dev[i] for i in good])
+    for i in good:
+        tx, nx, ty, ny, z, L, nz = dev[i]
+        alone, nza = ctx.mul(tx, ty)
+        assert torch.equal(alone, z) and nza == int(nz.item())
+    # the next sync is clean again
+    assert d.dmul_sync(ctx.handle) == d.DMUL_OK
+
+
+def test_served_bad_request_fails_only_itself(d):
+    """50 valid requests and one with a limb = 10^9, submitted together into the serving loop: each
+    ticket returns its own status, the 50 equal their alone-results and the oracle, and once every
+    ticket has been waited for the server holds none of them."""
+    rng = np.random.Generator(np.random.PCG64(45))
+    jobs = wl.c4_jobs(50, 2.0, 5.5, 0.3, seed=46)
+    where = 31
+    jobs = jobs[:where] + [_with_bad_limb(jobs, where, rng)] + jobs[where:]
+    with d.Context(0) as srv:
+        dev = _prep(d, jobs)
+        arr = d.make_jobs(dev)
+        tickets = []
+        for i in range(len(jobs)):
+            rc, t = d.dmul_submit(srv.handle, arr[i])
+            assert rc == 0
+            tickets.append(t)
+        rcs = [d.dmul_wait(srv.handle, t) for t in tickets]
+        assert rcs[where] == d.DMUL_ERR_INVALID
+        assert all(rc == d.DMUL_OK for i, rc in enumerate(rcs) if i != where)
+        good = [i for i in range(len(jobs)) if i != where]
+        _check(d, [jobs[i] for i in good], [dev[i] for i in good])
+        with d.Context(0) as alone:
+            for i in good:
+                tx, nx, ty, ny, z, L, nz = dev[i]
+                za, nza = alone.mul(tx, ty)
+                assert torch.equal(za, z) and nza == int(nz.item())
+        # every ticket was released by its wait: the table is empty and the tickets are gone
+        st = d.dmul_serve_stats(srv.handle)
+        assert (st["queued"], st["running"], st["held"]) == (0, 0, 0)
+        for t in tickets:
+            assert d.dmul_poll(srv.handle, t)[0] == d.DMUL_ERR_UNKNOWN_TICKET
+            assert d.dmul_wait(srv.handle, t) == d.DMUL_ERR_UNKNOWN_TICKET
 
 
 def test_served_mix_same_as_alone(d):
@@ -120,10 +198,21 @@ def test_served_mix_same_as_alone(d):
             t.start()
         for t in th:
             t.join()
-        for t in tickets:
+        # half the tickets collected by polling, half by waiting; each result is handed out once
+        pending = list(tickets[::2])
+        while pending:
+            still = []
+            for t in pending:
+                rc, done = d.dmul_poll(srv.handle, t)
+                assert rc == 0
+                if not done:
+                    still.append(t)
+            pending = still
+        for t in tickets[1::2]:
             assert d.dmul_wait(srv.handle, t) == 0
-            rc, done = d.dmul_poll(srv.handle, t)
-            assert rc == 0 and done
+        for t in tickets:
+            assert d.dmul_poll(srv.handle, t)[0] == d.DMUL_ERR_UNKNOWN_TICKET
+        assert d.dmul_serve_stats(srv.handle)["held"] == 0
         _check(d, jobs, dev)
         with d.Context(0) as alone:
             for j, (tx, nx, ty, ny, z, L, nz) in zip(jobs, dev):

@@ -1,15 +1,19 @@
-"""dmul_carry_noalloc against dmul_carry.
+"""dmul_carry_noalloc against dmul_carry and the oracle.
 
 dmul_carry_noalloc is the carry stage for callers that cannot allocate device memory (their GPU
 memory belongs to another allocator, or cudaMalloc's device-wide synchronization is not allowed on
 their path, or they cannot create a context).  It must give exactly the limbs and length that
-dmul_carry gives, call after call, although every call reuses the same static scratch array.
+dmul_carry gives, and that the oracle's carry recurrence gives, call after call, although every
+call reuses the same static scratch array -- including at the largest size that array holds,
+where the carry runs on its 8192-limb tiles.
 
 This file is collected last so that a run stopping at the first failure has run everything else;
 it also passes on its own in a fresh process.
 """
 import numpy as np
 import pytest
+
+import oracle
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -57,16 +61,44 @@ def _with_noalloc(d, tri, L):
     return d.to_host(z), int(nz.item())
 
 
-def test_noalloc_matches_dmul_carry_twice(d):
+def _with_oracle(tri, L):
+    """The carry recurrence of the oracle on the same sum: sum_k (d0_k + d1_k B + d2_k B^2) B^k
+    regrouped by power of B (c'_k = d0_k + d1_(k-1) + d2_(k-2) < 3 10^9), two extra positions for
+    the terms past L, which must carry nothing."""
+    t = tri.astype(np.uint64)
+    c = np.zeros(L + 2, dtype=np.uint64)
+    c[:L] += t[:, 0]
+    c[1:L + 1] += t[:, 1]
+    c[2:L + 2] += t[:, 2]
+    words = np.zeros((L + 2, 2), dtype=np.uint64)
+    words[:, 0] = c
+    z, top = oracle.carry(words)
+    assert top == 0 and z[L] == 0 and z[L + 1] == 0
+    return z[:L], len(oracle.normalize(z[:L]))
+
+
+@pytest.mark.parametrize("cases", [((70001, "random"), (4099, "ripple")),
+                                   (((1 << 22) - 5, "random"), (1 << 22, "ripple"))],
+                         ids=["short", "max_size"])
+def test_noalloc_matches_dmul_carry_and_oracle_twice(d, cases):
+    """Two calls in a row on the shared static scratch (the second overwrites the first's), each
+    equal to dmul_carry and to the oracle, limbs and normalized length.  The max_size case runs at
+    L = 2^22 - 5 and at the array's limit L = 2^22 (8192-limb tiles), the second with a carry
+    that ripples from position 1 through every tile to the top limb."""
+    assert d.DMUL_NOALLOC_MAX_LIMBS == 1 << 22
     rng = np.random.Generator(np.random.PCG64(2024))
     with d.Context(0) as ctx:
-        # two calls in a row on the shared static scratch (the second overwrites the first's)
-        for L, kind in ((70001, "random"), (4099, "ripple")):
+        for L, kind in cases:
             tri = _triples(rng, L, kind)
             ref_z, ref_nz = _with_existing(d, ctx, tri, L)
+            or_z, or_nz = _with_oracle(tri, L)
             got_z, got_nz = _with_noalloc(d, tri, L)
+            assert np.array_equal(got_z, or_z)
+            assert got_nz == or_nz
             assert np.array_equal(got_z, ref_z)
             assert got_nz == ref_nz
+            if kind == "ripple":
+                assert got_z[L - 1] == 1 and np.all(got_z[1:L - 1] == 0)
 
 
 def test_noalloc_limits_and_errors(d):

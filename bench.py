@@ -64,6 +64,15 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_samples(self, n: int, timeout: float = 2.0) -> None:
+        """Block until at least n samples have arrived (or timeout), so that a short timed region
+        is bracketed by a sample just before it and one just after it."""
+        if self.proc is None:
+            return
+        t_end = time.perf_counter() + timeout
+        while len(self.lines) < n and time.perf_counter() < t_end:
+            time.sleep(0.005)
+
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -151,6 +160,44 @@ def work_model(info, nx: int, ny: int, square: bool) -> dict:
     return k
 
 
+def _butterfly_mults(n: int) -> float:
+    """Modular products of the butterflies of one length-n transform in the survey's count:
+    (n/2) log2 n for n = 2^a; a radix-3 first pass (n = 3 2^a) adds 2n, a radix-5 one 1.2 n."""
+    odd = 1
+    while n % 2 == 0 and n > 1:
+        n //= 2
+        odd *= 2
+    a, m = odd.bit_length() - 1, n * odd
+    extra = {1: 0.0, 3: 2.0, 5: 1.2}[n]
+    return m / 2 * a + extra * m
+
+
+def survey_model(info, nx: int, ny: int, square: bool) -> dict:
+    """Algorithmic work per kernel launch by the hot-path scope table's count: modular products of
+    the transforms ((n/2) log2 n butterflies per length-n transform, N four-step twiddles per
+    column pass), N pointwise Montgomery products, and the CRT's three products per coefficient;
+    a Shoup product counts 3 IMAD, a Montgomery product 4.  Bytes: each pass's residues once in
+    and once out, limbs once (the two-pass HBM model)."""
+    N, N1, N2 = int(info.N), int(info.N1), int(info.N2)
+    L = nx + ny
+    ops = 1 if square else 2
+    l = 3
+    col = N2 * _butterfly_mults(N1) + N
+    k = {
+        "col_fwd": {"modmuls": l * ops * col, "imad": 3 * l * ops * col,
+                    "bytes": 4 * (nx + (0 if square else ny)) + 4 * l * N * ops},
+        "row_mul": {"modmuls": l * ((ops + 1) * N1 * _butterfly_mults(N2) + N),
+                    "imad": 3 * l * (ops + 1) * N1 * _butterfly_mults(N2) + 4 * l * N,
+                    "bytes": 4 * l * N * (ops + 1)},
+        "col_inv_crt": {"modmuls": l * col + l * L, "imad": 3 * l * col + 3 * l * L,
+                        "bytes": 4 * l * N + 4 * L + 8 * (L // 32)},
+        "carry_scan": {"modmuls": 0, "imad": 0.0, "bytes": 8 * L + 8 * (L // 32)},
+    }
+    k["total"] = {"modmuls": sum(v["modmuls"] for v in k.values()), "imad": sum(v["imad"] for v in k.values()),
+                  "bytes": (6 if not square else 4) * l * 4 * N + (8 * L if not square else 4 * nx + 4 * L)}
+    return k
+
+
 # ----------------------------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------------------------
@@ -207,6 +254,7 @@ def run_ours(args, rank, world, local):
             torch.distributed.barrier()
         clocks = ClockSampler(local)
         clocks.start()
+        clocks.wait_samples(1)  # sampling runs before the first timed step ...
         torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
@@ -219,7 +267,9 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         ms = [a.elapsed_time(b) for a, b in evs]
+        clocks.wait_samples(len(clocks.lines) + 1)  # ... and one more lands after the last
         clk = clocks.stop()
+        clk["window"] = "every 50 ms sample from the last one before the timed region to the first after it"
     rc = d.dmul_sync(ctx.handle, sptr)
     if rc:
         raise d.DmulError(rc, "timed region")
@@ -279,9 +329,10 @@ def run_ours(args, rank, world, local):
                                  else "copied (cudaMemcpyAsync)"},
                    "staged_copies_ms_per_step": staged_s * 1e3}
 
-    # ---- roofline of the dominant kernel ----
+    # ---- roofline of the dominant kernel and of the whole product ----
     info = d.dmul_get_plan(ctx.handle, L)
     model = work_model(info, nx, ny, False)
+    smodel = survey_model(info, nx, ny, False)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -290,21 +341,44 @@ def run_ours(args, rank, world, local):
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    imad_peak_t = n_sm * 64 * sm_max * 1e6 / 1e12  # T IMAD/s at the maximum SM clock
+    imad_derived_t = n_sm * 64 * sm_max * 1e6 / 1e12  # T IMAD/s at the maximum SM clock
+    # the integer-pipe peak, measured: independent IMAD chains on every SM (dmul_probe_imad), with
+    # the SM clock sampled while the probe runs
+    probe_clk = ClockSampler(local)
+    probe_clk.start()
+    probes = []
+    t_end = time.perf_counter() + 0.6
+    while time.perf_counter() < t_end:
+        probes.append(ctx.probe_imad())
+    pclk = probe_clk.stop()
+    imad_peak_t = max(probes) / 1e12
     dom = max((k for k in stages if k in model), key=lambda k: stages[k][0])
     dms = stages[dom][0] / max(1, stages[dom][1])
-    imad_t = model[dom]["imad"] / (dms * 1e-3) / 1e12
-    gbs = model[dom]["bytes"] / (dms * 1e-3) / 1e9
-    if imad_t / imad_peak_t >= gbs / hbm_peak:
-        roof = {"bound": "alu", "achieved": round(imad_t, 3), "peak": round(imad_peak_t, 3),
-                "unit": "TIMAD/s", "frac": round(imad_t / imad_peak_t, 4), "traffic": None,
-                "kernel": dom, "peak_source": f"{n_sm} SMs x 64 IMAD/clk x {sm_max:.0f} MHz (derived)",
-                "hbm_gbs": round(gbs, 1), "hbm_frac_of_measured": round(gbs / hbm_peak, 4)}
-    else:
-        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(gbs / hbm_peak, 4), "traffic": None, "kernel": dom,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                "imad_tps": round(imad_t, 3), "imad_frac": round(imad_t / imad_peak_t, 4)}
+    imad_t = smodel[dom]["imad"] / (dms * 1e-3) / 1e12
+    imad_r16_t = model[dom]["imad"] / (dms * 1e-3) / 1e12
+    gbs = smodel[dom]["bytes"] / (dms * 1e-3) / 1e9
+    t_int_us = smodel["total"]["imad"] / (imad_peak_t * 1e12) * 1e6
+    t_hbm_us = smodel["total"]["bytes"] / (hbm_peak * 1e9) * 1e6
+    roof = {"bound": "alu", "achieved": round(imad_t, 3), "peak": round(imad_peak_t, 3),
+            "unit": "TIMAD/s", "frac": round(imad_t / imad_peak_t, 4), "traffic": None, "kernel": dom,
+            "peak_source": "measured (dmul_probe_imad): independent 32-bit IMAD chains on every SM, "
+                           f"best of {len(probes)}, SM clock median {pclk.get('sm_mhz')} MHz during the probe",
+            "count_model": "SURVEY 8(d): butterfly modmuls (n/2) log2 n per length-n transform + N "
+                           "twiddles (four-step) + N pointwise + 3 L CRT; Shoup = 3 IMAD, Montgomery = 4",
+            "frac_per_survey_model": round(imad_t / imad_peak_t, 4),
+            "kernel_imad_per_launch": smodel[dom]["imad"],
+            "kernel_ms": round(dms, 5),
+            "frac_radix16_count": round(imad_r16_t / imad_peak_t, 4),
+            "radix16_count_imad_per_launch": model[dom]["imad"],
+            "peak_derived": round(imad_derived_t, 3),
+            "peak_derived_source": f"{n_sm} SMs x 64 IMAD/clk x {sm_max:.0f} MHz",
+            "frac_of_derived": round(imad_t / imad_derived_t, 4),
+            "hbm_gbs": round(gbs, 1), "hbm_frac_of_measured": round(gbs / hbm_peak, 4),
+            "whole_product": {"imad": smodel["total"]["imad"], "bytes": smodel["total"]["bytes"],
+                              "T_int_us": round(t_int_us, 2), "T_hbm_us": round(t_hbm_us, 2),
+                              "bound": "alu" if t_int_us >= t_hbm_us else "hbm",
+                              "ms_per_step": ms_per_step},
+            "whole_product_frac": round(max(t_int_us, t_hbm_us) * 1e-3 / ms_per_step, 4)}
     roof["traffic"] = NCU_TRAFFIC.get((dom, int(info.N), int(info.N1), int(info.N2), int(info.col_half)))
     launches = sum(v[1] for v in stages.values()) // max(1, stage_steps)
 
@@ -329,8 +403,8 @@ def run_ours(args, rank, world, local):
     }
     if rank == 0 and not args.no_forms:
         out["other_configs"] = run_other_configs(d, torch, dev, flush, stream)
-        out["batched"] = run_batched(d, torch, dev)
-        out["served"] = run_served(d, torch, dev)
+        out["batched"] = run_batched(d, torch, dev, check=not args.no_cpu_baseline)
+        out["served"] = run_served(d, torch, dev, check=not args.no_cpu_baseline)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(x_np, y_np, d.to_host(z), budget_s=args.cpu_seconds,
                                            digits=digits)
@@ -420,10 +494,53 @@ def run_other_configs(d, torch, dev, flush, stream) -> dict:
     return out
 
 
-def run_batched(d, torch, dev, reps=3, count=4096):
+def _fp_moduli(count=4):
+    """The first `count` primes of the seeded stream of 61-bit candidates (the fingerprint moduli
+    of the tests)."""
+    import oracle
+    from paper_2011_11524_gb300 import workloads as wl
+    out = []
+    for q in wl.fingerprint_candidates():
+        if oracle.is_prime_mr(q):
+            out.append(q)
+            if len(out) == count:
+                return out
+
+
+def check_products(d, xs, ys, zs, nzs, full_sample=8, seed=0):
+    """Oracle check of a list of GPU products (host arrays): x*y = z (mod q) for four seeded 61-bit
+    primes q on every product (fingerprints by Horner's rule, Sec. 3.2's value of a limb vector),
+    every normalized length, and a sample checked limb for limb against the oracle's product.
+    Runs outside every timed region."""
+    import numpy as np
+
+    import oracle
+    qs = _fp_moduli()
+    t0 = time.perf_counter()
+    fx = oracle.fingerprint_many(xs, qs)
+    fy = oracle.fingerprint_many(ys, qs)
+    fz = oracle.fingerprint_many(zs, qs)
+    bad = 0
+    for i in range(len(zs)):
+        ok = all(int(fz[i, j]) == int(fx[i, j]) * int(fy[i, j]) % q for j, q in enumerate(qs))
+        nzv = np.flatnonzero(zs[i])
+        ok = ok and int(nzs[i]) == (int(nzv[-1]) + 1 if nzv.size else 1)
+        bad += not ok
+    rng = np.random.Generator(np.random.PCG64(seed))
+    small = [i for i in range(len(zs)) if len(xs[i]) * len(ys[i]) <= 2 * 10**9]
+    sample = sorted(rng.choice(small, size=min(full_sample, len(small)), replace=False).tolist()) if small else []
+    full_bad = sum(not np.array_equal(zs[i], oracle.mul(xs[i], ys[i])) for i in sample)
+    return {"products": len(zs), "fingerprint_moduli": len(qs), "mismatches": bad,
+            "all_fingerprints_match": bad == 0, "full_oracle_sample": len(sample),
+            "full_oracle_mismatches": full_bad, "check_s": round(time.perf_counter() - t0, 2)}
+
+
+def run_batched(d, torch, dev, reps=5, count=4096, check=True):
     """4096 independent products, operand sizes log-uniform over 10^3..10^6 digits, 20% squarings:
     one dmul_batch call (grouped launches, replayed CUDA graph) against the same jobs issued one
-    at a time through dmul_mul."""
+    at a time through dmul_mul.  Every product is then checked against the oracle (fingerprints,
+    and a sample in full)."""
+    import numpy as np
     from paper_2011_11524_gb300 import workloads as wl
     jobs = wl.c4_jobs(count)
     dj = _upload_jobs(d, torch, jobs, dev)
@@ -436,16 +553,23 @@ def run_batched(d, torch, dev, reps=3, count=4096):
         assert d.dmul_batch(ctx.handle, arr, len(dj), sp) == 0
     assert d.dmul_sync(ctx.handle, sp) == 0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    best = None
+    times = []
     for _ in range(reps):
         torch.cuda.synchronize()
         e0.record(stream)
         assert d.dmul_batch(ctx.handle, arr, len(dj), sp) == 0
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        best = ms if best is None else min(best, ms)
+        times.append(e0.elapsed_time(e1))
     assert d.dmul_sync(ctx.handle, sp) == 0
+    statuses = d.job_statuses(arr, len(dj))
+    med = float(np.median(times))
+    verdict = None
+    if check:
+        zs = [d.to_host(z) for (_, _, _, _, z, _, _) in dj]
+        nzs = [int(nz.item()) for (_, _, _, _, _, _, nz) in dj]
+        verdict = check_products(d, [j.x for j in jobs], [j.y for j in jobs], zs, nzs, seed=4)
+        verdict["job_statuses_ok"] = all(v == d.DMUL_OK for v in statuses)
     # the plain form, one product at a time on the same stream
     for (tx, nx, ty, ny, z, L, nz) in dj[:64]:
         d.dmul_mul(ctx.handle, tx, nx, ty, ny, z, L, nz, sp)
@@ -460,20 +584,48 @@ def run_batched(d, torch, dev, reps=3, count=4096):
     plain_ms = max(e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3)
     assert d.dmul_sync(ctx.handle, sp) == 0
     ctx.close()
-    return {"workload": f"{count} jobs, digits log-uniform 10^3..10^6 per operand, 20% squarings",
-            "mults_per_s": count / (best * 1e-3), "digits_per_s": digits / (best * 1e-3),
-            "ms_per_batch": best, "plain_mults_per_s": count / (plain_ms * 1e-3),
-            "plain_ms_for_same_jobs": plain_ms, "speedup_vs_plain": plain_ms / best}
+    out = {"workload": f"{count} jobs, digits log-uniform 10^3..10^6 per operand, 20% squarings",
+           "mults_per_s": count / (med * 1e-3), "digits_per_s": digits / (med * 1e-3),
+           "ms_per_batch": med, "ms_per_batch_runs": [round(t, 4) for t in times],
+           "ms_per_batch_stat": f"median of {reps}",
+           "plain_mults_per_s": count / (plain_ms * 1e-3),
+           "plain_ms_for_same_jobs": plain_ms, "speedup_vs_plain": plain_ms / med}
+    if verdict is not None:
+        out["check"] = verdict
+        out["all_fingerprints_match"] = verdict["all_fingerprints_match"] and verdict["full_oracle_mismatches"] == 0
+    return out
 
 
-def run_served(d, torch, dev, count=2000, load=0.7, budget_gib=8, loads=(0.1, 0.3, 0.5, 0.9)):
+def run_served(d, torch, dev, distinct=2000, repeat=10, load=0.7, budget_gib=8,
+               loads=(0.1, 0.3, 0.5, 0.9), check=True):
     """Poisson stream of requests (digits log-uniform 10^2..10^7, 30% squarings) into the serving
     loop at a sweep of arrival rates (fractions `loads` and `load` of its measured saturated rate);
-    p50/p99 latency from arrival to completion at each.  The headline point is `load`."""
+    p50/p99 latency from arrival to completion at each.  The headline point is `load`.
+
+    Each rate point submits distinct * repeat requests (20,000 by default): `distinct` seeded
+    operand pairs, each submitted `repeat` times at its own Poisson arrival time and written to its
+    own output.  Every product is checked: the first copy of each pair against the oracle
+    (fingerprints, and a sample in full), every other copy, and every later rate point's outputs,
+    bit for bit against it on the device."""
+    import numpy as np
     from paper_2011_11524_gb300 import workloads as wl
-    _, jobs = wl.c5_stream(1.0, count)
-    dj = _upload_jobs(d, torch, jobs, dev)
-    arr = d.make_jobs(dj)
+    jp = wl.c5_pool(distinct)
+    count = distinct * repeat
+    dpool = torch.from_numpy(jp.pool.view(np.int32)).to(dev)
+    base = dpool.data_ptr()
+    Ls = np.array([len(j.x) + len(j.y) for j in jp.jobs], dtype=np.int64)
+    zoff = np.zeros(count + 1, dtype=np.int64)
+    zoff[1:] = np.cumsum(np.tile(Ls, repeat))
+    zbig = torch.full((int(zoff[-1]),), -1, dtype=torch.int32, device=dev)
+    nzs = torch.zeros(count, dtype=torch.int64, device=dev)
+    zb, nzb = zbig.data_ptr(), nzs.data_ptr()
+    rows = []
+    for r in range(count):
+        k = r % distinct
+        j = jp.jobs[k]
+        rows.append((base + 4 * int(jp.offsets[k, 0]), len(j.x), base + 4 * int(jp.offsets[k, 1]), len(j.y),
+                     zb + 4 * int(zoff[r]), int(Ls[k]), nzb + 8 * r))
+    arr = d.make_jobs(rows)
     budget = budget_gib << 30
     # one request of every transform length the stream uses: plans (twiddle tables, autotuned
     # splits) are built before the measurement and stay resident, as in a running server
@@ -486,24 +638,42 @@ def run_served(d, torch, dev, count=2000, load=0.7, budget_gib=8, loads=(0.1, 0.
             p *= 2
         return best, int(d.dmul_get_plan(None, n).N)
     warm, seen = [], set()
-    for i, j in enumerate(jobs):
-        nlen = tlen(len(j.x) + len(j.y))
+    for i in range(distinct):
+        nlen = tlen(int(Ls[i]))
         if nlen not in seen:
             seen.add(nlen)
             warm.append(i)
-    # saturated rate: everything submitted at once
+    verdict = None
     with d.Context(dev.index or 0, hbm_budget_bytes=budget) as srv:
         for i in warm + list(range(min(64, count))):
-            d.dmul_wait(srv.handle, d.dmul_submit(srv.handle, arr[i])[1])
+            assert d.dmul_wait(srv.handle, d.dmul_submit(srv.handle, arr[i])[1]) == 0
+        # saturated rate: everything submitted at once
         t0 = time.perf_counter()
         tk = [d.dmul_submit(srv.handle, arr[i])[1] for i in range(count)]
         for t in tk:
             assert d.dmul_wait(srv.handle, t) == 0
         sat = count / (time.perf_counter() - t0)
+        torch.cuda.synchronize()
+        # every copy of a pair equals the first; the first copies go to the oracle
+        zs = [zbig[int(zoff[r]):int(zoff[r + 1])] for r in range(count)]
+        copies_equal = all(torch.equal(zs[r], zs[r % distinct]) for r in range(distinct, count)) and \
+            torch.equal(nzs.view(repeat, distinct), nzs[:distinct].expand(repeat, distinct))
+        ref = zbig.clone()
+        ref_nz = nzs.clone()
+        if check:
+            zh = d.to_host(zbig[:int(zoff[distinct])])
+            verdict = check_products(d, [j.x for j in jp.jobs], [j.y for j in jp.jobs],
+                                     [zh[int(zoff[r]):int(zoff[r + 1])] for r in range(distinct)],
+                                     nzs[:distinct].cpu().tolist(), seed=5)
+            del zh
         sweep = []
+        later_equal = True
         for ld in sorted(set(list(loads) + [load])):
             rate = ld * sat
-            arrivals, _ = wl.c5_stream(rate, count)
+            arrivals = wl.c5_arrivals(rate, count)
+            zbig.fill_(-1)
+            nzs.zero_()
+            torch.cuda.synchronize()
             # one thread: submit at each arrival time, and in between poll every outstanding
             # ticket, oldest first, so that each request's completion is seen when it happens, not
             # when the requests before it complete
@@ -523,45 +693,110 @@ def run_served(d, torch, dev, count=2000, load=0.7, budget_gib=8, loads=(0.1, 0.
                 still = []
                 for k in pending:
                     rc, done = d.dmul_poll(srv.handle, tickets[k])
-                    assert rc == 0
                     if done:
+                        assert rc == 0
                         done_t[k] = time.perf_counter()
                         ndone += 1
                     else:
+                        assert rc == 0
                         still.append(k)
                 pending = still
             lat = sorted((done_t[i] - (start + float(arrivals[i]))) * 1e3 for i in range(count))
             wall = max(done_t) - start
+            torch.cuda.synchronize()
+            later_equal = later_equal and torch.equal(zbig, ref) and torch.equal(nzs, ref_nz)
             sweep.append({"load": ld, "offered_rate_per_s": rate, "mults_per_s": count / wall,
-                          "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]})
+                          "requests": count, "p50_ms": lat[len(lat) // 2],
+                          "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]})
         head_pt = next(p for p in sweep if p["load"] == load)
+        stats = d.dmul_serve_stats(srv.handle)
     # the same requests one at a time through the plain form, back to back
     with d.Context(dev.index or 0) as plain:
         stream = torch.cuda.Stream(device=dev)
         sp = stream.cuda_stream
-        for (tx, nx, ty, ny, z, L, nz) in [dj[i] for i in warm] + dj[:64]:
-            d.dmul_mul(plain.handle, tx, nx, ty, ny, z, L, nz, sp)
+        for r in warm + list(range(64)):
+            x, nx, y, ny, z, L, nz = rows[r]
+            d.dmul_mul(plain.handle, x, nx, y, ny, z, L, nz, sp)
         assert d.dmul_sync(plain.handle, sp) == 0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for (tx, nx, ty, ny, z, L, nz) in dj:
-            assert d.dmul_mul(plain.handle, tx, nx, ty, ny, z, L, nz, sp) == 0
+        for (x, nx, y, ny, z, L, nz) in rows:
+            assert d.dmul_mul(plain.handle, x, nx, y, ny, z, L, nz, sp) == 0
         assert d.dmul_sync(plain.handle, sp) == 0
         plain_rate = count / (time.perf_counter() - t0)
-    digits = sum(len(j.x) + len(j.y) for j in jobs) * 9
-    return {"workload": f"{count} Poisson requests, digits log-uniform 10^2..10^7, 30% squarings",
-            "plain_mults_per_s_same_requests": plain_rate,
-            "hbm_budget_gib": budget_gib, "saturated_mults_per_s": sat,
-            "offered_rate_per_s": head_pt["offered_rate_per_s"], "mults_per_s": head_pt["mults_per_s"],
-            "digits_per_s": digits / count * head_pt["mults_per_s"],
-            "p50_ms": head_pt["p50_ms"], "p99_ms": head_pt["p99_ms"], "load": load,
-            "sweep": sweep}
+        torch.cuda.synchronize()
+        plain_equal = torch.equal(zbig, ref) and torch.equal(nzs, ref_nz)
+    digits = int(np.tile(Ls, repeat).sum()) * 9
+    out = {"workload": f"{count} Poisson requests per rate point ({distinct} seeded operand pairs x {repeat}), "
+                       f"digits log-uniform 10^2..10^7, 30% squarings",
+           "plain_mults_per_s_same_requests": plain_rate,
+           "hbm_budget_gib": budget_gib, "saturated_mults_per_s": sat,
+           "offered_rate_per_s": head_pt["offered_rate_per_s"], "mults_per_s": head_pt["mults_per_s"],
+           "digits_per_s": digits / count * head_pt["mults_per_s"],
+           "p50_ms": head_pt["p50_ms"], "p99_ms": head_pt["p99_ms"], "load": load,
+           "requests_per_point": count, "sweep": sweep, "peak_running": stats["peak_running"],
+           "tickets_held_after": stats["held"],
+           "copies_bit_identical": bool(copies_equal), "rate_points_bit_identical": bool(later_equal),
+           "plain_form_bit_identical": bool(plain_equal)}
+    if verdict is not None:
+        out["check"] = verdict
+        out["all_fingerprints_match"] = (verdict["all_fingerprints_match"] and verdict["full_oracle_mismatches"] == 0
+                                         and bool(copies_equal) and bool(later_equal) and bool(plain_equal))
+    return out
 
 
-def cpu_baseline(x, y, z_gpu=None, budget_s=10.0, digits=DIGITS) -> dict:
+def host_cpu() -> dict:
+    """The host's core count and CPU model (lscpu where it names one, else the kernel's own)."""
+    import platform
+    fields = {}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            fields.setdefault(k.strip(), v.strip())
+    except Exception:
+        pass
+    model = fields.get("Model name") or fields.get("Vendor ID") or platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
+def libmpdec_context(sizes=(100_000, 1_000_000, DIGITS), budget_s=3.0) -> dict:
+    """CPython's decimal (libmpdec, the paper's comparison library, Sec. 10) multiplying random
+    operands of the same digit counts, single thread, operands built before timing, up to
+    floor(8 10^7 / n) repetitions per size as in the paper (capped by a time budget).  Context only:
+    a third-party library, not this project's oracle."""
+    import decimal
+
+    import numpy as np
+    from paper_2011_11524_gb300 import workloads as wl
+    if hasattr(sys, "set_int_max_str_digits"):
+        sys.set_int_max_str_digits(0)
+    ctx = decimal.Context(prec=decimal.MAX_PREC, Emax=decimal.MAX_EMAX, Emin=decimal.MIN_EMIN)
+    out = {"library": f"libmpdec {decimal.__libmpdec_version__} via CPython decimal", "threads": 1, "points": []}
+    for nd in sizes:
+        rng = np.random.Generator(np.random.PCG64(10 + nd % 97))
+        x, y = wl.random_operand(nd, rng), wl.random_operand(nd, rng)
+        dx = ctx.create_decimal("".join(f"{int(v):09d}" for v in x[::-1]))
+        dy = ctx.create_decimal("".join(f"{int(v):09d}" for v in y[::-1]))
+        reps, t0 = 0, time.perf_counter()
+        while reps < max(1, 80_000_000 // nd):
+            ctx.multiply(dx, dy)
+            reps += 1
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        el = time.perf_counter() - t0
+        out["points"].append({"digits": nd, "reps": reps, "ms_per_mult": el / reps * 1e3,
+                              "digits_per_s": 2 * nd * reps / el})
+    return out
+
+
+def cpu_baseline(x, y, z_gpu=None, budget_s=10.0, digits=DIGITS, all_cores=True, mpdec=True) -> dict:
     """The CPU oracle (slow two-prime NTT route, as it stands) on the same 2^24-digit product,
-    repeated until about budget_s seconds of CPU work.  Its product also checks, limb by limb, the
-    GPU's result of the last timed step."""
+    repeated until about budget_s seconds of CPU work, on one thread; then the same on every core
+    (independent products, one per thread).  Its product also checks, limb by limb, the GPU's
+    result of the last timed step.  libmpdec's timings are added as context."""
+    import concurrent.futures as cf
+
     import numpy as np
 
     import oracle
@@ -572,11 +807,24 @@ def cpu_baseline(x, y, z_gpu=None, budget_s=10.0, digits=DIGITS) -> dict:
         el = time.perf_counter() - t0
         if el >= budget_s or reps >= 8:
             break
+    cpu = host_cpu()
     out = {"value": 2 * digits * reps / el, "unit": "digits/s", "cores": 1, "kind": "oracle",
            "sample": f"{reps} full {digits} x {digits}-digit products by the oracle's two-prime NTT route "
-                     f"({el:.1f} s, single thread)"}
+                     f"({el:.1f} s, single thread)",
+           "host": cpu}
     if z_gpu is not None:
         out["gpu_result_matches_oracle"] = bool(np.array_equal(np.asarray(z_gpu), ref))
+    if all_cores and (cpu["nproc"] or 1) > 1:
+        n = int(cpu["nproc"])
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(max_workers=n) as ex:  # the oracle's C call releases the GIL
+            res = list(ex.map(lambda _: oracle.mul_ntt(x, y), range(n)))
+        el_all = time.perf_counter() - t0
+        out["all_cores"] = {"value": 2 * digits * n / el_all, "unit": "digits/s", "cores": n,
+                            "sample": f"{n} independent full products, one per thread ({el_all:.1f} s)",
+                            "all_equal": all(np.array_equal(r, ref) for r in res)}
+    if mpdec:
+        out["libmpdec_context"] = libmpdec_context()
     return out
 
 

@@ -7,7 +7,7 @@ Operands are little-endian base-10^9 ``uint32`` limb vectors.  An operand of ``d
 has ``ceil(d / 9)`` limbs; every limb but the top one is uniform in ``[0, 10^9 - 1]`` and the top
 limb is uniform over the values with exactly ``r = d - 9 (ceil(d/9) - 1)`` digits, so the leading
 decimal digit is nonzero.  The paper's own workload is random operands of ``n`` decimal digits
-(Sec. 10); the configurations below follow the recipe stated in the design doc.
+(Sec. 10); the functions below draw the five workload configurations.
 """
 from __future__ import annotations
 
@@ -121,14 +121,57 @@ def c4_jobs(count: int = 4096, lo_exp: float = 3.0, hi_exp: float = 6.0, p_squar
     return jobs
 
 
-def c5_stream(rate_per_s: float, count: int, lo_exp: float = 2.0, hi_exp: float = 7.0,
-              p_square: float = 0.3, seed: int = 5):
-    """Served workload: Poisson arrival times (seconds) and jobs, sizes log-uniform."""
+def c5_arrivals(rate_per_s: float, count: int, seed: int = 5) -> np.ndarray:
+    """Served workload: Poisson arrival times (seconds from the start) at the given rate."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    gaps = rng.exponential(1.0 / rate_per_s, size=count)
-    arrivals = np.cumsum(gaps)
-    jobs = c4_jobs(count, lo_exp, hi_exp, p_square, seed=seed + 1000)
-    return arrivals, jobs
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, size=count))
+
+
+@dataclass
+class JobPool:
+    """Jobs whose operands are consecutive, non-overlapping slices of one limb array, so that a
+    stream of tens of thousands of requests is drawn in one call and moved in one copy."""
+    pool: np.ndarray          # every operand's limbs, back to back
+    jobs: list                # Job objects whose x, y are views into pool
+    offsets: np.ndarray       # (count, 2) limb offsets of x and y in pool (y = x for a squaring)
+
+
+def pooled_jobs(count: int, lo_exp: float, hi_exp: float, p_square: float, seed: int) -> JobPool:
+    """The size law of c4_jobs (digits log-uniform per operand, a fraction p_square of
+    squarings), every limb uniform in [0, 10^9) except each operand's top limb, which is uniform
+    over the values with the operand's exact digit count."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sq = rng.random(count) < p_square
+    dx = np.floor(10.0 ** rng.uniform(lo_exp, hi_exp, size=count)).astype(np.int64)
+    dy = np.floor(10.0 ** rng.uniform(lo_exp, hi_exp, size=count)).astype(np.int64)
+    dy[sq] = dx[sq]
+    nx = -(-dx // LIMB_DIGITS)
+    ny = np.where(sq, 0, -(-dy // LIMB_DIGITS))
+    starts = np.zeros(2 * count + 1, dtype=np.int64)
+    starts[1:] = np.cumsum(np.stack([nx, ny], axis=1).reshape(-1))
+    pool = rng.integers(0, LIMB_BASE, size=int(starts[-1]), dtype=np.uint32)
+    offsets = np.stack([starts[0:-1:2], np.where(sq, starts[0:-1:2], starts[1:-1:2])], axis=1)
+    # top limbs: r = digits - 9 (limbs - 1) in 1..9; uniform over [10^(r-1), 10^r - 1]
+    for d, n, off, use in ((dx, nx, offsets[:, 0], np.ones(count, bool)), (dy, ny, offsets[:, 1], ~sq)):
+        r = d - LIMB_DIGITS * (n - 1)
+        lo = 10 ** (r - 1)
+        top = lo + np.floor(rng.random(count) * (9 * lo)).astype(np.int64)
+        pool[(off + n - 1)[use]] = top[use].astype(np.uint32)
+    jobs = []
+    for i in range(count):
+        x = pool[offsets[i, 0]:offsets[i, 0] + nx[i]]
+        if sq[i]:
+            jobs.append(Job(x, x, True))
+        else:
+            jobs.append(Job(x, pool[offsets[i, 1]:offsets[i, 1] + ny[i]], False))
+    return JobPool(pool, jobs, offsets)
+
+
+def c5_pool(count: int, lo_exp: float = 2.0, hi_exp: float = 7.0, p_square: float = 0.3,
+            seed: int = 5) -> JobPool:
+    """Served workload's requests: digits log-uniform over [10^2, 10^7] per operand, 30%
+    squarings (seed 5)."""
+    return pooled_jobs(count, lo_exp, hi_exp, p_square, seed + 1000)
 
 
 def fingerprint_candidates(seed: int = 61):

@@ -259,9 +259,13 @@ int dmul_carry_noalloc(const uint32_t *d, size_t L, uint32_t *z, size_t z_cap, u
 /* In-place transpose of a rows x cols row-major uint32 matrix on the device (Sec. 7.5-7.6):
  * square matrices by tile-pair swaps (TransposeSquareSubMatrix semantics); n x 2n by the paper's
  * procedure (rho on every row, then the two n x n halves transposed in place with row stride
- * 2n); 2n x n by its inverse (the halves first, then rho^-1 on every row).  rows and cols must
- * be equal or one twice the other, each a multiple of 32.  The row permutation's scratch is
- * the CTA's shared memory (2n words per row, Sec. 7.6). */
+ * 2n); 2n x n by its inverse (the halves first, then rho^-1 on every row); n x Cn and Cn x n for
+ * any integer C by the generalization the paper closes Sec. 7.6 with (rho_C: column C i + k of a
+ * row to position k n + i, then the C blocks; the mirror for Cn x n).  rows and cols must each be
+ * a multiple of 32, the larger a multiple of the smaller and at most 16384 when they differ.
+ * The row permutation's scratch is the CTA's shared memory (C n words per row, Sec. 7.6).  A
+ * 16-byte aligned matrix moves through the bulk-copy engine: 2-D tensor-map tile loads of the
+ * tile pairs and one bulk copy per permuted row; otherwise plain loads. */
 int dmul_transpose(dmul_ctx *ctx, uint32_t *a, size_t rows, size_t cols, void *stream);
 
 /* ---- host-side information (no GPU work; usable without a device) ---------------------------- */

@@ -551,14 +551,14 @@ int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
         }
         {
             Timed t(c, kStTranspose, s);
-            CK(launch_transpose(A, pd.N1, pd.N2, kPrimes, N, s));
+            CK(launch_transpose(A, pd.N1, pd.N2, kPrimes, N, s, c->status));
         }
         {
             Timed t(c, kStRowDft, s);
             CK(launch_rowdft_fwd_tw(pd, A, s));
         }
         Timed t(c, kStTranspose, s);
-        CK(launch_transpose(A, pd.N2, pd.N1, kPrimes, N, s));
+        CK(launch_transpose(A, pd.N2, pd.N1, kPrimes, N, s, c->status));
     }
     {
         Timed t(c, kStRowMul, s);
@@ -566,14 +566,14 @@ int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
     }
     {
         Timed t(c, kStTranspose, s);
-        CK(launch_transpose(c->X, pd.N1, pd.N2, kPrimes, N, s));
+        CK(launch_transpose(c->X, pd.N1, pd.N2, kPrimes, N, s, c->status));
     }
     {
         Timed t(c, kStRowDft, s);
         CK(launch_rowdft_inv_tw(pd, c->X, s));
     }
     Timed t(c, kStTranspose, s);
-    CK(launch_transpose(c->X, pd.N2, pd.N1, kPrimes, N, s));
+    CK(launch_transpose(c->X, pd.N2, pd.N1, kPrimes, N, s, c->status));
     return DMUL_OK;
 }
 
@@ -796,14 +796,16 @@ int dmul_carry(dmul_ctx *c, const uint32_t *d, size_t L, uint32_t *z, size_t z_c
 
 int dmul_transpose(dmul_ctx *c, uint32_t *a, size_t rows, size_t cols, void *stream) {
     if (!c || !a) return DMUL_ERR_INVALID;
-    if (rows % 32 || cols % 32 || rows == 0) return DMUL_ERR_INVALID;
-    if (!(rows == cols || rows == 2 * cols || cols == 2 * rows)) return DMUL_ERR_INVALID;
+    if (rows % 32 || cols % 32 || rows == 0 || cols == 0) return DMUL_ERR_INVALID;
+    // square, or n x Cn / Cn x n with C n <= 16384 (the permuted row lives in shared memory)
+    const size_t lo = rows < cols ? rows : cols, hi = rows < cols ? cols : rows;
+    if (hi % lo || (hi != lo && hi > 16384)) return DMUL_ERR_INVALID;
     int rc = set_device(c);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     c->last_stream = s;
     Timed t(c, kStTranspose, s);
-    CK(launch_transpose(a, rows, cols, 1, rows * cols, s));
+    CK(launch_transpose(a, rows, cols, 1, rows * cols, s, c->status));
     return DMUL_OK;
 }
 

@@ -118,7 +118,7 @@ __device__ __forceinline__ void scenter(uint32_t *sx, const uint32_t *sy, uint32
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const uint32_t a = v[0][outpos<R>(k)];
-            z[k] = mont<PI>(a, SQR ? a : v[1][outpos<R>(k)]);
+            z[k] = pointwise<PI>(a, SQR ? a : v[1][outpos<R>(k)]);
         }
         dft<PI, 1, R, 2>(z);
         uint32_t *sb = sx + 17 * b;

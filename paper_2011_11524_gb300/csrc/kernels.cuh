@@ -172,8 +172,10 @@ cudaError_t launch_carry(uint32_t *z, const uint2 *spill, uint64_t L, CarryCtl *
 // Six-step pieces (Sec. 7.2, 7.6).
 cudaError_t launch_pack(const uint32_t *x, uint64_t nx, uint64_t N, uint32_t *X, uint32_t *status,
                         cudaStream_t s);
+// In place; 16-byte aligned matrices take the TMA-fed kernels (tensor-map tile loads of the I <= J
+// tile pairs, bulk-copied rows for rho).  status (may be null) receives an expired bounded wait.
 cudaError_t launch_transpose(uint32_t *a, uint64_t rows, uint64_t cols, uint64_t batch,
-                             uint64_t batch_stride, cudaStream_t s);
+                             uint64_t batch_stride, cudaStream_t s, uint32_t *status = nullptr);
 cudaError_t launch_rowdft_fwd_tw(const PlanDev &pd, uint32_t *A, cudaStream_t s);
 cudaError_t launch_rowdft_inv_tw(const PlanDev &pd, uint32_t *A, cudaStream_t s);
 cudaError_t launch_crt_natural(const uint32_t *X, uint64_t N, uint64_t L, InvMode mode,

@@ -67,6 +67,33 @@ __device__ __forceinline__ uint32_t mont(uint32_t a, uint32_t b) {
     return hi - t + c_prime[PI].p;
 }
 
+// The signed Montgomery product of the Prospects (Sec. 9) on the same unadjusted inputs: centred
+// a - p, b - p in [-p, p), m = lo((a-p)(b-p)) p^-1 mod 2^32 as a signed word, and
+// r = hi((a-p)(b-p)) - hi(m p) (signed high halves) lies in (-3p/4, 3p/4): |(a-p)(b-p)| <= p^2
+// < p 2^30 puts the first high half within p/4 of 0 and |m p| < p 2^31 the second within p/2.
+// So r + p is in (0, 2p) with no correction, congruent to ab 2^-32 mod p, as mont() returns.  It
+// costs the two centring subtractions on top of mont()'s instructions, which is why the row pass
+// keeps mont() (the measured comparison builds with -DDMUL_POINTWISE_SIGNED).
+template <int PI>
+__device__ __forceinline__ uint32_t mont_signed(uint32_t a, uint32_t b) {
+    const int32_t p = (int32_t)c_prime[PI].p;
+    const int32_t sa = (int32_t)a - p, sb = (int32_t)b - p;
+    const int64_t t = (int64_t)sa * sb;
+    const int32_t m = (int32_t)((uint32_t)t * c_prime[PI].pinv);
+    const int32_t hm = __mulhi(m, p);
+    return (uint32_t)((int32_t)(t >> 32) - hm + p);
+}
+
+// The pointwise product of the row pass: mont(), or mont_signed() in the comparison build.
+template <int PI>
+__device__ __forceinline__ uint32_t pointwise(uint32_t a, uint32_t b) {
+#ifdef DMUL_POINTWISE_SIGNED
+    return mont_signed<PI>(a, b);
+#else
+    return mont<PI>(a, b);
+#endif
+}
+
 // Gentleman-Sande (DIF) butterfly of Sec. 5.3 on unadjusted values: x' = x + y,
 // y' = (x - y) * xi_16^e.  e == 0 is the factor-1 butterfly of Sec. 5.6 (no multiply).
 // RS / RD = false leave the sum / the factor-1 difference in [0, 4p) unreduced: allowed only

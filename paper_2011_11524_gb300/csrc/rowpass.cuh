@@ -176,7 +176,7 @@ __device__ __forceinline__ void row_center_ct(uint32_t *sx, const uint32_t *sy, 
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const uint32_t a = v[0][outpos<R>(k)];
-            z[k] = mont<PI>(a, SQR ? a : v[1][outpos<R>(k)]);
+            z[k] = pointwise<PI>(a, SQR ? a : v[1][outpos<R>(k)]);
         }
         dft<PI, 1, R, 2>(z);
         uint32_t *sb = sx + 17 * b;

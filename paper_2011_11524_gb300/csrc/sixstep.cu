@@ -9,11 +9,15 @@
 // the first one of the inverse are omitted (Sec. 7.4).  The DFTs of step 2 leave their outputs in
 // the stage order (no bit reversal): the twiddle is indexed by the true frequency of each position,
 // and the inverse mirrors the order, so no reordering pass is needed.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "kernels.cuh"
 #include "modarith.cuh"
+#include "tma.cuh"
 
 namespace dml {
 
@@ -97,39 +101,246 @@ __global__ void __launch_bounds__(256) k_permute_rho(uint32_t *a, uint64_t n, ui
     }
 }
 
-static cudaError_t square_sub(uint32_t *a, uint64_t n, uint64_t rs, uint64_t batch,
-                              uint64_t batch_stride, cudaStream_t s) {
+// ---- the TMA-fed forms of both (used whenever the matrix is 16-byte aligned) -------------------
+constexpr uint64_t kRhoMaxBytes = 16384 * 4 + 16;  // rows of up to 16384 words, and the barrier
+constexpr uint64_t kRhoCMaxWords = 16384;          // the longest row rho_C permutes (n x Cn: C n)
+// Square tile-pair swap: one CTA per pair of 32 x 32 tiles (I, J), I <= J, of the n x n submatrix
+// (pair index p = J (J + 1) / 2 + I, so no CTA is launched for I > J).  Both tiles arrive in shared
+// memory through a 3-D tensor map (columns, rows, batch) before anything is written, which makes
+// the swap in place.  Each thread then transposes 4 x 4 blocks in registers: 128-bit shared loads
+// along a tile row (eight lanes cover one 128-byte row, so no bank conflict) and 128-bit global
+// stores.  xoff is the submatrix's first column within the mapped rows (0, or n for the right
+// half of an n x 2n matrix).
+constexpr uint32_t kTT = 32;
+
+__device__ __forceinline__ void tile_pair(uint32_t p, uint32_t &I, uint32_t &J) {
+    uint32_t j = (uint32_t)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+    while ((j + 1) * (j + 2) / 2 <= p) ++j;
+    while (j * (j + 1) / 2 > p) --j;
+    J = j;
+    I = p - j * (j + 1) / 2;
+}
+
+__global__ void __launch_bounds__(128) k_transpose_tma(const __grid_constant__ CUtensorMap map, uint32_t *a,
+                                                       uint64_t rs, uint64_t batch_stride, uint32_t xoff,
+                                                       uint32_t *status) {
+    __shared__ __align__(128) uint32_t tile[2][kTT * kTT];
+    __shared__ __align__(8) uint64_t bar;
+    uint32_t I, J;
+    tile_pair(blockIdx.x, I, J);
+    const uint32_t z = blockIdx.y;
+    const bool diag = I == J;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect_tx(&bar, (diag ? 1u : 2u) * kTT * kTT * 4u);
+        tma_load_3d(tile[0], &map, (int)(xoff + J * kTT), (int)(I * kTT), (int)z, &bar);
+        if (!diag) tma_load_3d(tile[1], &map, (int)(xoff + I * kTT), (int)(J * kTT), (int)z, &bar);
+    }
+    __syncthreads();
+    if (!__syncthreads_and(mbar_wait(&bar, 0) ? 1 : 0)) {
+        if (threadIdx.x == 0) {
+            if (status) atomicOr(status, kStatusTimeout);
+            mbar_wait(&bar, 0);  // the copies in flight (bounded again)
+        }
+        return;
+    }
+    const uint32_t w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const uint32_t sel = w >> 1;  // 0: tile (I, J) goes to (J, I); 1: tile (J, I) goes to (I, J)
+    if (sel == 1 && diag) return;
+    const uint32_t R = sel ? J : I, C = sel ? I : J;  // the source tile's row and column tile
+    const uint32_t c = l & 7, q = (l >> 3) + 4 * (w & 1);
+    const uint32_t *S = tile[sel];
+    uint4 v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = *(const uint4 *)&S[(4 * q + i) * kTT + 4 * c];
+    uint32_t *m = a + (uint64_t)z * batch_stride;
+    const uint64_t col = xoff + R * kTT + 4 * q;
+    uint64_t row = (uint64_t)C * kTT + 4 * c;
+    *(uint4 *)&m[row * rs + col] = make_uint4(v[0].x, v[1].x, v[2].x, v[3].x);
+    *(uint4 *)&m[(row + 1) * rs + col] = make_uint4(v[0].y, v[1].y, v[2].y, v[3].y);
+    *(uint4 *)&m[(row + 2) * rs + col] = make_uint4(v[0].z, v[1].z, v[2].z, v[3].z);
+    *(uint4 *)&m[(row + 3) * rs + col] = make_uint4(v[0].w, v[1].w, v[2].w, v[3].w);
+}
+
+// rho / rho^-1 on every row of an n x 2n matrix, the row brought into shared memory by one bulk
+// copy, the permuted row written back with 128-bit stores: rho sends (z[8k], z[8k+2], z[8k+4],
+// z[8k+6]) to p[4k..4k+3] and the odd ones to p[n+4k..n+4k+3]; rho^-1 interleaves z[4k..4k+3]
+// with z[n+4k..n+4k+3] into p[8k..8k+7].
+__global__ void __launch_bounds__(256) k_permute_rho_tma(uint32_t *a, uint64_t n, uint64_t batch_stride,
+                                                         int inverse, uint32_t *status) {
+    extern __shared__ __align__(128) uint32_t zeta[];
+    uint64_t *bar = (uint64_t *)(zeta + 2 * n);
+    uint32_t *p = a + (uint64_t)blockIdx.z * batch_stride + (uint64_t)blockIdx.x * 2 * n;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect_tx(bar, (uint32_t)(8 * n));
+        tma_load_1d(zeta, p, (uint32_t)(8 * n), bar);
+    }
+    __syncthreads();
+    if (!__syncthreads_and(mbar_wait(bar, 0) ? 1 : 0)) {
+        if (threadIdx.x == 0) {
+            if (status) atomicOr(status, kStatusTimeout);
+            mbar_wait(bar, 0);
+        }
+        return;
+    }
+    for (uint64_t k = threadIdx.x; k < n / 4; k += blockDim.x) {
+        if (!inverse) {
+            const uint4 lo = *(const uint4 *)&zeta[8 * k], hi = *(const uint4 *)&zeta[8 * k + 4];
+            *(uint4 *)&p[4 * k] = make_uint4(lo.x, lo.z, hi.x, hi.z);
+            *(uint4 *)&p[n + 4 * k] = make_uint4(lo.y, lo.w, hi.y, hi.w);
+        } else {
+            const uint4 e = *(const uint4 *)&zeta[4 * k], o = *(const uint4 *)&zeta[n + 4 * k];
+            *(uint4 *)&p[8 * k] = make_uint4(e.x, o.x, e.y, o.y);
+            *(uint4 *)&p[8 * k + 4] = make_uint4(e.z, o.z, e.w, o.w);
+        }
+    }
+}
+
+// The generalization to n x Cn matrices (the closing remark of Sec. 7.6): with M = [A_0 ... A_{C-1}],
+// transposing every n x n block in place gives rows alpha^0_1, alpha^1_1, ..., alpha^{C-1}_1, alpha^0_2
+// ... where M^T wants all alpha^0 first, then all alpha^1, and so on: the row permutation
+// rho_C(i) = n (i mod C) + (i div C) of the Cn x n view, which equals rho_C on the columns of M
+// before the block transposes.  So the forward applies p[k n + i] <- z[C i + k] (k < C, i < n) to
+// every row of M, then the C block transposes; the inverse (Cn x n) the block transposes of the
+// n x Cn view, then p[C i + k] <- z[k n + i].  The row (Cn words) is the CTA's shared memory; it
+// arrives by one bulk copy when the row is 16-byte aligned.
+__global__ void __launch_bounds__(256) k_permute_rho_c(uint32_t *a, uint64_t n, uint32_t C, uint64_t batch_stride,
+                                                       int inverse, int bulk, uint32_t *status) {
+    extern __shared__ __align__(128) uint32_t zeta[];
+    const uint64_t len = (uint64_t)C * n;
+    uint64_t *bar = (uint64_t *)(zeta + len + (len & 1));
+    uint32_t *p = a + (uint64_t)blockIdx.z * batch_stride + (uint64_t)blockIdx.x * len;
+    if (bulk) {
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            mbar_expect_tx(bar, (uint32_t)(4 * len));
+            tma_load_1d(zeta, p, (uint32_t)(4 * len), bar);
+        }
+        __syncthreads();
+        if (!__syncthreads_and(mbar_wait(bar, 0) ? 1 : 0)) {
+            if (threadIdx.x == 0) {
+                if (status) atomicOr(status, kStatusTimeout);
+                mbar_wait(bar, 0);
+            }
+            return;
+        }
+    } else {
+        for (uint64_t i = threadIdx.x; i < len; i += blockDim.x) zeta[i] = p[i];
+        __syncthreads();
+    }
+    for (uint64_t o = threadIdx.x; o < len; o += blockDim.x) {
+        if (!inverse) {
+            const uint64_t k = o / n, i = o - k * n;  // p[k n + i] <- z[C i + k]
+            p[o] = zeta[C * i + k];
+        } else {
+            const uint64_t i = o / C, k = o - i * C;  // p[C i + k] <- z[k n + i]
+            p[o] = zeta[k * n + i];
+        }
+    }
+}
+
+// cuTensorMapEncodeTiled, from the driver through the runtime (no link against libcuda).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                   CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// A tensor map of 32 x 32 uint32 boxes over `batch` matrices of `rows` rows of `cols` words (row
+// stride rs words, matrix stride bs words).  False when the base is not 16-byte aligned or the
+// driver refuses the map; the caller then takes the plain kernels.
+static bool tile_map(CUtensorMap *m, uint32_t *a, uint64_t cols, uint64_t rows, uint64_t batch, uint64_t rs,
+                     uint64_t bs) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || ((uintptr_t)a & 15) || (rs % 4) || (bs % 4)) return false;
+    const cuuint64_t dims[3] = {cols, rows, batch};
+    const cuuint64_t strides[2] = {rs * 4, bs * 4};
+    const cuuint32_t box[3] = {kTT, kTT, 1}, es[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, a, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The n x n submatrix starting at column xoff of the rows of `a` (row stride rs) transposed in place.
+static cudaError_t square_sub(uint32_t *a, uint64_t n, uint64_t rs, uint64_t xoff, uint64_t batch,
+                              uint64_t batch_stride, cudaStream_t s, uint32_t *status) {
+    CUtensorMap map;
+    if (tile_map(&map, a, rs, n, batch, rs, batch_stride)) {
+        const uint64_t T = n / kTT;
+        k_transpose_tma<<<dim3((unsigned)(T * (T + 1) / 2), (unsigned)batch), 128, 0, s>>>(
+            map, a, rs, batch_stride, (uint32_t)xoff, status);
+        return cudaGetLastError();
+    }
     dim3 grid((unsigned)(n / 32), (unsigned)(n / 32), (unsigned)batch);
-    k_transpose_square<<<grid, 256, 0, s>>>(a, n, rs, batch_stride);
+    k_transpose_square<<<grid, 256, 0, s>>>(a + xoff, n, rs, batch_stride);
     return cudaGetLastError();
 }
 
 static cudaError_t rho_rows(uint32_t *a, uint64_t n, uint64_t batch, uint64_t batch_stride,
-                            int inverse, cudaStream_t s) {
+                            int inverse, cudaStream_t s, uint32_t *status) {
     dim3 grid((unsigned)n, 1, (unsigned)batch);
+    if (!((uintptr_t)a & 15) && !(batch_stride % 4) && 8 * n + 16 <= kRhoMaxBytes) {
+        k_permute_rho_tma<<<grid, 256, 8 * n + 16, s>>>(a, n, batch_stride, inverse, status);
+        return cudaGetLastError();
+    }
     k_permute_rho<<<grid, 256, 2 * n * sizeof(uint32_t), s>>>(a, n, batch_stride, inverse);
     return cudaGetLastError();
 }
 
 cudaError_t launch_transpose(uint32_t *a, uint64_t rows, uint64_t cols, uint64_t batch,
-                             uint64_t batch_stride, cudaStream_t s) {
+                             uint64_t batch_stride, cudaStream_t s, uint32_t *status) {
     cudaError_t e;
-    if (rows == cols) return square_sub(a, rows, cols, batch, batch_stride, s);
+    if (rows == cols) return square_sub(a, rows, cols, 0, batch, batch_stride, s, status);
     if (cols == 2 * rows) {
         // TransposeMatrixNx2N: rho on every row, then the left and right n x n halves (stride 2n)
         const uint64_t n = rows;
-        if ((e = rho_rows(a, n, batch, batch_stride, 0, s)) != cudaSuccess) return e;
-        if ((e = square_sub(a, n, 2 * n, batch, batch_stride, s)) != cudaSuccess) return e;
-        return square_sub(a + n, n, 2 * n, batch, batch_stride, s);
+        if ((e = rho_rows(a, n, batch, batch_stride, 0, s, status)) != cudaSuccess) return e;
+        if ((e = square_sub(a, n, 2 * n, 0, batch, batch_stride, s, status)) != cudaSuccess) return e;
+        return square_sub(a, n, 2 * n, n, batch, batch_stride, s, status);
     }
     if (rows == 2 * cols) {
         // TransposeMatrix2NxN: the two halves of the n x 2n view first, then rho^-1 on every row
         const uint64_t n = cols;
-        if ((e = square_sub(a, n, 2 * n, batch, batch_stride, s)) != cudaSuccess) return e;
-        if ((e = square_sub(a + n, n, 2 * n, batch, batch_stride, s)) != cudaSuccess) return e;
-        return rho_rows(a, n, batch, batch_stride, 1, s);
+        if ((e = square_sub(a, n, 2 * n, 0, batch, batch_stride, s, status)) != cudaSuccess) return e;
+        if ((e = square_sub(a, n, 2 * n, n, batch, batch_stride, s, status)) != cudaSuccess) return e;
+        return rho_rows(a, n, batch, batch_stride, 1, s, status);
     }
-    return cudaErrorInvalidValue;
+    // n x Cn and Cn x n for C > 2: rho_C, then the C block transposes (or the mirror)
+    const bool wide = cols > rows;
+    const uint64_t n = wide ? rows : cols, C = wide ? cols / rows : rows / cols;
+    if (C * n != (wide ? cols : rows) || C * n > kRhoCMaxWords) return cudaErrorInvalidValue;
+    const int bulk = !((uintptr_t)a & 15) && !(batch_stride % 4);
+    const size_t smem = C * n * 4 + 16;
+    dim3 grid((unsigned)n, 1, (unsigned)batch);
+    if (wide) {
+        k_permute_rho_c<<<grid, 256, smem, s>>>(a, n, (uint32_t)C, batch_stride, 0, bulk, status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    for (uint64_t k = 0; k < C; ++k)
+        if ((e = square_sub(a, n, C * n, k * n, batch, batch_stride, s, status)) != cudaSuccess) return e;
+    if (!wide) {
+        k_permute_rho_c<<<grid, 256, smem, s>>>(a, n, (uint32_t)C, batch_stride, 1, bulk, status);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
 }
 
 // ---- step 2 (and its inverse): length-N1 DFTs along the contiguous rows of the N2 x N1 matrix,
@@ -318,6 +529,10 @@ cudaError_t init_kernel_attributes_sixstep() {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_permute_rho, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   16384 * 4)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_permute_rho_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kRhoMaxBytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_permute_rho_c, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(kRhoCMaxWords * 4 + 16))) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_rowdft6<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   8192 * 4)) != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_rowdft6<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 4);

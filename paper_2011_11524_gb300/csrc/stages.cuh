@@ -20,6 +20,7 @@
 
 #include "kernels.cuh"
 #include "modarith.cuh"
+#include "tma.cuh"
 
 namespace dml {
 
@@ -368,7 +369,7 @@ __device__ __forceinline__ void row_fused_center(uint32_t *sx, const uint32_t *s
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             uint32_t a = vx[outpos<R>(k)];
-            z[k] = mont<PI>(a, SQR ? a : vy[outpos<R>(k)]);
+            z[k] = pointwise<PI>(a, SQR ? a : vy[outpos<R>(k)]);
         }
         dft<PI, 1, R>(z);
 #pragma unroll
@@ -484,7 +485,7 @@ __device__ __forceinline__ void row_center_lazy(uint32_t *sx, const uint32_t *sy
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const uint32_t a = v[0][outpos<R>(k)];
-            z[k] = mont<PI>(a, SQR ? a : v[1][outpos<R>(k)]);
+            z[k] = pointwise<PI>(a, SQR ? a : v[1][outpos<R>(k)]);
         }
         dft<PI, 1, R, LAZY_OUT ? 2 : 0>(z);
 #pragma unroll
@@ -526,42 +527,6 @@ __device__ __forceinline__ void row_mul_body(const PlanDev &pd, uint32_t *sm, ui
 }
 
 // ---- TMA (bulk async copy) helpers -----------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-// 1-D bulk copy global -> shared, completion counted on the mbarrier (16-byte aligned, size % 16 == 0)
-__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-// Bounded wait for the mbarrier phase with the given parity; false when the bound runs out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = 0) {
-    if (!limit) limit = 1u << 20;
-    for (uint32_t i = 0; i < limit; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(smem_addr(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
 // Persistent, TMA-fed row pass: CTA (g, prime) handles rows g, g + G, ...; while it computes one
 // row, the bulk-copy engine brings the next row's X and Y into the other landing buffer.
 // Shared memory: landing buffers [2][X, Y] (plain layout) + working buffers [X, Y] (swizzled)

@@ -336,6 +336,9 @@ def test_argument_errors(d, ctx):
     assert d.dmul_mul(ctx.handle, t, 10, t, 10, t, 20, None) == d.DMUL_ERR_INVALID  # z aliases x
     big = 3 * 2**22
     assert d.dmul_mul(ctx.handle, t, big, t, 10, z, big + 10, None) == d.DMUL_ERR_TOO_LARGE
+    # transposes: sides multiples of 32, the larger a multiple of the smaller, at most 16384 apart
+    for rows, cols in ((64, 96), (96, 64), (32, 32768), (33, 33), (0, 32)):
+        assert d.dmul_transpose(ctx.handle, z, rows, cols) == d.DMUL_ERR_INVALID
 
 
 @pytest.mark.parametrize("n,m", [(7777, 5555), (300000, 250001), (1 << 20, (1 << 20) - 3)])
@@ -468,16 +471,29 @@ def test_sixstep_plan_shapes(d, ctx6):
         assert (info.N1, info.N2) == (n1, n2) and info.sixstep == 1
 
 
-@pytest.mark.parametrize("rows,cols", [(32, 32), (64, 64), (32, 64), (64, 32), (256, 512), (512, 256),
-                                       (1024, 1024), (1024, 2048), (2048, 1024)])
-def test_inplace_transpose(d, ctx, rows, cols):
+@pytest.mark.parametrize("rows,cols", [(32, 32), (64, 64), (32, 64), (64, 32), (96, 96), (256, 512), (512, 256),
+                                       (1024, 1024), (1024, 2048), (2048, 1024), (2048, 4096),
+                                       (4096, 2048), (4096, 4096),
+                                       # n x Cn and Cn x n, C > 2 (the generalization of Sec. 7.6)
+                                       (32, 96), (96, 32), (64, 256), (256, 64), (128, 640),
+                                       (640, 128), (2048, 8192), (8192, 2048), (32, 16384)])
+@pytest.mark.parametrize("aligned", [True, False], ids=["tma", "unaligned"])
+def test_inplace_transpose(d, ctx, rows, cols, aligned):
+    """In place against the oracle's out-of-place transpose (the definition) and back.  A 16-byte aligned matrix
+    takes the tensor-map tile loads (and bulk-copied rows for rho); one offset by a word takes the
+    plain kernels."""
+    if not aligned and rows * cols > 1 << 22:
+        pytest.skip("the plain kernels are covered at the smaller sizes")
     rng = _rng(9000 + rows + cols)
     a = rng.integers(0, 2**32, size=rows * cols, dtype=np.uint64).astype(np.uint32)
-    t = d.to_device(a)
+    buf = torch.zeros(rows * cols + 4, dtype=torch.int32, device="cuda")
+    t = buf[0:rows * cols] if aligned else buf[1:1 + rows * cols]
+    t.copy_(d.to_device(a))
     ctx.transpose_(t, rows, cols)
     assert np.array_equal(d.to_host(t), oracle.transpose(a, rows, cols))
     ctx.transpose_(t, cols, rows)  # and back
     assert np.array_equal(d.to_host(t), a)
+    assert int(buf[-1].item()) == 0 and (aligned or int(buf[0].item()) == 0)  # nothing outside
 
 
 def test_c1_workload(d, ctx):

@@ -4,6 +4,7 @@ import math
 import os
 import re
 
+import numpy as np
 import pytest
 
 import oracle
@@ -145,3 +146,29 @@ def test_every_admissible_length_plans(N):
     assert d.dmul_get_plan(None, N - 1).N == N
     if N < 3 * 2**22:
         assert d.dmul_get_plan(None, N + 1).N > N
+
+
+@pytest.mark.parametrize("n,C", [(4, 2), (4, 3), (6, 4), (5, 5), (3, 8)])
+def test_rho_c_then_block_transposes_is_the_transpose(n, C):
+    """The generalization closing Sec. 7.6, as the library's n x Cn transpose applies it: moving
+    column C i + k of every row to position k n + i, then transposing each of the C n x n blocks
+    in place, gives M^T in row-major order; the mirror (blocks of the n x Cn view, then the
+    inverse move on every row) undoes it.  Checked against numpy's transpose."""
+    rng = np.random.default_rng(n * 10 + C)
+    M = rng.integers(0, 1 << 30, size=(n, C * n))
+    P = np.empty_like(M)
+    for k in range(C):
+        for i in range(n):
+            P[:, k * n + i] = M[:, C * i + k]
+    for k in range(C):
+        P[:, k * n:(k + 1) * n] = P[:, k * n:(k + 1) * n].T.copy()
+    assert np.array_equal(P.reshape(-1), M.T.reshape(-1))
+    # inverse: the flat array seen as n x Cn again, blocks transposed, then the inverse move
+    Q = P.reshape(n, C * n).copy()
+    for k in range(C):
+        Q[:, k * n:(k + 1) * n] = Q[:, k * n:(k + 1) * n].T.copy()
+    R = np.empty_like(Q)
+    for i in range(n):
+        for k in range(C):
+            R[:, C * i + k] = Q[:, k * n + i]
+    assert np.array_equal(R, M)

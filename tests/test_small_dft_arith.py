@@ -135,3 +135,31 @@ def test_shoup_and_montgomery_bounds():
             for b in [0, 1, 2 * p - 1] + [int(x) for x in rng.integers(0, 2 * p, 20)]:
                 r = mont(a, b, p, pinv)
                 assert 0 < r < 2 * p and r % p == a * b * r_inv % p
+
+
+def mont_signed(a, b, p, pinv):
+    """Signed Montgomery (Sec. 9, Prospects) on centred inputs a - p, b - p: signed high halves,
+    r = hi(ab') - hi(m p) + p with m the signed low word times p^-1 mod 2^32."""
+    sa, sb = a - p, b - p
+    t = sa * sb
+    lo = t & M32
+    m = (lo * pinv) & M32
+    m = m - (1 << 32) if m >= 1 << 31 else m
+    assert (t - m * p) % (1 << 32) == 0
+    r = (t >> 32) - ((m * p) >> 32) + p  # Python's >> floors, as the arithmetic shift does
+    return r
+
+
+def test_signed_montgomery_bounds():
+    """The signed form returns ab 2^-32 mod p in (0, 2p) for inputs in [0, 2p), like the
+    subtractive form, with no correction step."""
+    rng = np.random.Generator(np.random.PCG64(37))
+    for p in d.dmul_primes():
+        pinv = pow(p, -1, 1 << 32)
+        r_inv = pow(1 << 32, -1, p)
+        vals = [0, 1, p - 1, p, p + 1, 2 * p - 1] + [int(x) for x in rng.integers(0, 2 * p, 300)]
+        for a in vals:
+            for b in vals[:6] + [int(x) for x in rng.integers(0, 2 * p, 20)]:
+                r = mont_signed(a, b, p, pinv)
+                assert 0 < r < 2 * p and r % p == a * b * r_inv % p
+                assert r % p == mont(a, b, p, pinv) % p

@@ -97,6 +97,52 @@ __device__ __forceinline__ void fwd_stage_ct(const Stage &st, const uint2 *tw, u
     }
 }
 
+// The same stage on X and Y at once (a product, not a square): the groups of X and Y with the
+// same index share their twiddle index j, so each thread loads the R - 1 twiddles once for both,
+// and the two independent DFTs give the scheduler twice the instruction-level parallelism.
+template <int PI, uint32_t R, uint32_t M, uint32_t N>
+__device__ __forceinline__ void fwd_stage_pair(const Stage &st, const uint2 *tw, uint32_t *sx, uint32_t *sy,
+                                               const uint32_t *gx, const uint32_t *gy, bool from_plain,
+                                               uint32_t rows) {
+    constexpr uint32_t stride = M / R;
+    constexpr uint32_t pstride = stride + stride / 16;
+    static_assert(stride % 16 == 0, "padded rows need strides that are multiples of 16");
+    const uint32_t per_op = rows * (N / R);
+    constexpr bool has_tw = M > R;
+    for (uint32_t g = threadIdx.x; g < per_op; g += blockDim.x) {
+        const uint32_t blk = g / stride, j = g % stride;
+        const uint32_t base = blk * M + j;
+        uint32_t *px = sx + pidx(base), *py = sy + pidx(base);
+        uint32_t v[R], u[R];
+        if (from_plain) {
+#pragma unroll
+            for (uint32_t k = 0; k < R; ++k) {
+                v[k] = gx[base + k * stride];
+                u[k] = gy[base + k * stride];
+            }
+        } else {
+#pragma unroll
+            for (uint32_t k = 0; k < R; ++k) {
+                v[k] = px[k * pstride];
+                u[k] = py[k * pstride];
+            }
+        }
+        dft<PI, 0, (int)R, has_tw ? 1 : 0>(v);
+        dft<PI, 0, (int)R, has_tw ? 1 : 0>(u);
+#pragma unroll
+        for (uint32_t k = 0; k < R; ++k) {
+            uint32_t o = v[outpos<(int)R>((int)k)], o2 = u[outpos<(int)R>((int)k)];
+            if (k > 0 && has_tw) {
+                const uint2 w = ldtw(tw + st.tw + (k - 1) * stride + j);
+                o = shoup<PI>(o, w.x, w.y);
+                o2 = shoup<PI>(o2, w.x, w.y);
+            }
+            px[k * pstride] = o;
+            py[k * pstride] = o2;
+        }
+    }
+}
+
 template <int PI, uint32_t R, uint32_t M, uint32_t N>
 __device__ __forceinline__ void inv_stage_ct(const Stage &st, const uint2 *tw, uint32_t *sb,
                                              uint32_t *gout, uint32_t rows) {
@@ -135,15 +181,21 @@ __device__ __forceinline__ void inv_stage_ct(const Stage &st, const uint2 *tw, u
 }
 
 // forward stages 0 .. NS-2, then the center, then inverse stages NS-2 .. 0
-template <int PI, uint32_t N, int T>
+template <int PI, uint32_t N, int T, bool SQR>
 __device__ __forceinline__ void fwd_stages_ct(const PlanDev &pd, const uint2 *tw, uint32_t *sx,
                                               uint32_t *sy, const uint32_t *gx, const uint32_t *gy,
-                                              uint32_t nops, uint32_t rows) {
+                                              uint32_t rows) {
     using S = Pow2Sched<N>;
     if constexpr (T < S::NS - 1) {
-        fwd_stage_ct<PI, S::radix(T), S::span(T), N>(pd.rs[T], tw, sx, sy, gx, gy, T == 0, nops, rows);
+#ifndef DMUL_ROW_UNPAIRED
+        if constexpr (!SQR)
+            fwd_stage_pair<PI, S::radix(T), S::span(T), N>(pd.rs[T], tw, sx, sy, gx, gy, T == 0, rows);
+        else
+#endif
+            fwd_stage_ct<PI, S::radix(T), S::span(T), N>(pd.rs[T], tw, sx, sy, gx, gy, T == 0, SQR ? 1u : 2u,
+                                                          rows);
         __syncthreads();
-        fwd_stages_ct<PI, N, T + 1>(pd, tw, sx, sy, gx, gy, nops, rows);
+        fwd_stages_ct<PI, N, T + 1, SQR>(pd, tw, sx, sy, gx, gy, rows);
     }
 }
 
@@ -191,7 +243,7 @@ __device__ __forceinline__ void row_core_ct(const PlanDev &pd, uint32_t *sx, uin
                                             uint32_t *__restrict__ xout, uint32_t rows = 1) {
     using S = Pow2Sched<N>;
     const uint2 *tw = pd.tw[PI];
-    fwd_stages_ct<PI, N, 0>(pd, tw, sx, sy, xin, yin, SQR ? 1u : 2u, rows);
+    fwd_stages_ct<PI, N, 0, SQR>(pd, tw, sx, sy, xin, yin, rows);
     static_assert(S::radix(S::NS - 1) == 16, "the center stage is radix 16");
     row_center_ct<PI, SQR>(sx, sy, rows * (N / 16));
     __syncthreads();
@@ -349,8 +401,135 @@ static cudaError_t launch_ct_b(const PlanDev &pd, const JobDev *jobs, int njobs,
 }
 
 
+// ---- step 2 of the six-step form (Sec. 7.2) and its inverse, specialized the same way --------------
+// The length-N DFTs (the column schedule, pd.cs) along the contiguous rows of the N2 x N matrix,
+// with the four-step twiddle xi_N^(k1 n2) = Q[k][n2] A[b][n2] on the last forward stage's outputs
+// (the inverse: the scaled inverse tables on the first stage's inputs).  n2 is the CTA's row, so
+// the R - 1 factors Q[k][n2] are shared by the CTA.  Same tables, stage order and output order as
+// the generic k_rowdft6 (sixstep.cu); the inverse ends reduced to [0, p) for the natural CRT.
+template <int PI, uint32_t N, int T>
+__device__ __forceinline__ void fwd6_stages(const Stage *cs, const uint2 *tw, uint32_t *sb, const uint32_t *g) {
+    using S = Pow2Sched<N>;
+    if constexpr (T < S::NS - 1) {
+        fwd_stage_ct<PI, S::radix(T), S::span(T), N>(cs[T], tw, sb, nullptr, g, nullptr, T == 0, 1u, 1u);
+        __syncthreads();
+        fwd6_stages<PI, N, T + 1>(cs, tw, sb, g);
+    }
+}
+
+template <int PI, uint32_t N, int T>
+__device__ __forceinline__ void inv6_stages(const Stage *cs, const uint2 *tw, uint32_t *sb) {
+    if constexpr (T >= 0) {
+        using S = Pow2Sched<N>;
+        inv_stage_ct<PI, S::radix(T), S::span(T), N>(cs[T], tw, sb, nullptr, 1u);
+        __syncthreads();
+        inv6_stages<PI, N, T - 1>(cs, tw, sb);
+    }
+}
+
+template <int PI, uint32_t N, bool INV>
+__device__ __forceinline__ void rowdft6_body(const PlanDev &pd, uint32_t *sb, uint2 *qs, uint32_t *row, uint32_t n2) {
+    using S = Pow2Sched<N>;
+    static_assert(S::radix(S::NS - 1) == 16, "the last stage is radix 16");
+    constexpr uint32_t nb = N / 16;
+    const uint2 *tw = pd.tw[PI];
+    const uint2 *A = tw + (INV ? pd.offAi : pd.offA);
+    if (threadIdx.x >= 1 && threadIdx.x < 16)
+        qs[threadIdx.x] = ldtw(tw + (INV ? pd.offQi : pd.offQ) + (uint64_t)threadIdx.x * pd.N2 + n2);
+    if (!INV) {
+        fwd6_stages<PI, N, 0>(pd.cs, tw, sb, row);  // ends with a barrier (qs visible too)
+        for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
+            uint32_t v[16];
+            const uint32_t *s = sb + 17 * b;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) v[u] = s[u];
+            dft<PI, 0, 16, 2>(v);  // every output goes straight into the twiddle products
+            const uint2 a = ldtw(A + (uint64_t)b * pd.N2 + n2);
+            uint32_t o[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                uint32_t x = v[outpos<16>(k)];
+                if (k > 0) x = shoup<PI>(x, qs[k].x, qs[k].y);
+                o[k] = shoup<PI>(x, a.x, a.y);
+            }
+            uint4 *dst = (uint4 *)(row + 16 * b);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dst[i] = make_uint4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+        }
+    } else {
+        __syncthreads();  // qs
+        for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
+            const uint2 a = ldtw(A + (uint64_t)b * pd.N2 + n2);
+            const uint4 *src = (const uint4 *)(row + 16 * b);
+            uint32_t v[16];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint4 t = src[i];
+                v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                uint32_t x = v[k];
+                if (k > 0) x = shoup<PI>(x, qs[k].x, qs[k].y);
+                v[k] = shoup<PI>(x, a.x, a.y);
+            }
+            dft<PI, 1, 16, 2>(v);  // the next inverse stage reduces / untwiddles its inputs
+            uint32_t *s = sb + 17 * b;
+#pragma unroll
+            for (int u = 0; u < 16; ++u) s[u] = v[outpos<16>(u)];
+        }
+        __syncthreads();
+        inv6_stages<PI, N, S::NS - 2>(pd.cs, tw, sb);
+        for (uint32_t i = threadIdx.x; i < N / 4; i += blockDim.x) {
+            uint32_t o[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) o[t] = red1p<PI>(red2p<PI>(sb[pidx(4 * i + t)]));
+            ((uint4 *)row)[i] = make_uint4(o[0], o[1], o[2], o[3]);
+        }
+    }
+}
+
+template <uint32_t N, bool INV>
+__global__ void __launch_bounds__(256) k_rowdft6_ct(const PlanDev pd, uint32_t *A) {
+    extern __shared__ uint32_t sm[];
+    __shared__ uint2 qs[16];
+    const uint32_t n2 = blockIdx.x;
+    const int pi = blockIdx.y;
+    uint32_t *row = A + (uint64_t)pi * pd.N + (uint64_t)n2 * N;
+    DMUL_PRIME_SWITCH(pi, (rowdft6_body<PI, N, INV>(pd, sm, qs, row, n2)));
+}
+
+template <uint32_t N>
+static bool cols_schedule_matches(const PlanDev &pd) {
+    using S = Pow2Sched<N>;
+    if (pd.N1 != N || pd.ncs != S::NS) return false;
+    for (int t = 0; t < S::NS; ++t)
+        if (pd.cs[t].R != S::radix(t) || pd.cs[t].m != S::span(t)) return false;
+    return true;
+}
+
+template <uint32_t N>
+static cudaError_t launch_dft6(const PlanDev &pd, uint32_t *A, bool inv, cudaStream_t s) {
+    const unsigned threads = N / 16 < 64 ? 64u : (N / 16 > 256 ? 256u : N / 16);
+    const size_t smem = (size_t)RowPad<N>::NP * 4;
+    dim3 grid(pd.N2, kPrimes);
+    if (inv) k_rowdft6_ct<N, true><<<grid, threads, smem, s>>>(pd, A);
+    else k_rowdft6_ct<N, false><<<grid, threads, smem, s>>>(pd, A);
+    return cudaGetLastError();
+}
+
 template <uint32_t... Ns>
 struct RowSet {
+    static bool dft6_matches(const PlanDev &pd) {
+        bool r = false;
+        (void)((pd.N1 == Ns && (r = cols_schedule_matches<Ns>(pd), true)) || ...);
+        return r;
+    }
+    static cudaError_t dft6(const PlanDev &pd, uint32_t *A, bool inv, cudaStream_t s) {
+        cudaError_t r = cudaErrorInvalidValue;
+        (void)((pd.N1 == Ns && (r = launch_dft6<Ns>(pd, A, inv, s), true)) || ...);
+        return r;
+    }
     static bool matches(const PlanDev &pd) {
         bool r = false;
         (void)((pd.N2 == Ns && (r = schedule_matches<Ns>(pd), true)) || ...);
@@ -387,6 +566,10 @@ struct RowSet {
                                      bool rows) {                                                      \
         return RowSet_##TAG::run_b(pd, jobs, njobs, s, rows);                                          \
     }                                                                                                  \
-    cudaError_t rowpass_##TAG##_attrs() { return RowSet_##TAG::attrs(); }
+    cudaError_t rowpass_##TAG##_attrs() { return RowSet_##TAG::attrs(); }                            \
+    bool rowpass_##TAG##_dft6_matches(const PlanDev &pd) { return RowSet_##TAG::dft6_matches(pd); }   \
+    cudaError_t rowpass_##TAG##_dft6(const PlanDev &pd, uint32_t *A, bool inv, cudaStream_t s) {      \
+        return RowSet_##TAG::dft6(pd, A, inv, s);                                                      \
+    }
 
 }  // namespace dml

@@ -555,14 +555,14 @@ int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
         }
         {
             Timed t(c, kStRowDft, s);
-            CK(launch_rowdft_fwd_tw(pd, A, s));
+            CK(rowdft6_specialized(pd) ? launch_rowdft6_ct(pd, A, false, s) : launch_rowdft_fwd_tw(pd, A, s));
         }
         Timed t(c, kStTranspose, s);
         CK(launch_transpose(A, pd.N2, pd.N1, kPrimes, N, s, c->status));
     }
     {
         Timed t(c, kStRowMul, s);
-        CK(launch_row_mul(pd, c->X, c->Y, square, s, c->status));
+        CK(launch_row_any(pd, c->X, c->Y, square, c->status, s));
     }
     {
         Timed t(c, kStTranspose, s);
@@ -570,7 +570,7 @@ int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
     }
     {
         Timed t(c, kStRowDft, s);
-        CK(launch_rowdft_inv_tw(pd, c->X, s));
+        CK(rowdft6_specialized(pd) ? launch_rowdft6_ct(pd, c->X, true, s) : launch_rowdft_inv_tw(pd, c->X, s));
     }
     Timed t(c, kStTranspose, s);
     CK(launch_transpose(c->X, pd.N2, pd.N1, kPrimes, N, s, c->status));

@@ -177,6 +177,9 @@ cudaError_t launch_pack(const uint32_t *x, uint64_t nx, uint64_t N, uint32_t *X,
 cudaError_t launch_transpose(uint32_t *a, uint64_t rows, uint64_t cols, uint64_t batch,
                              uint64_t batch_stride, cudaStream_t s, uint32_t *status = nullptr);
 cudaError_t launch_rowdft_fwd_tw(const PlanDev &pd, uint32_t *A, cudaStream_t s);
+// The same two steps specialized on N1 in {256, ..., 8192} with the planner's schedule (rowpass.cuh).
+bool rowdft6_specialized(const PlanDev &pd);
+cudaError_t launch_rowdft6_ct(const PlanDev &pd, uint32_t *A, bool inv, cudaStream_t s);
 cudaError_t launch_rowdft_inv_tw(const PlanDev &pd, uint32_t *A, cudaStream_t s);
 cudaError_t launch_crt_natural(const uint32_t *X, uint64_t N, uint64_t L, InvMode mode,
                                uint32_t *out, uint2 *spill, cudaStream_t s);

@@ -14,7 +14,9 @@ namespace dml {
                                    uint32_t *status, cudaStream_t s);                                  \
     cudaError_t rowpass_##TAG##_run_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s, \
                                      bool rows);                                                       \
-    cudaError_t rowpass_##TAG##_attrs();
+    cudaError_t rowpass_##TAG##_attrs();                                                             \
+    bool rowpass_##TAG##_dft6_matches(const PlanDev &pd);                                              \
+    cudaError_t rowpass_##TAG##_dft6(const PlanDev &pd, uint32_t *A, bool inv, cudaStream_t s);
 DMUL_ROWPASS_DECL(big)
 DMUL_ROWPASS_DECL(small)
 
@@ -32,6 +34,14 @@ cudaError_t launch_row_pass_ct(const PlanDev &pd, uint32_t *X, const uint32_t *Y
 
 cudaError_t launch_row_pass_ct_b(const PlanDev &pd, const JobDev *jobs, int njobs, cudaStream_t s, bool rows) {
     return is_big(pd.N2) ? rowpass_big_run_b(pd, jobs, njobs, s, rows) : rowpass_small_run_b(pd, jobs, njobs, s, rows);
+}
+
+bool rowdft6_specialized(const PlanDev &pd) {
+    return is_big(pd.N1) ? rowpass_big_dft6_matches(pd) : rowpass_small_dft6_matches(pd);
+}
+
+cudaError_t launch_rowdft6_ct(const PlanDev &pd, uint32_t *A, bool inv, cudaStream_t s) {
+    return is_big(pd.N1) ? rowpass_big_dft6(pd, A, inv, s) : rowpass_small_dft6(pd, A, inv, s);
 }
 
 cudaError_t init_kernel_attributes_rowpass() {

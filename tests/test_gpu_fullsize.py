@@ -97,3 +97,16 @@ def test_c3_shapes(d, ctx, which):
     for k in ks:
         got = int(dg[k, 0]) + int(dg[k, 1]) * B + int(dg[k, 2]) * B * B
         assert got == oracle.conv_at(x, y, k), k
+
+
+@pytest.mark.parametrize("which", ["c2", "c3a"])
+def test_sixstep_full_size(d, which):
+    """The six-step form at the full sizes (N = 2^22 with square in-place transposes, N = 2^23 with
+    the n x 2n and 2n x n ones), every limb against the oracle's slow NTT route."""
+    x, y = wl.c2_random_pair() if which == "c2" else wl.c3_pairs()[0]
+    with d.Context(0, flags=d.DMUL_FLAG_SIXSTEP) as c6:
+        info = d.dmul_get_plan(c6.handle, len(x) + len(y))
+        assert info.sixstep == 1 and info.N == (1 << 22 if which == "c2" else 1 << 23)
+        z, nz = _mul(d, c6, x, y)
+    ref = oracle.mul_ntt(x, y)
+    assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))

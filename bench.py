@@ -402,6 +402,15 @@ def run_ours(args, rank, world, local):
         "clocks": clk,
     }
     if rank == 0 and not args.no_forms:
+        # the prime width chosen by measurement (Sec. 4.2's two 64-bit primes against the three
+        # 30-bit primes): the same fused row pass over this product's transform length
+        ms64, ms32 = d.dmul_probe_prime_width(ctx.handle, int(info.N))
+        out["prime_width_probe"] = {
+            "N": int(info.N), "row_pass_ms_two_62bit_primes": ms64, "row_pass_ms_three_30bit_primes": ms32,
+            "ratio": ms64 / ms32,
+            "what": "fused row pass (forward row DFTs of x and y, pointwise Montgomery, inverse) on resident "
+                    "operands, rows of 4096; 64-bit words with Shoup and R = 2^64 Montgomery for the two "
+                    "primes c 3 2^n + 1 < 2^62, the library's specialized pass for the three primes < 2^30"}
         out["other_configs"] = run_other_configs(d, torch, dev, flush, stream)
         out["batched"] = run_batched(d, torch, dev, check=not args.no_cpu_baseline)
         out["served"] = run_served(d, torch, dev, check=not args.no_cpu_baseline)
@@ -450,6 +459,29 @@ def time_product(d, torch, dev, ctx, x_np, y_np, reps, flush, stream, square=Fal
     return float(np.median(ts))
 
 
+def stage_ms(d, torch, dev, ctx, x_np, y_np, flush, stream, reps=20) -> dict:
+    """Per-stage device times (ms, mean of reps) of one product, events between the stages."""
+    x, y = d.to_device(x_np, dev), d.to_device(y_np, dev)
+    L = len(x_np) + len(y_np)
+    z = torch.empty(L, dtype=torch.int32, device=dev)
+    nz = torch.zeros(1, dtype=torch.int64, device=dev)
+    sp = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            d.dmul_mul(ctx.handle, x, len(x_np), y, len(y_np), z, L, nz, sp)
+        torch.cuda.synchronize()
+        ctx.stage_times()
+        ctx.stage_timing(True)
+        for _ in range(reps):
+            flush.zero_()
+            d.dmul_mul(ctx.handle, x, len(x_np), y, len(y_np), z, L, nz, sp)
+        torch.cuda.synchronize()
+        st = ctx.stage_times()
+        ctx.stage_timing(False)
+    assert d.dmul_sync(ctx.handle, sp) == 0
+    return {k: round(v[0] / reps, 5) for k, v in st.items()}
+
+
 def run_other_configs(d, torch, dev, flush, stream) -> dict:
     """The other workload configurations, one product each (median of several runs)."""
     import numpy as np
@@ -475,6 +507,19 @@ def run_other_configs(d, torch, dev, flush, stream) -> dict:
         ms = time_product(d, torch, dev, ctx, a5, b5, 10, flush, stream)
         out["len5_19M_x_19M"] = {"ms": ms, "digits_per_s": 38_000_000 / (ms * 1e-3),
                                  "N": int(d.dmul_get_plan(ctx.handle, len(a5) + len(b5)).N)}
+        # An internal base of 10^18 (two I/O limbs per coefficient, Sec. 4.2-4.3) halves the transform
+        # length but needs five primes below 2^30 (B^2 min(n, m) ~ 2^140 for 2^24 digits).  Its
+        # transform stages are the same per-prime kernels at N / 2: time them on a product of half
+        # the limbs (2^23 digits per operand, N = 2^21) and scale the three primes to five.
+        xs, ys = wl.c2_random_pair(DIGITS // 2)
+        full = stage_ms(d, torch, dev, ctx, *wl.c2_random_pair(), flush, stream)
+        half = stage_ms(d, torch, dev, ctx, xs, ys, flush, stream)
+        tf = lambda st: st.get("col_fwd", 0) + st.get("row_mul", 0) + st.get("col_inv_crt", 0)
+        out["base_1e18_estimate"] = {
+            "transform_ms_base_1e9_3_primes_N": tf(full), "transform_ms_3_primes_half_N": tf(half),
+            "transform_ms_base_1e18_5_primes_half_N": tf(half) * 5 / 3,
+            "stages_full": full, "stages_half": half,
+            "note": "col_inv_crt includes the CRT; a five-prime CRT would cost more per coefficient"}
     with d.Context(dev.index or 0, flags=d.DMUL_FLAG_NO_RADIX5) as ctx23:
         ms = time_product(d, torch, dev, ctx23, a5, b5, 10, flush, stream)
         out["len5_19M_x_19M_without_5x2k"] = {

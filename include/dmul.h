@@ -316,6 +316,26 @@ int dmul_stage_timing(dmul_ctx *ctx, int on);
  * modular arithmetic) on every SM and returns the achieved rate in operations per second. */
 int dmul_probe_imad(dmul_ctx *ctx, double *imad_per_s);
 
+/* Prime-width probe (the choice of Sec. 4.2 made by measurement on the GPU): the fused row pass
+ * of the four-step form (forward row DFTs of X and Y, pointwise Montgomery product, inverse row
+ * DFTs; Sec. 5.4, 6, 7.1) over N residues, once with the paper's two-prime design in 64-bit words
+ * (two primes c 3 2^n + 1 < 2^62 from FindPrimes(63, 23, 2), Shoup products by constants,
+ * Montgomery with R = 2^64, rows of 4096) and once as the library runs it (three primes < 2^30,
+ * 32-bit words, the plan the context has for length N).  Both on resident operands; the median
+ * device times of ten runs each, in ms.  N: a multiple of 4096, at most 2^23.  Allocates about
+ * 32 N bytes beyond the context's plain-form scratch. */
+int dmul_probe_prime_width(dmul_ctx *ctx, uint64_t N, double *ms_two_62bit, double *ms_three_30bit);
+
+/* The two-prime probe's primes, ascending (host-only). */
+int dmul_probe64_primes(uint64_t out[2]);
+
+/* Parity hook of that probe: for each prime i (of dmul_probe64_primes) and row r < rows, the
+ * cyclic convolution of length 4096 of a[i][r][.] and b[i][r][.] modulo p_i (the convolution
+ * theorem, Sec. 3.3), reduced to [0, p_i), into out[i][r][.].  a, b, out: device arrays of
+ * 2 x rows x 4096 uint64 residues (< p_i for a and b); rows <= 65535.  Synchronous on `stream`. */
+int dmul_probe64_conv(dmul_ctx *ctx, const uint64_t *a, const uint64_t *b, uint64_t *out, size_t rows,
+                      void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -134,6 +134,8 @@ int dev_alloc(dmul_ctx *c, void **p, size_t bytes);
 void dev_free(dmul_ctx *c, void *p, size_t bytes);
 int get_plan(dmul_ctx *c, uint64_t N, PlanEntry **out);
 int get_small_plan(dmul_ctx *c, uint64_t N, SmallPlanEntry **out);
+// The plain form's residue buffers (3 N words each), spills and carry control block for L limbs.
+int ensure_scratch(dmul_ctx *c, uint64_t N, uint64_t L, bool need_y);
 bool overlaps(const void *a, size_t abytes, const void *b, size_t bbytes);
 uint64_t max_min_limbs();
 

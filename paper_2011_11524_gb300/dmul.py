@@ -45,7 +45,8 @@ EXPORTS = [
     "dmul_mul_host", "dmul_batch", "dmul_submit", "dmul_poll", "dmul_wait", "dmul_conv_residues",
     "dmul_conv_coeffs", "dmul_carry", "dmul_transpose", "dmul_get_plan", "dmul_primes",
     "dmul_lambda", "dmul_max_min_limbs", "dmul_stage_times", "dmul_stage_timing", "dmul_probe_imad",
-    "dmul_carry_noalloc", "dmul_host_direct", "dmul_serve_stats",
+    "dmul_carry_noalloc", "dmul_host_direct", "dmul_serve_stats", "dmul_probe_prime_width",
+    "dmul_probe64_primes", "dmul_probe64_conv",
 ]
 
 
@@ -120,6 +121,9 @@ def load() -> ctypes.CDLL:
                               ctypes.POINTER(u64), ctypes.POINTER(i32)], i32),
         "dmul_stage_timing": ([vp, i32], i32),
         "dmul_probe_imad": ([vp, ctypes.POINTER(ctypes.c_double)], i32),
+        "dmul_probe_prime_width": ([vp, u64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], i32),
+        "dmul_probe64_primes": ([ctypes.POINTER(u64)], i32),
+        "dmul_probe64_conv": ([vp, vp, vp, vp, sz, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -309,6 +313,27 @@ def dmul_probe_imad(ctx) -> float:
     if rc:
         raise DmulError(rc, "dmul_probe_imad")
     return v.value
+
+
+def dmul_probe_prime_width(ctx, N: int) -> tuple[float, float]:
+    """(ms of the two-prime 62-bit row pass, ms of the library's three-prime row pass) over N."""
+    a, b = ctypes.c_double(0), ctypes.c_double(0)
+    rc = load().dmul_probe_prime_width(ctx, N, ctypes.byref(a), ctypes.byref(b))
+    if rc:
+        raise DmulError(rc, "dmul_probe_prime_width")
+    return a.value, b.value
+
+
+def dmul_probe64_primes() -> list[int]:
+    out = (ctypes.c_uint64 * 2)()
+    rc = load().dmul_probe64_primes(out)
+    if rc:
+        raise DmulError(rc, "dmul_probe64_primes")
+    return [int(v) for v in out]
+
+
+def dmul_probe64_conv(ctx, a, b, out, rows, stream=None) -> int:
+    return load().dmul_probe64_conv(ctx, _ptr(a), _ptr(b), _ptr(out), rows, _stream(stream))
 
 
 # ---------------------------------------------------------------------------------------------

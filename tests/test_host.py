@@ -172,3 +172,9 @@ def test_rho_c_then_block_transposes_is_the_transpose(n, C):
         for k in range(C):
             R[:, C * i + k] = Q[:, k * n + i]
     assert np.array_equal(R, M)
+
+
+def test_probe64_primes_are_findprimes_63():
+    """The prime-width probe's two 62-bit primes are FindPrimes(63, 23, 2) of Sec. 4.5, as the
+    oracle's independent implementation finds them."""
+    assert d.dmul_probe64_primes() == sorted(oracle.find_primes(63, 23, 2))

@@ -134,10 +134,10 @@ def _transform_mults(n: int, radices: list[int]) -> float:
 # summarized under profiles/).  Keyed by (stage, N, N1, N2, half-width column tiles); a stage whose
 # kernel changes after the capture must be dropped from this table until it is captured again.
 NCU_TRAFFIC = {
-    ("col_fwd", 4194304, 1024, 4096, 1): 23.665920e6 + 46.631936e6,
-    ("row_mul", 4194304, 1024, 4096, 1): 100.954624e6 + 8.025856e6,
-    ("col_inv_crt", 4194304, 1024, 4096, 1): 58.211584e6 + 0.839936e6,
-    ("carry_scan", 4194304, 1024, 4096, 1): 15.895040e6 + 0.000000e6,
+    ("col_fwd", 4194304, 1024, 4096, 1): 23.667968e6 + 46.707456e6,
+    ("row_mul", 4194304, 1024, 4096, 1): 100.970240e6 + 7.634688e6,
+    ("col_inv_crt", 4194304, 1024, 4096, 1): 58.211584e6 + 1.039360e6,
+    ("carry_scan", 4194304, 1024, 4096, 1): 15.895808e6 + 0.000000e6,
 }
 
 

@@ -51,7 +51,7 @@ __device__ __forceinline__ void colf0_ct(const Stage &st, const uint2 *tw, uint3
 #pragma unroll
         for (uint32_t u = 0; u < R; ++u) {
             uint32_t a = sm[(j + u * stride) * 32 + lane];
-            bad |= (a >= kBase);
+            if (PI == 0) bad |= (a >= kBase);  // prime 0's CTAs report invalid limbs
             if (PI == 0) a = red2p<PI>(a);  // 10^9 < 4 p0: [0, 10^9) -> [0, 2 p0)
             v[u] = a;
         }
@@ -407,7 +407,7 @@ __device__ __forceinline__ void hcolf0(const Stage &st, const uint2 *tw, uint32_
         hload<PI, R, stride>(sm, b0, odd, v);
 #pragma unroll
         for (uint32_t u = 0; u < R; ++u) {
-            bad |= (v[u] >= kBase);
+            if (PI == 0) bad |= (v[u] >= kBase);  // prime 0's CTAs report invalid limbs
             if (PI == 0) v[u] = red2p<PI>(v[u]);  // 10^9 < 4 p0: [0, 10^9) -> [0, 2 p0)
         }
         dft<PI, 0, (int)R, 1>(v);

@@ -73,7 +73,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         done = dict(zip(order, ex.map(compile_one, order)))
     objs = [done[f] for f in srcs]
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
+    # every symbol must resolve at link time (a missing definition fails the build, not the load)
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread", "-Xlinker", "--no-undefined"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -40,7 +40,7 @@ static int cuda_fail(cudaError_t e) {
     } while (0)
 
 static const char *kStageNames[kNumStages] = {"col_fwd", "row_mul", "col_inv_crt", "carry_scan",
-                                              "transpose", "row_dft", "crt_natural", "pack",
+                                              "transpose", "row_dft", "crt", "pack_transpose",
                                               "small_mul", "batch"};
 
 Timed::Timed(dmul_ctx *c_, int id_, cudaStream_t s_) : c(c_), id(id_), s(s_) {
@@ -478,7 +478,7 @@ int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, si
     const bool six = (c->cfg.flags & DMUL_FLAG_SIXSTEP) != 0;
     if (six) {
         Timed t(c, kStCrt, s);
-        CK(launch_crt_natural(c->X, N, L, mode, mode == kInvDigits ? z : mode_out, c->spill, s));
+        CK(launch_crt_transposed(c->X, pe->pd.N1, pe->pd.N2, L, mode, mode == kInvDigits ? z : mode_out, c->spill, s));
         if (mode == kInvDigits) CK(cudaMemsetAsync(c->ctl, 0, carry_ctl_bytes(L), s));
     } else {
         // the inverse pass also clears the carry scan's control block (no memset in between)
@@ -546,12 +546,9 @@ int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
     for (int op = 0; op < (square ? 1 : 2); ++op) {
         uint32_t *A = op ? c->Y : c->X;
         {
+            // packing and step 1 in one out-of-place pass: limbs -> the primes' N2 x N1 transposes
             Timed t(c, kStPack, s);
-            CK(launch_pack(op ? y : x, op ? ny : nx, N, A, c->status, s));
-        }
-        {
-            Timed t(c, kStTranspose, s);
-            CK(launch_transpose(A, pd.N1, pd.N2, kPrimes, N, s, c->status));
+            CK(launch_pack_transpose(op ? y : x, op ? ny : nx, pd.N1, pd.N2, A, c->status, s));
         }
         {
             Timed t(c, kStRowDft, s);
@@ -568,12 +565,9 @@ int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
         Timed t(c, kStTranspose, s);
         CK(launch_transpose(c->X, pd.N1, pd.N2, kPrimes, N, s, c->status));
     }
-    {
-        Timed t(c, kStRowDft, s);
-        CK(rowdft6_specialized(pd) ? launch_rowdft6_ct(pd, c->X, true, s) : launch_rowdft_inv_tw(pd, c->X, s));
-    }
-    Timed t(c, kStTranspose, s);
-    CK(launch_transpose(c->X, pd.N2, pd.N1, kPrimes, N, s, c->status));
+    Timed t(c, kStRowDft, s);
+    CK(rowdft6_specialized(pd) ? launch_rowdft6_ct(pd, c->X, true, s) : launch_rowdft_inv_tw(pd, c->X, s));
+    // the last transpose is fused into the CRT that follows (launch_crt_transposed)
     return DMUL_OK;
 }
 

@@ -170,8 +170,9 @@ cudaError_t launch_carry(uint32_t *z, const uint2 *spill, uint64_t L, CarryCtl *
                          uint32_t *status, cudaStream_t s, uint32_t *zo = nullptr, uint32_t spin = 0);
 
 // Six-step pieces (Sec. 7.2, 7.6).
-cudaError_t launch_pack(const uint32_t *x, uint64_t nx, uint64_t N, uint32_t *X, uint32_t *status,
-                        cudaStream_t s);
+// packing + the first transpose (limbs as N1 x N2 -> the three primes' N2 x N1 residues), out of place
+cudaError_t launch_pack_transpose(const uint32_t *x, uint64_t nx, uint32_t N1, uint32_t N2, uint32_t *X,
+                                  uint32_t *status, cudaStream_t s);
 // In place; 16-byte aligned matrices take the TMA-fed kernels (tensor-map tile loads of the I <= J
 // tile pairs, bulk-copied rows for rho).  status (may be null) receives an expired bounded wait.
 cudaError_t launch_transpose(uint32_t *a, uint64_t rows, uint64_t cols, uint64_t batch,
@@ -181,8 +182,9 @@ cudaError_t launch_rowdft_fwd_tw(const PlanDev &pd, uint32_t *A, cudaStream_t s)
 bool rowdft6_specialized(const PlanDev &pd);
 cudaError_t launch_rowdft6_ct(const PlanDev &pd, uint32_t *A, bool inv, cudaStream_t s);
 cudaError_t launch_rowdft_inv_tw(const PlanDev &pd, uint32_t *A, cudaStream_t s);
-cudaError_t launch_crt_natural(const uint32_t *X, uint64_t N, uint64_t L, InvMode mode,
-                               uint32_t *out, uint2 *spill, cudaStream_t s);
+// the last transpose + CRT: residues in N2 x N1 matrices ([n2][k1] = coefficient k1 N2 + n2)
+cudaError_t launch_crt_transposed(const uint32_t *X, uint32_t N1, uint32_t N2, uint64_t L, InvMode mode,
+                                  uint32_t *out, uint2 *spill, cudaStream_t s);
 
 // Batched forms (batch.cu).  small: one cluster of three CTAs per job does the whole product.
 cudaError_t launch_small_mul(const SmallPlanDev &sp, const JobDev *jobs, int njobs, uint32_t *status,

@@ -1,12 +1,14 @@
 // sixstep.cu -- the six-step form of the transform (Sec. 7.2) with the paper's in-place
-// transposes (Sec. 7.5-7.6), and the natural-layout CRT it ends with.
+// transposes (Sec. 7.5-7.6), and the CRT it ends with.
 //
-// Forward, for N = N1 * N2 = 2^k with N1 = 2^floor(k/2), N2 = 2^ceil(k/2) (Sec. 7.9): pack the limbs
-// as an N1 x N2 matrix, transpose it in place (step 1), run length-N1 DFTs on the contiguous rows
-// of the N2 x N1 result (step 2) and multiply by the four-step twiddle xi_N^(k1 n2) in the same
-// kernel (step 4), transpose back in place (step 3), then the row pass (step 5, fused with the
-// pointwise product and the first inverse step).  The final transpose of the forward transform and
-// the first one of the inverse are omitted (Sec. 7.4).  The DFTs of step 2 leave their outputs in
+// Forward, for N = N1 * N2 = 2^k with N1 = 2^floor(k/2), N2 = 2^ceil(k/2) (Sec. 7.9): the limbs seen
+// as an N1 x N2 matrix go straight into the primes' N2 x N1 transposes (packing and step 1 in one
+// out-of-place pass), length-N1 DFTs run on the contiguous rows of that result (step 2) with the
+// four-step twiddle xi_N^(k1 n2) in the same kernel (step 4), an in-place transpose brings it back
+// (step 3), then the row pass (step 5, fused with the pointwise product and the first inverse
+// step).  The inverse mirrors it; its last transpose is fused into the CRT, which reads the
+// transposed tiles.  The final transpose of the forward transform and the first one of the inverse
+// are omitted (Sec. 7.4).  The DFTs of step 2 leave their outputs in
 // the stage order (no bit reversal): the twiddle is indexed by the true frequency of each position,
 // and the inverse mirrors the order, so no reordering pass is needed.
 #include <cuda.h>
@@ -41,24 +43,6 @@ __device__ __forceinline__ uint32_t swz6(uint32_t a) {
     uint32_t r = a >> 5;
     uint32_t f = (r & 15u) | (((r >> 3) & 1u) << 4);
     return a ^ f;
-}
-
-// ---- packing: limbs -> residues [3][N], natural order, zero padded (Sec. 3.2) ------------------
-__global__ void k_pack(const uint32_t *__restrict__ x, uint64_t nx, uint64_t N, uint32_t *X,
-                       uint32_t *status) {
-    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    uint32_t a = i < nx ? x[i] : 0u;
-    if (a >= kBase) atomicOr(status, kStatusInvalid);
-    X[i] = red2p<0>(a);          // [0, 10^9) -> [0, 2 p0)
-    X[N + i] = a;                // 10^9 < 2 p1
-    X[2 * N + i] = a;            // 10^9 < 2 p2
-}
-
-cudaError_t launch_pack(const uint32_t *x, uint64_t nx, uint64_t N, uint32_t *X, uint32_t *status,
-                        cudaStream_t s) {
-    k_pack<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(x, nx, N, X, status);
-    return cudaGetLastError();
 }
 
 // ---- in-place transposes -------------------------------------------------------------------------
@@ -473,7 +457,7 @@ cudaError_t launch_rowdft_inv_tw(const PlanDev &pd, uint32_t *A, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// ---- CRT on natural-layout residues (the six-step form ends in natural order) -------------------
+// ---- Garner CRT (Sec. 8.2.2 extended to three primes) and the base-10^9 digits of one coefficient --
 __device__ __forceinline__ void crt_digits6(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t &d0,
                                             uint32_t &d1, uint32_t &d2) {
     const uint32_t p1 = c_prime[1].p, p2 = c_prime[2].p;
@@ -491,37 +475,93 @@ __device__ __forceinline__ void crt_digits6(uint32_t a0, uint32_t a1, uint32_t a
     d2 = (uint32_t)q1;
 }
 
-__global__ void __launch_bounds__(256) k_crt_natural(const uint32_t *__restrict__ X, uint64_t N,
-                                                     uint64_t L, int mode, uint32_t *__restrict__ out,
-                                                     uint2 *__restrict__ spill) {
-    const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t k0 = k & ~31ull;
-    if (k0 >= L) return;  // warp-uniform
-    const int lane = threadIdx.x & 31;
-    uint32_t a0 = 0, a1 = 0, a2 = 0;
-    if (k < L) { a0 = X[k]; a1 = X[N + k]; a2 = X[2 * N + k]; }
-    if (mode == kInvResidues) {
-        if (k < L) { out[k] = a0; out[L + k] = a1; out[2 * L + k] = a2; }
-        return;
+// ---- the first and the last data movement of the six-step form, fused with their neighbours ------
+// Packing + step 1: the limbs seen as the N1 x N2 matrix (zero past nx) go straight into the three
+// primes' N2 x N1 transposes, out of place (x is the caller's, X the scratch): one read of the limbs
+// and one write of the residues instead of a packing pass and an in-place transpose.  Any
+// N1 x N2 shape (also n x 2n: out of place no rho is needed).  CTA (J, I) moves the 32 x 32 tile of
+// rows 32 I.., columns 32 J.. through shared memory (one padding word per row).
+__global__ void __launch_bounds__(256) k_pack_transpose(const uint32_t *__restrict__ x, uint64_t nx, uint32_t N1,
+                                                        uint32_t N2, uint64_t N, uint32_t *__restrict__ X,
+                                                        uint32_t *status) {
+    __shared__ uint32_t t[32][33];
+    const uint32_t I = blockIdx.y, J = blockIdx.x;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    uint32_t bad = 0;
+    for (int r = ty; r < 32; r += 8) {
+        const uint64_t k = (uint64_t)(I * 32 + r) * N2 + J * 32 + tx;
+        const uint32_t a = k < nx ? x[k] : 0u;
+        bad |= a >= kBase;
+        t[r][tx] = a;
     }
-    uint32_t d0, d1, d2;
-    crt_digits6(a0, a1, a2, d0, d1, d2);
-    if (mode == kInvTriples) {
-        if (k < L) { out[3 * k] = d0; out[3 * k + 1] = d1; out[3 * k + 2] = d2; }
-        return;
+    if (__syncthreads_or((int)bad) && threadIdx.x == 0) atomicOr(status, kStatusInvalid);
+    for (int r = ty; r < 32; r += 8) {
+        const uint32_t a = t[tx][r];  // element (row 32 I + tx, column 32 J + r)
+        const uint64_t o = (uint64_t)(J * 32 + r) * N1 + I * 32 + tx;
+        X[o] = red2p<0>(a);  // [0, 10^9) -> [0, 2 p0)
+        X[N + o] = a;        // 10^9 < 2 p1
+        X[2 * N + o] = a;    // 10^9 < 2 p2
     }
-    uint32_t d1p = __shfl_up_sync(0xffffffffu, d1, 1);
-    uint32_t d2p = __shfl_up_sync(0xffffffffu, d2, 2);
-    if (lane < 1) d1p = 0;
-    if (lane < 2) d2p = 0;
-    uint32_t d2_30 = __shfl_sync(0xffffffffu, d2, 30);
-    if (k < L) out[k] = d0 + d1p + d2p;
-    if (lane == 31) spill[k0 >> 5] = make_uint2(d1 + d2_30, d2);
 }
 
-cudaError_t launch_crt_natural(const uint32_t *X, uint64_t N, uint64_t L, InvMode mode,
-                               uint32_t *out, uint2 *spill, cudaStream_t s) {
-    k_crt_natural<<<(unsigned)((L + 255) / 256), 256, 0, s>>>(X, N, L, (int)mode, out, spill);
+cudaError_t launch_pack_transpose(const uint32_t *x, uint64_t nx, uint32_t N1, uint32_t N2, uint32_t *X,
+                                  uint32_t *status, cudaStream_t s) {
+    if (N1 % 32 || N2 % 32) return cudaErrorInvalidValue;
+    k_pack_transpose<<<dim3(N2 / 32, N1 / 32), 256, 0, s>>>(x, nx, N1, N2, (uint64_t)N1 * N2, X, status);
+    return cudaGetLastError();
+}
+
+// Step 1 of the inverse (the last transpose) + CRT: the residues of the three primes sit in N2 x N1
+// matrices, coefficient k = k1 N2 + n2 at [n2][k1].  CTA (I, J) brings the 32 x 32 tile of rows
+// 32 J.. (n2), columns 32 I.. (k1) of each prime into shared memory; warp row k1 then covers the 32
+// consecutive coefficients k1 N2 + 32 J .. + 31: one chunk of the digit sums.
+__global__ void __launch_bounds__(256) k_crt_transposed(const uint32_t *__restrict__ X, uint32_t N1, uint32_t N2,
+                                                        uint64_t N, uint64_t L, int mode,
+                                                        uint32_t *__restrict__ out, uint2 *__restrict__ spill) {
+    __shared__ uint32_t t[3][32][33];
+    const uint32_t I = blockIdx.x, J = blockIdx.y;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const uint64_t first = (uint64_t)(I * 32) * N2 + J * 32;  // the tile's smallest coefficient
+    if (first >= L) return;  // uniform over the CTA
+    for (int r = ty; r < 32; r += 8) {
+        const uint64_t o = (uint64_t)(J * 32 + r) * N1 + I * 32 + tx;
+        t[0][r][tx] = X[o];
+        t[1][r][tx] = X[N + o];
+        t[2][r][tx] = X[2 * N + o];
+    }
+    __syncthreads();
+    const int lane = tx;
+    for (int r = ty; r < 32; r += 8) {  // k1 = 32 I + r, n2 = 32 J + lane
+        const uint64_t k0 = (uint64_t)(I * 32 + r) * N2 + J * 32;
+        if (k0 >= L) continue;  // warp-uniform
+        const uint64_t k = k0 + lane;
+        const bool in = k < L;
+        const uint32_t a0 = in ? t[0][lane][r] : 0u, a1 = in ? t[1][lane][r] : 0u, a2 = in ? t[2][lane][r] : 0u;
+        if (mode == kInvResidues) {
+            if (in) { out[k] = a0; out[L + k] = a1; out[2 * L + k] = a2; }
+            continue;
+        }
+        uint32_t d0, d1, d2;
+        crt_digits6(a0, a1, a2, d0, d1, d2);
+        if (mode == kInvTriples) {
+            if (in) { out[3 * k] = d0; out[3 * k + 1] = d1; out[3 * k + 2] = d2; }
+            continue;
+        }
+        // digit sums within the chunk; the two digits past it go to the chunk's spill
+        uint32_t d1p = __shfl_up_sync(0xffffffffu, d1, 1);
+        uint32_t d2p = __shfl_up_sync(0xffffffffu, d2, 2);
+        if (lane < 1) d1p = 0;
+        if (lane < 2) d2p = 0;
+        const uint32_t d2_30 = __shfl_sync(0xffffffffu, d2, 30);
+        if (in) out[k] = d0 + d1p + d2p;
+        if (lane == 31) spill[k0 >> 5] = make_uint2(d1 + d2_30, d2);
+    }
+}
+
+cudaError_t launch_crt_transposed(const uint32_t *X, uint32_t N1, uint32_t N2, uint64_t L, InvMode mode,
+                                  uint32_t *out, uint2 *spill, cudaStream_t s) {
+    if (N1 % 32 || N2 % 32) return cudaErrorInvalidValue;
+    k_crt_transposed<<<dim3(N1 / 32, N2 / 32), 256, 0, s>>>(X, N1, N2, (uint64_t)N1 * N2, L, (int)mode, out, spill);
     return cudaGetLastError();
 }
 

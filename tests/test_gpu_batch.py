@@ -289,3 +289,32 @@ def test_few_short_jobs_take_the_measured_path(d):
                 rc, t = d.dmul_submit(srv.handle, arr[i])
                 assert rc == 0 and d.dmul_wait(srv.handle, t) == 0
             _check(d, jobs, dev)
+
+
+def test_batch_status_edge_cases(d, ctx):
+    """An empty batch, a batch of only rejected jobs, and the pending state before the sync."""
+    arr = d.make_jobs([])
+    assert d.dmul_batch(ctx.handle, arr, 0) == d.DMUL_OK
+    assert d.dmul_sync(ctx.handle) == d.DMUL_OK
+    jobs = wl.c4_jobs(2, 2.0, 3.0, 0.0, seed=47)
+    dev = _prep(d, jobs)
+    bad = [(tx, 0, ty, ny, z, L, nz) for (tx, nx, ty, ny, z, L, nz) in dev]  # nx = 0
+    arr = d.make_jobs(bad)
+    assert d.dmul_batch(ctx.handle, arr, 2) == d.DMUL_OK
+    assert d.job_statuses(arr, 2) == [d.DMUL_ERR_INVALID] * 2
+    assert d.dmul_sync(ctx.handle) == d.DMUL_OK
+    # a good batch reads PENDING until the next sync fills in its statuses
+    arr = d.make_jobs(dev)
+    assert d.dmul_batch(ctx.handle, arr, 2) == d.DMUL_OK
+    assert d.job_statuses(arr, 2) == [d.DMUL_PENDING] * 2
+    assert d.dmul_sync(ctx.handle) == d.DMUL_OK
+    assert d.job_statuses(arr, 2) == [d.DMUL_OK] * 2
+    _check(d, jobs, dev)
+
+
+def test_serve_stats_before_any_request(d):
+    with d.Context(0) as c:
+        st = d.dmul_serve_stats(c.handle)
+        assert all(v == 0 for v in st.values())
+        assert d.dmul_wait(c.handle, 1) == d.DMUL_ERR_UNKNOWN_TICKET
+        assert d.dmul_poll(c.handle, 1)[0] == d.DMUL_ERR_UNKNOWN_TICKET

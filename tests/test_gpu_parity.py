@@ -465,6 +465,23 @@ def test_sixstep_mul(d, ctx6, n, m):
     assert np.array_equal(z, oracle.mul(x, x))
 
 
+@pytest.mark.parametrize("n,m", [(1, 1), (700, 333), (3000, 5000), (40000, 25536)])
+def test_sixstep_residues_and_coeffs(d, ctx6, n, m):
+    """The six-step form's CRT reads the inverse's transposed tiles: the residues c_k mod p_i and
+    the exact coefficients it recovers, against the oracle's schoolbook column sums."""
+    rng = _rng(8100 + n)
+    x, y = _rand(rng, n), _rand(rng, m)
+    c = oracle.conv_schoolbook_words(x, y)
+    L = n + m
+    tx, ty = d.to_device(x), d.to_device(y)
+    r = d.to_host(ctx6.conv_residues(tx, ty)).reshape(3, L)
+    for i, p in enumerate(d.dmul_primes()):
+        assert np.array_equal(r[i], oracle.residues(c, p).astype(np.uint32)), i
+    dg = d.to_host(ctx6.conv_coeffs(tx, ty)).reshape(L, 3).astype(object)
+    got = [int(a) + int(b) * 10**9 + int(e) * 10**18 for a, b, e in dg]
+    assert got == [int(lo) | (int(hi) << 64) for lo, hi in c]
+
+
 def test_sixstep_plan_shapes(d, ctx6):
     for L, (n1, n2) in ((1024, (32, 32)), (2048, (32, 64)), (2**21, (1024, 2048)), (2**22, (2048, 2048))):
         info = d.dmul_get_plan(ctx6.handle, L)

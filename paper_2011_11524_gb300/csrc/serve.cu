@@ -2,6 +2,7 @@
 #include "serve.h"
 
 #include <algorithm>
+#include <chrono>
 
 namespace dml {
 
@@ -31,6 +32,7 @@ Server::Server(dmul_ctx *c) : ctx_(c) {
         auto s = std::make_unique<Slot>();
         s->owner = this;
         if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) init_ok_ = false;
+        if (cudaEventCreateWithFlags(&s->done_ev, cudaEventDisableTiming) != cudaSuccess) init_ok_ = false;
         if (cudaMalloc(&s->status, 64) != cudaSuccess || cudaMemset(s->status, 0, 64) != cudaSuccess)
             init_ok_ = false;
         if (init_batch_state(&s->bs) != DMUL_OK) init_ok_ = false;
@@ -43,6 +45,7 @@ Server::~Server() {
     {
         std::lock_guard<std::mutex> g(mu_);
         stop_ = true;
+        gen_.fetch_add(1, std::memory_order_release);
     }
     cv_.notify_all();
     if (worker_.joinable()) worker_.join();
@@ -51,6 +54,7 @@ Server::~Server() {
         if (s->stream) cudaStreamSynchronize(s->stream);
         free_batch_state(ctx_, &s->bs);
         if (s->status) cudaFree(s->status);
+        if (s->done_ev) cudaEventDestroy(s->done_ev);
         if (s->stream) cudaStreamDestroy(s->stream);
     }
     if (pool_) cudaMemPoolDestroy(pool_);
@@ -72,6 +76,7 @@ int Server::submit(const dmul_job &job, uint64_t *ticket) {
     tk.bytes = bytes;
     tk.four = four;
     queue_.push_back(t);
+    gen_.fetch_add(1, std::memory_order_release);
     *ticket = t;
     cv_.notify_all();
     return DMUL_OK;
@@ -118,30 +123,24 @@ void Server::stats(dmul_serve_info *out) {
     out->inflight_bytes = inflight_;
 }
 
-// Runs on CUDA's callback thread once the slot's batch, and the copy of its jobs' status words,
-// are done: completes each launched ticket with its own job's status (no CUDA calls are allowed
-// here); the worker recycles the slot afterwards.
-void CUDART_CB Server::on_done(void *p) {
-    Slot *s = (Slot *)p;
-    Server *self = s->owner;
-    {
-        std::lock_guard<std::mutex> g(self->mu_);
-        const BatchState &b = s->bs;
-        for (size_t i = 0; i < b.launched; ++i) {
-            auto it = self->tickets_.find(s->tickets[b.order[i]]);
-            if (it == self->tickets_.end()) continue;
-            it->second.status = device_code(((volatile uint32_t *)b.hstat)[i]);
-            it->second.done = true;
-        }
-        self->running_ -= b.launched;
-        s->tickets.clear();
-        s->finished = true;
+// The worker saw the slot's completion event (the batch, and the copy of its jobs' status words,
+// are done): complete each launched ticket with its own job's status; rc != DMUL_OK (the event
+// reported a failure) completes them all with rc.  Called with the lock held.
+void Server::complete(Slot &s, int rc) {
+    const BatchState &b = s.bs;
+    for (size_t i = 0; i < b.launched; ++i) {
+        auto it = tickets_.find(s.tickets[b.order[i]]);
+        if (it == tickets_.end()) continue;
+        it->second.status = rc ? rc : device_code(((volatile uint32_t *)b.hstat)[i]);
+        it->second.done = true;
     }
-    self->done_cv_.notify_all();
-    self->cv_.notify_all();
+    running_ -= b.launched;
+    s.tickets.clear();
+    s.finished = true;
+    done_cv_.notify_all();
 }
 
-// A finished slot (its tickets already completed by on_done): release its budget.
+// A finished slot (its tickets already completed by complete()): release its budget.
 void Server::retire(Slot &s, std::unique_lock<std::mutex> &g) {
     (void)g;
     s.busy = false;
@@ -166,7 +165,6 @@ bool Server::launch(Slot &s, std::unique_lock<std::mutex> &g) {
     }
     if (jobs.empty()) return false;
     std::vector<int> hs(jobs.size(), DMUL_OK);
-    // on_done may run (and clear s.tickets) before this thread takes the lock again
     const std::vector<uint64_t> tick = s.tickets;
     s.busy = true;
     s.bytes = bytes;
@@ -188,10 +186,10 @@ bool Server::launch(Slot &s, std::unique_lock<std::mutex> &g) {
         s.bs.arena_cap = 0;
     }
     if (arena) cudaFreeAsync(arena, s.stream);
-    if (rc == DMUL_OK && cudaLaunchHostFunc(s.stream, on_done, &s) != cudaSuccess) rc = DMUL_ERR_CUDA;
+    if (rc == DMUL_OK && cudaEventRecord(s.done_ev, s.stream) != cudaSuccess) rc = DMUL_ERR_CUDA;
     g.lock();
     if (rc != DMUL_OK) {
-        // nothing of this batch will complete on the stream (no callback was enqueued)
+        // nothing of this batch will complete on the stream (no completion event was recorded)
         for (uint64_t t : tick) {
             tickets_[t].status = rc;
             tickets_[t].done = true;
@@ -204,7 +202,7 @@ bool Server::launch(Slot &s, std::unique_lock<std::mutex> &g) {
         done_cv_.notify_all();
     } else {
         // requests the host checks rejected were left out of the launch: they complete now, with
-        // their own code; the launched ones complete in on_done
+        // their own code; the launched ones complete when the slot's event does
         bool any = false;
         for (size_t k = 0; k < hs.size(); ++k)
             if (hs[k]) {
@@ -218,32 +216,58 @@ bool Server::launch(Slot &s, std::unique_lock<std::mutex> &g) {
     return true;
 }
 
+// The worker: launches admitted requests into free slots and completes slots whose event has
+// passed.  While a batch is in flight, or for a short while after the last activity, it polls
+// instead of sleeping, so that a completion or a new request is seen within microseconds rather
+// than after a host callback and a thread wake-up; otherwise it sleeps until a request arrives.
+// The polling itself takes no lock: the slots' busy / finished flags are written by this thread
+// only, the events are queried without the lock, and new requests (or shutdown) show as a change
+// of gen_; the lock is taken only when there is something to do, so submitting and polling
+// threads never queue behind the worker.
 void Server::loop() {
     set_device(ctx_);
-    std::unique_lock<std::mutex> g(mu_);
+    auto last = std::chrono::steady_clock::now();
+    uint64_t seen = gen_.load(std::memory_order_acquire) - 1;  // the first pass looks at everything
+    std::vector<int> done(slots_.size());
     for (;;) {
-        // Wake only for something actionable, so that the lock is released while waiting (the
-        // completion callback needs it): a finished slot, a free slot with an admissible request,
-        // or shutdown with nothing in flight.
-        cv_.wait(g, [&] {
-            bool any_busy = false, any_free = false;
-            for (auto &s : slots_) {
-                if (s->busy && s->finished) return true;
-                any_busy |= s->busy;
-                any_free |= !s->busy;
+        bool any_done = false, any_busy = false;
+        for (size_t i = 0; i < slots_.size(); ++i) {
+            done[i] = -1;
+            Slot &s = *slots_[i];
+            if (!s.busy || s.finished) continue;
+            any_busy = true;
+            const cudaError_t q = cudaEventQuery(s.done_ev);
+            if (q == cudaErrorNotReady) continue;
+            if (q != cudaSuccess) cudaGetLastError();
+            done[i] = q == cudaSuccess ? DMUL_OK : DMUL_ERR_CUDA;
+            any_done = true;
+        }
+        const uint64_t gen = gen_.load(std::memory_order_acquire);
+        auto now = std::chrono::steady_clock::now();
+        if (!any_done && gen == seen) {
+            if (any_busy || now - last < std::chrono::microseconds(kIdlePollUs)) {
+                std::this_thread::yield();
+                continue;
             }
-            if (stop_) return !any_busy;
-            return !queue_.empty() && any_free && !mem_blocked_;
-        });
+            std::unique_lock<std::mutex> g(mu_);
+            cv_.wait(g, [&] { return gen_.load(std::memory_order_acquire) != seen; });
+            last = std::chrono::steady_clock::now();
+            continue;
+        }
+        seen = gen;
+        last = now;
+        std::unique_lock<std::mutex> g(mu_);
+        for (size_t i = 0; i < slots_.size(); ++i)
+            if (done[i] >= 0) complete(*slots_[i], done[i]);
         for (auto &s : slots_)
             if (s->busy && s->finished) {
                 retire(*s, g);
                 mem_blocked_ = false;  // memory came back: retry the head of the queue
             }
-        bool any_busy = false;
+        any_busy = false;
         for (auto &s : slots_) any_busy |= s->busy;
         if (stop_) {
-            if (any_busy) continue;
+            if (any_busy) continue;  // the batches in flight complete first
             for (uint64_t t : queue_) {  // never started: the context is going away
                 tickets_[t].status = DMUL_ERR_INVALID;
                 tickets_[t].done = true;
@@ -270,6 +294,9 @@ void Server::loop() {
             }
             any_busy = true;
         }
+        // requests that arrived while this pass held (or dropped, in launch) the lock are seen
+        // by the next pass through gen_; a queue left non-empty because every slot is busy waits
+        // for a completion
     }
 }
 

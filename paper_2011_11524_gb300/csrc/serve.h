@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <condition_variable>
 #include <deque>
 #include <memory>
@@ -30,7 +31,9 @@ int run_batch(dmul_ctx *c, dmul_job *jobs, size_t count, cudaStream_t s);
 // length, see batch.cu) and returns to the queue; requests that arrive while batches run join the
 // next one.  Scratch comes from the server's stream-ordered memory pool (allocated and freed on
 // the slot's stream), so admitting and retiring batches never synchronizes the device.  A slot's
-// completion is signalled by a host callback on its stream.
+// completion is an event recorded after its batch, which the worker polls while anything is in
+// flight (and for kIdlePollUs after its last activity) instead of sleeping: a completion or a new
+// request is seen within microseconds, at the price of one host core kept busy meanwhile.
 class Server {
   public:
     explicit Server(dmul_ctx *c);
@@ -42,6 +45,7 @@ class Server {
 
     static constexpr int kSlots = 4;
     static constexpr size_t kMaxBatch = 1024;
+    static constexpr int kIdlePollUs = 300;  // the worker keeps polling this long after its last activity
 
   private:
     struct Ticket {
@@ -55,6 +59,7 @@ class Server {
         Server *owner = nullptr;
         BatchState bs;
         cudaStream_t stream = nullptr;
+        cudaEvent_t done_ev = nullptr;  // recorded after each batch (the worker polls it)
         uint32_t *status = nullptr;  // launch status word of this slot's batches (every job also
                                      // has its own, in the batch state: bs.hstat / bs.order)
         std::vector<uint64_t> tickets;  // the batch's requests, in the order they were passed
@@ -63,7 +68,7 @@ class Server {
         bool busy = false;
         bool finished = false;
     };
-    static void CUDART_CB on_done(void *slot);
+    void complete(Slot &s, int rc);
     void loop();
     void retire(Slot &s, std::unique_lock<std::mutex> &g);
     bool launch(Slot &s, std::unique_lock<std::mutex> &g);
@@ -75,6 +80,7 @@ class Server {
     std::unordered_map<uint64_t, Ticket> tickets_;  // issued and not yet released
     uint64_t next_ = 1;
     uint64_t running_ = 0;  // requests in launched batches
+    std::atomic<uint64_t> gen_{0};  // bumped by every submission and by shutdown (the worker's wake-up)
     uint64_t peak_running_ = 0;
     bool stop_ = false;
     bool init_ok_ = false;

@@ -60,7 +60,7 @@ typedef struct dmul_ctx dmul_ctx;
                                   /* the four-step form (Sec. 7.1-7.2); results are identical     */
 #define DMUL_FLAG_STAGE_TIMING 2u /* record CUDA events around each pipeline stage (see          */
                                   /* dmul_stage_times); adds a little launch overhead             */
-#define DMUL_FLAG_NO_SMALL 4u     /* never use the fused one-launch path for short products       */
+#define DMUL_FLAG_NO_SMALL 4u     /* never use the one-cluster kernel for short products          */
                                   /* (transform length <= 24576); they take the four-step path    */
 #define DMUL_FLAG_NO_AUTOTUNE 8u  /* plan every length with the default split instead of timing   */
                                   /* the candidate splits and CTA sizes on first use              */
@@ -86,6 +86,10 @@ typedef struct dmul_ctx dmul_ctx;
                                        /* never runs and tile 1's bounded look-back wait expires */
                                        /* (DMUL_ERR_TIMEOUT at the next dmul_sync); the kernels  */
                                        /* end normally and the context stays usable              */
+#define DMUL_FLAG_NO_FUSED 4096u       /* never run a lone short product (transform length       */
+                                       /* 16384, 20480 or 24576, as N1 x 256) as the four-step   */
+                                       /* steps in one cooperative launch; it takes the small    */
+                                       /* kernel or the four-kernel pipeline                     */
 
 typedef struct {
     int device;                /* CUDA device ordinal                                          */
@@ -119,7 +123,12 @@ int dmul_sync(dmul_ctx *ctx, void *stream);
  * device pointers; z must not overlap x or y.  x == y with nx == ny is a squaring (the aliasing
  * case of Sec. 6) and takes the cheaper dmul_sqr path.  All nx + ny limbs of z are written.
  * nz (device pointer to one uint64_t, or NULL) receives the normalized length: the index of the
- * highest nonzero limb + 1, or 1 for a zero product.  Asynchronous on `stream`. */
+ * highest nonzero limb + 1, or 1 for a zero product.  Asynchronous on `stream`.
+ * A short product (transform length <= 24576) runs, by the first such product's timing, as one
+ * cluster kernel, as the four-kernel pipeline or, at lengths 16384, 20480 and 24576 with 16-byte
+ * aligned operands and outside a stream capture, as one cooperative launch of the same four-step
+ * steps; the limbs are identical on every path (DMUL_FLAG_NO_SMALL / DMUL_FLAG_NO_FUSED rule
+ * paths out). */
 int dmul_mul(dmul_ctx *ctx, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny,
              uint32_t *z, size_t z_cap, uint64_t *nz, void *stream);
 

@@ -41,7 +41,7 @@ static int cuda_fail(cudaError_t e) {
 
 static const char *kStageNames[kNumStages] = {"col_fwd", "row_mul", "col_inv_crt", "carry_scan",
                                               "transpose", "row_dft", "crt", "pack_transpose",
-                                              "small_mul", "batch"};
+                                              "small_mul", "batch", "short_fused"};
 
 Timed::Timed(dmul_ctx *c_, int id_, cudaStream_t s_) : c(c_), id(id_), s(s_) {
         if (!c->timing) return;
@@ -356,31 +356,81 @@ int enqueue_transforms(dmul_ctx *c, PlanEntry *pe, const uint32_t *x, size_t nx,
                        const uint32_t *y, size_t ny, bool square, cudaStream_t s,
                        cudaEvent_t y_ready = nullptr);
 
-// A lone short product can run as one cluster (the fused kernel: one launch, three SMs) or as the
-// four-step pipeline (four launches, many CTAs).  Which is faster depends on the length; the
-// first product of each short length times both on operands of nonzero limbs (the work of a real
-// product) and keeps the faster.
+// A lone short product can run three ways: as one cluster (the small kernel: one launch, three
+// SMs), as the four-step pipeline (four launches, many CTAs), or -- at N = N1 x 256 with N1 in
+// {64, 80, 96} -- as the four-step steps in one cooperative launch over every SM (shortfused.cu).
+// Which is fastest depends on the length: the first product of each length times the candidates
+// on operands of nonzero limbs (the work of a real product) and keeps the fastest.  small_single
+// holds the small kernel against the four-step pipeline alone (the batched form's choice for its
+// short groups), short_path the lone product's choice among every candidate.
 int small_single_cached(const dmul_ctx *c, uint64_t Ns) {
     std::lock_guard<std::mutex> g(c->small_mu);
     auto it = c->small_single.find(Ns);
     return it == c->small_single.end() ? -1 : (it->second ? 1 : 0);
 }
 
-int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
-    const int known = small_single_cached(c, Ns);
-    if (known >= 0) {
-        *use_small = known == 1;
+// The fused kernel's plan for N: the split N1 x 256 whatever the autotuner picked for the pipeline.
+static int get_fused_plan(dmul_ctx *c, uint64_t N, PlanEntry **out) {
+    auto it = c->fused_plans.find(N);
+    if (it != c->fused_plans.end()) {
+        *out = it->second.get();
         return DMUL_OK;
     }
-    SmallPlanEntry *se;
-    PlanEntry *pe;
-    int rc = get_small_plan(c, Ns, &se);
+    HostPlan hp;
+    if (N % 256 || !make_host_plan(N, &hp, (uint32_t)(N / 256))) return DMUL_ERR_INVALID;
+    std::unique_ptr<PlanEntry> pe;
+    int rc = build_plan_entry(c, hp, &pe);
+    if (rc) return rc;
+    if (!short_fused_supported(pe->pd)) {
+        dev_free(c, pe->dtables, pe->bytes);
+        return DMUL_ERR_INVALID;
+    }
+    *out = pe.get();
+    c->fused_plans[N] = std::move(pe);
+    return DMUL_OK;
+}
+
+// Whether a lone product of transform length N may take the fused kernel: the length and the
+// operands' alignment suit it, and no stream capture is in progress (a captured product takes the
+// pipeline's plain launches).
+static bool fused_candidate(const dmul_ctx *c, uint64_t N, const void *x, const void *y, cudaStream_t s) {
+    if (c->cfg.flags & (DMUL_FLAG_SIXSTEP | DMUL_FLAG_NO_FUSED)) return false;
+    const uint64_t n1 = N / 256;
+    if (N % 256 || (n1 != 64 && n1 != 80 && n1 != 96)) return false;
+    if ((((uintptr_t)x) | ((uintptr_t)y)) & 15) return false;
+    if (current_device_sms() < 48) return false;  // a CTA per column task of both operands
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cap == cudaStreamCaptureStatusNone;
+}
+
+static cudaError_t launch_fused_product(dmul_ctx *c, const PlanEntry *fe, const JobDev &jd, cudaStream_t s) {
+    return launch_short_fused(fe->pd, fe->bytes, jd.x, jd.nx, jd.y, jd.ny, c->X, c->Y, jd.z, jd.nz, c->spill,
+                              (CarryCtl *)c->ctl, c->status, c->grid_sync, c->spin_limit,
+                              (uint32_t)current_device_sms(), s);
+}
+
+struct ShortTimes {
+    float small = 1e30f, four = 1e30f, fused = 1e30f;
+};
+
+// Times a product of length min(Ns, N) (or N without a small plan) on each candidate path: the
+// small kernel (Ns > 0), the pipeline, the fused kernel (fused).  The best of three runs after a
+// warm-up; the context's status word is kept for the next dmul_sync.
+static int time_short_paths(dmul_ctx *c, uint64_t Ns, uint64_t N, bool fused, ShortTimes *t) {
+    SmallPlanEntry *se = nullptr;
+    PlanEntry *pe = nullptr, *fe = nullptr;
+    int rc = Ns ? get_small_plan(c, Ns, &se) : DMUL_OK;
     if (!rc) rc = get_plan(c, N, &pe);
+    if (!rc && fused) rc = get_fused_plan(c, N, &fe);
     if (rc) return rc;
     CK(cudaDeviceSynchronize());
-    uint32_t saved_status = 0;  // kept for the next dmul_sync, as in autotune_plan
+    uint32_t saved_status = 0;
     CK(cudaMemcpy(&saved_status, c->status, 4, cudaMemcpyDeviceToHost));
-    const uint64_t Lt = Ns;  // a full-length product: L = N of the short plan
+    const uint64_t Lt = Ns ? std::min(Ns, N) : N;
     rc = ensure_scratch(c, N, Lt, true);
     if (rc) return rc;
     uint32_t *buf = nullptr;
@@ -388,32 +438,42 @@ int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
     if ((rc = dev_alloc(c, (void **)&buf, 2 * Lt * 4))) return rc;
     if ((rc = dev_alloc(c, (void **)&nzb, 64))) { dev_free(c, buf, 2 * Lt * 4); return rc; }
     cudaStream_t s = c->own_stream;
-    // operands of valid nonzero limbs (0x11111111 < 10^9): both paths do the work of a real product
+    // operands of valid nonzero limbs (0x11111111 < 10^9): every path does the work of a real product
     cudaMemsetAsync(buf, 0x11, 2 * Lt * 4, s);
     JobDev jd;
     memset(&jd, 0, sizeof(jd));
-    jd.x = buf; jd.y = buf + Lt / 2; jd.z = buf + Lt; jd.nz = nzb; jd.nx = Lt / 2; jd.ny = Lt / 2; jd.L = Lt;
+    jd.x = buf; jd.y = buf + Lt / 2; jd.z = buf + Lt; jd.nz = nzb; jd.nx = Lt / 2; jd.ny = Lt - Lt / 2; jd.L = Lt;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float t_small = 1e30f, t_four = 1e30f;
-    for (int it2 = 0; it2 < 4; ++it2) {
+    auto timed = [&](float &best, int it, auto &&body) {
         float ms = 0;
         cudaEventRecord(e0, s);
-        launch_small_mul_one(se->sp, jd, c->status, s);
+        body();
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         cudaEventElapsedTime(&ms, e0, e1);
-        if (it2) t_small = std::min(t_small, ms);
-        cudaEventRecord(e0, s);
-        launch_col_fwd(pe->pd, jd.x, jd.nx, jd.y, jd.ny, c->X, c->Y, c->status, s);
-        launch_row_any(pe->pd, c->X, c->Y, false, c->status, s);
-        launch_col_inv(pe->pd, c->X, Lt, kInvDigits, jd.z, c->spill, s, c->ctl, carry_ctl_bytes(Lt));
-        launch_carry(jd.z, c->spill, Lt, (CarryCtl *)c->ctl, nzb, c->status, s);
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (it2) t_four = std::min(t_four, ms);
+        if (it) best = std::min(best, ms);  // the first run warms up
+    };
+    for (int it = 0; it < 4; ++it) {
+        if (se) timed(t->small, it, [&] { launch_small_mul_one(se->sp, jd, c->status, s); });
+        timed(t->four, it, [&] {
+            launch_col_fwd(pe->pd, jd.x, jd.nx, jd.y, jd.ny, c->X, c->Y, c->status, s);
+            launch_row_any(pe->pd, c->X, c->Y, false, c->status, s);
+            launch_col_inv(pe->pd, c->X, Lt, kInvDigits, jd.z, c->spill, s, c->ctl, carry_ctl_bytes(Lt));
+            launch_carry(jd.z, c->spill, Lt, (CarryCtl *)c->ctl, nzb, c->status, s);
+        });
+        if (fe) {
+            // a cooperative launch the device refuses (too few SMs free for its grid) leaves the
+            // fused kernel out of the choice; the refusal is not a sticky error
+            bool ok = true;
+            timed(t->fused, it, [&] { ok = launch_fused_product(c, fe, jd, s) == cudaSuccess; });
+            if (!ok) {
+                cudaGetLastError();
+                t->fused = 1e30f;
+                fe = nullptr;
+            }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -422,9 +482,47 @@ int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
     dev_free(c, buf, 2 * Lt * 4);
     dev_free(c, nzb, 64);
     if (cudaGetLastError() != cudaSuccess) return DMUL_ERR_CUDA;
-    *use_small = t_small <= t_four;
+    return DMUL_OK;
+}
+
+int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
+    const int known = small_single_cached(c, Ns);
+    if (known >= 0) {
+        *use_small = known == 1;
+        return DMUL_OK;
+    }
+    ShortTimes t;
+    int rc = time_short_paths(c, Ns, N, false, &t);
+    if (rc) return rc;
+    *use_small = t.small <= t.four;
     std::lock_guard<std::mutex> g(c->small_mu);
     c->small_single[Ns] = *use_small;
+    return DMUL_OK;
+}
+
+enum ShortPath { kPathFour = 0, kPathSmall = 1, kPathFused = 2 };
+
+// The lone product's path among the candidates (Ns > 0: the small kernel; fused: the fused kernel).
+static int prefer_short_path(dmul_ctx *c, uint64_t Ns, uint64_t N, bool fused, int *path) {
+    const uint64_t key = (Ns << 40) | (N << 1) | (fused ? 1u : 0u);
+    {
+        std::lock_guard<std::mutex> g(c->small_mu);
+        auto it = c->short_path.find(key);
+        if (it != c->short_path.end()) {
+            *path = it->second;
+            return DMUL_OK;
+        }
+    }
+    ShortTimes t;
+    int rc = time_short_paths(c, Ns, N, fused, &t);
+    if (rc) return rc;
+    *path = kPathFour;
+    float best = t.four;
+    if (Ns && t.small <= best) { *path = kPathSmall; best = t.small; }
+    if (fused && t.fused < best) *path = kPathFused;
+    std::lock_guard<std::mutex> g(c->small_mu);
+    if (Ns && !c->small_single.count(Ns)) c->small_single[Ns] = t.small <= t.four;
+    c->short_path[key] = *path;
     return DMUL_OK;
 }
 
@@ -444,25 +542,39 @@ int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, si
     rc = set_device(c);
     if (rc) return rc;
     const uint64_t Ns = choose_N_small(L);
-    bool use_small = mode == kInvDigits && Ns && !(c->cfg.flags & (DMUL_FLAG_SIXSTEP | DMUL_FLAG_NO_SMALL));
-    if (use_small && !(c->cfg.flags & DMUL_FLAG_NO_AUTOTUNE)) {
-        rc = prefer_small_single(c, Ns, N, &use_small);
-        if (rc) return rc;
+    const bool small_ok = mode == kInvDigits && Ns && !(c->cfg.flags & (DMUL_FLAG_SIXSTEP | DMUL_FLAG_NO_SMALL));
+    const bool fused_ok = mode == kInvDigits && fused_candidate(c, N, x, y, s);
+    int path = kPathFour;
+    if (small_ok || fused_ok) {
+        if (c->cfg.flags & DMUL_FLAG_NO_AUTOTUNE) path = small_ok ? kPathSmall : kPathFused;
+        else if ((rc = prefer_short_path(c, small_ok ? Ns : 0, N, fused_ok, &path))) return rc;
     }
-    if (use_small) {
-        // the whole product in one cluster launch (batch.cu): transforms, CRT and carry in SMEM
-        SmallPlanEntry *se;
-        rc = get_small_plan(c, Ns, &se);
-        if (rc) return rc;
+    if (path != kPathFour) {
         JobDev jd;
         memset(&jd, 0, sizeof(jd));
         jd.x = x; jd.y = y; jd.z = z; jd.nz = nz; jd.nx = nx; jd.ny = ny; jd.L = L;
         jd.square = (x == y && nx == ny) ? 1u : 0u;
-        c->last_stream = s;
-        if (y_ready) CK(cudaStreamWaitEvent(s, y_ready, 0));
-        Timed t(c, kStSmall, s);
-        CK(launch_small_mul_one(se->sp, jd, c->status, s));
-        // the fused kernel keeps its digit sums in z: its limbs are copied out afterwards
+        if (path == kPathSmall) {
+            // the whole product in one cluster launch (batch.cu): transforms, CRT and carry in SMEM
+            SmallPlanEntry *se;
+            rc = get_small_plan(c, Ns, &se);
+            if (rc) return rc;
+            c->last_stream = s;
+            if (y_ready) CK(cudaStreamWaitEvent(s, y_ready, 0));
+            Timed t(c, kStSmall, s);
+            CK(launch_small_mul_one(se->sp, jd, c->status, s));
+        } else {
+            // the four-step steps in one cooperative launch (shortfused.cu)
+            PlanEntry *fe;
+            rc = get_fused_plan(c, N, &fe);
+            if (!rc) rc = ensure_scratch(c, N, L, true);
+            if (rc) return rc;
+            c->last_stream = s;
+            if (y_ready) CK(cudaStreamWaitEvent(s, y_ready, 0));
+            Timed t(c, kStFused, s);
+            CK(launch_fused_product(c, fe, jd, s));
+        }
+        // both kernels leave the limbs in z: they are copied out afterwards
         if (z_out) CK(cudaMemcpyAsync(z_out, z, L * 4, cudaMemcpyDefault, s));
         return DMUL_OK;
     }
@@ -678,6 +790,7 @@ int dmul_init(dmul_ctx **out, const dmul_config *cfg) {
     CK(upload_constants_batch(pc, crt));
     CK(upload_constants_rowpass(pc, crt));
     CK(upload_constants_colpass(pc, crt));
+    CK(upload_constants_shortfused(pc, crt));
     CK(init_kernel_attributes_main());
     CK(init_kernel_attributes_sixstep());
     CK(init_kernel_attributes_batch());
@@ -689,6 +802,7 @@ int dmul_init(dmul_ctx **out, const dmul_config *cfg) {
     rc = dev_alloc(c.get(), (void **)&c->fwd_sync, 256);
     if (rc) return rc;
     CK(cudaMemset(c->fwd_sync, 0, 256));
+    c->grid_sync = c->fwd_sync + 32;
     CK(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
     *out = c.release();
     return DMUL_OK;
@@ -700,6 +814,7 @@ void dmul_destroy(dmul_ctx *c) {
     c->server.reset();
     cudaDeviceSynchronize();
     for (auto &kv : c->plans) dev_free(c, kv.second->dtables, kv.second->bytes);
+    for (auto &kv : c->fused_plans) dev_free(c, kv.second->dtables, kv.second->bytes);
     dev_free(c, c->X, c->res_words * 4);
     dev_free(c, c->Y, c->res_words * 4);
     dev_free(c, c->spill, c->spill_cap * sizeof(uint2));

@@ -82,8 +82,10 @@ struct dmul_ctx {
     uint64_t used = 0;  // library-owned device bytes
     std::map<uint64_t, std::unique_ptr<dml::PlanEntry>> plans;
     std::map<uint64_t, std::unique_ptr<dml::SmallPlanEntry>> small_plans;
-    std::map<uint64_t, bool> small_single;  // per short length: fused kernel faster than four-step
-    mutable std::mutex small_mu;            // guards small_single (read by dmul_submit callers)
+    std::map<uint64_t, bool> small_single;  // per short length: small kernel faster than four-step
+    std::map<uint64_t, int> short_path;     // per lone short product's lengths: its fastest path
+    std::map<uint64_t, std::unique_ptr<dml::PlanEntry>> fused_plans;  // N1 x 256 plans of the fused kernel
+    mutable std::mutex small_mu;            // guards small_single, short_path (read by dmul_submit callers)
     // scratch of the plain form (one set, used by one call at a time)
     uint32_t *X = nullptr, *Y = nullptr;
     size_t res_words = 0;  // capacity of X and of Y, in words
@@ -96,6 +98,8 @@ struct dmul_ctx {
     // reset) and the host's running total of the columns the plain path has sent through them
     uint32_t *fwd_sync = nullptr;
     uint32_t fwd_cols = 0;
+    // the fused short-product kernel's grid barrier word (in fwd_sync's allocation; never reset)
+    uint32_t *grid_sync = nullptr;
     // bound of every device-side wait of this context's kernels, in polls (0: the defaults;
     // DMUL_FLAG_SHORT_WAITS makes it short, so that tests can make a wait run out quickly)
     uint32_t spin_limit = 0;
@@ -127,7 +131,7 @@ struct dmul_ctx {
 namespace dml {
 
 enum StageId { kStColFwd = 0, kStRowMul, kStColInv, kStCarry, kStTranspose, kStRowDft, kStCrt,
-               kStPack, kStSmall, kStBatch, kNumStages };
+               kStPack, kStSmall, kStBatch, kStFused, kNumStages };
 
 int set_device(dmul_ctx *c);
 int dev_alloc(dmul_ctx *c, void **p, size_t bytes);
@@ -179,8 +183,8 @@ int flush_batch_status(BatchState *b);
 // Library scratch a job needs on the four-step path: 0 for a short product, unless the measured
 // choice for its length is the four-step pipeline (then *four = true, when four is non-null).
 size_t job_scratch_bytes(const dmul_ctx *c, const dmul_job &j, bool *four = nullptr);
-// The measured choice for lone short products of transform length Ns: 1 fused kernel, 0 four-step,
-// -1 not measured yet.
+// The measured choice for short products of transform length Ns: 1 the small kernel (one cluster),
+// 0 the four-step pipeline, -1 not measured yet.
 int small_single_cached(const dmul_ctx *c, uint64_t Ns);
 int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small);
 

@@ -202,6 +202,20 @@ cudaError_t launch_col_inv_b(const PlanDev &pd, const JobDev *jobs, int njobs, c
 cudaError_t launch_carry_b(const JobDev *jobs, int njobs, uint32_t maxtiles, uint32_t *status,
                            cudaStream_t s);
 
+// A short four-step product in one cooperative launch (shortfused.cu): forward columns, row pass,
+// inverse columns, CRT with digit sums, carry scan as five phases separated by grid barriers.
+// Supported for the planner's schedules at N1 in {64, 80, 96}, N2 = 256; x and y 16-byte aligned.
+// gbar: a device word of the grid barriers (zero-initialized once, never reset; one launch at a
+// time per word).  48 <= grid <= the SM count (every CTA resident at once).  pd.tw[0] starts the
+// plan's contiguous twiddle tables of table_bytes bytes.
+// The carry scan's control block ctl (carry_ctl_bytes(nx + ny)) is cleared by the kernel.
+bool short_fused_supported(const PlanDev &pd);
+cudaError_t launch_short_fused(const PlanDev &pd, uint64_t table_bytes, const uint32_t *x, uint64_t nx,
+                               const uint32_t *y, uint64_t ny, uint32_t *X, uint32_t *Y, uint32_t *z, uint64_t *nz,
+                               uint2 *spill, CarryCtl *ctl, uint32_t *status, uint32_t *gbar, uint32_t spin,
+                               uint32_t grid, cudaStream_t s);
+cudaError_t upload_constants_shortfused(const PrimeConst pc[kPrimes], const CrtConst &crt);
+
 // Sets the shared-memory / cluster attributes of every kernel once (outside any graph capture).
 cudaError_t init_kernel_attributes_main();
 cudaError_t init_kernel_attributes_sixstep();

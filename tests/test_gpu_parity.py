@@ -39,8 +39,9 @@ def ctx(d):
 
 @pytest.fixture(scope="module")
 def ctx4(d):
-    """Four-step path for every length (the fused one-launch path for short products is off)."""
-    c = d.Context(0, flags=d.DMUL_FLAG_NO_SMALL)
+    """Four-kernel pipeline for every length (the one-cluster and the cooperative one-launch paths
+    for short products are off)."""
+    c = d.Context(0, flags=d.DMUL_FLAG_NO_SMALL | d.DMUL_FLAG_NO_FUSED)
     yield c
     c.close()
 
@@ -48,7 +49,8 @@ def ctx4(d):
 @pytest.fixture(scope="module")
 def ctx_tma(d):
     """Four-step path with the persistent TMA-fed row pass for every length."""
-    c = d.Context(0, flags=d.DMUL_FLAG_NO_SMALL | d.DMUL_FLAG_NO_AUTOTUNE | d.DMUL_FLAG_ROW_TMA)
+    c = d.Context(0, flags=d.DMUL_FLAG_NO_SMALL | d.DMUL_FLAG_NO_FUSED | d.DMUL_FLAG_NO_AUTOTUNE |
+                  d.DMUL_FLAG_ROW_TMA)
     yield c
     c.close()
 
@@ -521,11 +523,129 @@ def test_c1_workload(d, ctx):
     assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))
 
 
+# ---- short products as one cooperative launch (N = N1 x 256, N1 in {64, 80, 96}) ----------------
+@pytest.fixture(scope="module")
+def ctx_fused(d):
+    """Short products of N = 16384, 20480 and 24576 through the cooperative one-launch kernel (no
+    first-use timing, the one-cluster kernel off), with stage timing to see which path ran."""
+    c = d.Context(0, flags=d.DMUL_FLAG_NO_SMALL | d.DMUL_FLAG_NO_AUTOTUNE | d.DMUL_FLAG_STAGE_TIMING)
+    yield c
+    c.close()
+
+
+# (n, m) with their transform lengths: full and ragged, balanced and unbalanced, one-limb operands
+FUSED_SHAPES = [(8192, 8192), (7001, 8000), (16383, 1), (1, 16000), (12289 - 4000, 4000),
+                (10240, 10240), (9000, 11480), (20480 - 1, 1),
+                (11112, 11112), (12288, 12288), (24575, 1), (3, 24573), (12000, 12001)]
+
+
+def _fused_launches(ctx):
+    return ctx.stage_times().get("short_fused", (0.0, 0))[1]
+
+
+@pytest.mark.parametrize("n,m", FUSED_SHAPES)
+def test_fused_short_product(d, ctx_fused, n, m):
+    L = n + m
+    assert d.dmul_get_plan(ctx_fused.handle, L).N in (16384, 20480, 24576)
+    rng = _rng(12000 + n + 3 * m)
+    x, y = _rand(rng, n), _rand(rng, m)
+    _fused_launches(ctx_fused)
+    for square in (False, True):
+        z, nz = _gpu_mul(d, ctx_fused, x, x if square else y, square=square)
+        ref = oracle.mul(x, x) if square else oracle.mul(x, y)
+        assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))
+    # the square has length 2n: fused only when that length is one of the three
+    expect = 1 + (d.dmul_get_plan(ctx_fused.handle, 2 * n).N in (16384, 20480, 24576))
+    assert _fused_launches(ctx_fused) == expect
+
+
+def test_fused_worst_case_and_zero(d, ctx_fused):
+    """All-nines operands (the largest convolution coefficients: the prime-product bound) against
+    the closed form, a zero operand, leading zero limbs, and the overflow-free top limb."""
+    for h in (8192, 10240, 12288):
+        nines = np.full(h, B - 1, np.uint32)
+        z, nz = _gpu_mul(d, ctx_fused, nines, nines, square=True)
+        expect = np.zeros(2 * h, np.uint32)
+        expect[0] = 1
+        expect[h] = B - 2
+        expect[h + 1:] = B - 1
+        assert np.array_equal(z, expect) and nz == 2 * h
+    rng = _rng(12500)
+    x = _rand(rng, 9000)
+    zero = np.zeros(7000, np.uint32)
+    z, nz = _gpu_mul(d, ctx_fused, x, zero)
+    assert not z.any() and nz == 1
+    y = _rand(rng, 7000)
+    y[-500:] = 0  # leading zero limbs
+    z, nz = _gpu_mul(d, ctx_fused, x, y)
+    ref = oracle.mul(x, y)
+    assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))
+    assert _fused_launches(ctx_fused) == 5
+
+
+def test_fused_back_to_back(d, ctx_fused):
+    """Forty launches queued without a synchronization in between (the grid barrier word carries
+    over from launch to launch): every product against the oracle."""
+    rng = _rng(12600)
+    pairs = [(_rand(rng, int(n)), _rand(rng, int(m)))
+             for n, m in zip(rng.integers(6145, 12289, 40), rng.integers(6145, 12288, 40))]
+    outs = []
+    for x, y in pairs:
+        tx, ty = d.to_device(x), d.to_device(y)
+        outs.append((tx, ty) + ctx_fused.mul(tx, ty, sync=False))
+    ctx_fused.sync()
+    for (x, y), (_, _, z, nz) in zip(pairs, outs):
+        ref = oracle.mul(x, y)
+        assert np.array_equal(d.to_host(z), ref) and int(nz.item()) == len(oracle.normalize(ref))
+    assert _fused_launches(ctx_fused) == 40
+
+
+def test_fused_invalid_limb_flagged(d, ctx_fused):
+    """A limb >= 10^9 makes dmul_sync report DMUL_ERR_INVALID, and the context stays usable."""
+    rng = _rng(12700)
+    x, y = _rand(rng, 8000), _rand(rng, 8000)
+    bad = x.copy()
+    bad[4321] = B
+    with pytest.raises(d.DmulError) as e:
+        _gpu_mul(d, ctx_fused, bad, y)
+    assert e.value.status == d.DMUL_ERR_INVALID
+    z, nz = _gpu_mul(d, ctx_fused, x, y)
+    assert np.array_equal(z, oracle.mul(x, y))
+
+
+def test_fused_unaligned_takes_pipeline(d, ctx_fused):
+    """Operands that are not 16-byte aligned take the four-kernel pipeline (same limbs)."""
+    rng = _rng(12800)
+    x, y = _rand(rng, 9000), _rand(rng, 9001)
+    buf = torch.zeros(9000 + 9001 + 8, dtype=torch.int32, device="cuda")
+    tx = buf[1:9001]
+    ty = buf[9003:9003 + 9001]
+    tx.copy_(d.to_device(x))
+    ty.copy_(d.to_device(y))
+    _fused_launches(ctx_fused)
+    z, nz = ctx_fused.mul(tx, ty)
+    assert np.array_equal(d.to_host(z), oracle.mul(x, y))
+    t = ctx_fused.stage_times()
+    assert "short_fused" not in t and t["carry_scan"][1] == 1
+
+
+def test_fused_matches_other_paths(d, ctx, ctx4):
+    """The same products through the default (timed) context and the four-kernel pipeline are
+    bit-identical with the oracle; the timed choice may be any of the three paths."""
+    rng = _rng(12900)
+    for n, m in [(11112, 11112), (8192, 8000), (10000, 10480)]:
+        x, y = _rand(rng, n), _rand(rng, m)
+        ref = oracle.mul(x, y)
+        for c in (ctx, ctx4):
+            z, nz = _gpu_mul(d, c, x, y)
+            assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))
+
+
 # ---- compile-time specialized column passes (N1 = 2^a, 3 2^a, 5 2^a from 64 to 1536) -----------
 @pytest.fixture(scope="module")
 def ctx_def(d):
     """Four-step path with the planner's default split and the one-CTA-per-row pass."""
-    c = d.Context(0, flags=d.DMUL_FLAG_NO_SMALL | d.DMUL_FLAG_NO_AUTOTUNE)
+    c = d.Context(0, flags=d.DMUL_FLAG_NO_SMALL | d.DMUL_FLAG_NO_FUSED | d.DMUL_FLAG_NO_AUTOTUNE)
     yield c
     c.close()
 
@@ -554,7 +674,8 @@ SPECIALIZED_COLS = [((3000, 3000), 96, 64),           # N = 3 * 2^11
 @pytest.fixture(scope="module")
 def ctx_half(d):
     """As ctx_def, with the column passes on N1 x 16 half tiles (six-CTA CRT clusters)."""
-    c = d.Context(0, flags=d.DMUL_FLAG_NO_SMALL | d.DMUL_FLAG_NO_AUTOTUNE | d.DMUL_FLAG_COL_HALF)
+    c = d.Context(0, flags=d.DMUL_FLAG_NO_SMALL | d.DMUL_FLAG_NO_FUSED | d.DMUL_FLAG_NO_AUTOTUNE |
+                  d.DMUL_FLAG_COL_HALF)
     yield c
     c.close()
 

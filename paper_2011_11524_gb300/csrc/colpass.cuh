@@ -228,6 +228,7 @@ __global__ void __launch_bounds__(512) k_col_fwd_ct(const PlanDev pd, const uint
                                                     uint32_t *status) {
     extern __shared__ __align__(16) uint32_t sm[];
     pdl_trigger();
+    prefetch_tables(pd);
     pdl_wait();
     uint32_t pi, tile;
     bool second;
@@ -563,6 +564,7 @@ __global__ void __launch_bounds__(256, 3) k_col_fwd_h(const PlanDev pd, const ui
                                                       uint32_t *status) {
     extern __shared__ __align__(16) uint32_t sm[];
     pdl_trigger();
+    prefetch_tables(pd);
     pdl_wait();
     uint32_t pi, tile;
     bool second;

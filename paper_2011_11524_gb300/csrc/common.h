@@ -66,6 +66,9 @@ struct PlanDev {
     uint32_t spin;                      // bound of the device-side waits (polls); 0: the defaults
     uint64_t offA, offQ, offAi, offQi;  // four-step twiddle tables (uint2 offsets)
     const uint2 *tw[kPrimes];           // per-prime table buffers (device)
+    // bytes of the contiguous tables at tw[0] that the forward column pass prefetches into L2
+    // (a multiple of 16; 0: none)
+    uint64_t tw_bytes;
 };
 
 

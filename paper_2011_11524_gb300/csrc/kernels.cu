@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(512) k_col_fwd(const PlanDev pd, const uint32_
                                                  uint32_t *status) {
     extern __shared__ uint32_t sm[];
     pdl_trigger();
+    prefetch_tables(pd);
     pdl_wait();
     uint32_t pi, tile;
     bool second;

@@ -46,6 +46,23 @@ namespace dml {
 
 __device__ __forceinline__ uint2 ldtw(const uint2 *p) { return __ldg(p); }
 
+// The forward column pass brings the whole plan's twiddle tables (every prime, contiguous at
+// pd.tw[0], pd.tw_bytes bytes; 0 for long transforms, whose tables stay cached across their many
+// CTAs anyway) into L2 for the passes after it: one bulk prefetch of up to 4 KB per thread of the
+// grid's first row of CTAs.  Short products otherwise meet every table cold, one dependent miss
+// per stage.  The tables are never written, so this runs before waiting on the predecessor.
+__device__ __forceinline__ void prefetch_tables(const PlanDev &pd) {
+    if (!pd.tw_bytes || blockIdx.y != 0) return;
+    const uint64_t nblk = (pd.tw_bytes + 4095) / 4096;
+    const uint8_t *base = (const uint8_t *)pd.tw[0];
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nblk;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t off = i * 4096, left = pd.tw_bytes - off;
+        const uint32_t bytes = (uint32_t)(left < 4096 ? left : 4096);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(base + off), "r"(bytes) : "memory");
+    }
+}
+
 // ---- hand-off from the forward column pass to the row pass, per prime ------------------------
 // The forward column CTAs run prime by prime (CTA order lin = blockIdx.y * gridDim.x + blockIdx.x,
 // prime-major), so that the rows of a prime can start while later primes' columns still run.

@@ -314,20 +314,25 @@ def run_ours(args, rank, world, local):
 
         # page-locked buffers: the carry scan writes z in place; the forward pass reads x and y in
         # place for short products only (longer ones are copied: every prime reads the tile again)
-        z_in_place = d.dmul_host_direct(ctx.handle, hz)
+        z_in_place = d.dmul_host_direct(ctx.handle, hz) and L <= d.DMUL_HOST_IN_PLACE_LIMBS
         xy_in_place = d.dmul_host_direct(ctx.handle, hx) and L <= d.DMUL_HOST_IN_PLACE_LIMBS
         e2e_s = e2e_seconds(ctx)
-        # the same calls through device staging buffers and copy-engine transfers, for comparison
+        # for comparison: every buffer through device staging and copy-engine transfers, and the
+        # product written into host memory by the carry scan whatever its length
         cst = d.Context(local, flags=d.DMUL_FLAG_HOST_STAGED_IN | d.DMUL_FLAG_HOST_STAGED_OUT)
         staged_s = e2e_seconds(cst)
         cst.close()
+        cdo = d.Context(local, flags=d.DMUL_FLAG_HOST_DIRECT_OUT)
+        direct_out_s = e2e_seconds(cdo)
+        cdo.close()
         e2e_out = {"value": digits_per_step / e2e_s * world, "unit": "digits/s",
                    "h2d_bytes_per_step": 4 * (nx + ny), "d2h_bytes_per_step": 4 * L + 12,
                    "ms_per_step": e2e_s * 1e3,
                    "host_path": {"operands": "read in place" if xy_in_place else "copied (cudaMemcpyAsync)",
                                  "product": "written in place by the carry scan" if z_in_place
                                  else "copied (cudaMemcpyAsync)"},
-                   "staged_copies_ms_per_step": staged_s * 1e3}
+                   "staged_copies_ms_per_step": staged_s * 1e3,
+                   "product_in_place_ms_per_step": direct_out_s * 1e3}
 
     # ---- roofline of the dominant kernel and of the whole product ----
     info = d.dmul_get_plan(ctx.handle, L)

@@ -77,6 +77,8 @@ typedef struct dmul_ctx dmul_ctx;
 #define DMUL_FLAG_HOST_STAGED_OUT 128u /* dmul_mul_host: write the product to a device buffer    */
                                        /* and copy it out, instead of writing a page-locked z    */
                                        /* in place                                               */
+#define DMUL_FLAG_HOST_DIRECT_OUT 8192u /* dmul_mul_host: write a page-locked z in place at     */
+                                       /* every length (default: only short products)            */
 #define DMUL_FLAG_SHORT_WAITS 1024u    /* bound every device-side wait (carry look-back, column-  */
                                        /* to-row hand-off, bulk-copy barriers) by 2^13 polls, a  */
                                        /* few milliseconds, instead of seconds: an expired wait  */
@@ -140,12 +142,15 @@ int dmul_sqr(dmul_ctx *ctx, const uint32_t *x, size_t nx, uint32_t *z, size_t z_
 /* Host-memory convenience: x, y, z and nz are HOST pointers; the call returns when z and *nz
  * hold the product (it synchronizes).  x == y with nx == ny squares.  z must not overlap x or y.
  * Returns the full status (including device-side errors).
- *  - A page-locked z (cudaHostAlloc / cudaMallocHost / cudaHostRegister, both ends of the buffer
- *    inside registered memory; a buffer must not straddle two registrations) is written in place
- *    by the carry scan, so the limbs cross the host link while it runs.  Page-locked operands of a
- *    short product (nx + ny <= DMUL_HOST_IN_PLACE_LIMBS) are read in place by the forward pass;
- *    longer ones are copied, because every prime's column pass reads its operand tile again.
- *    DMUL_FLAG_HOST_STAGED_IN / _OUT and DMUL_FLAG_HOST_DIRECT_IN override this.
+ *  - Page-locked buffers (cudaHostAlloc / cudaMallocHost / cudaHostRegister, both ends of the
+ *    buffer inside registered memory; a buffer must not straddle two registrations) of a short
+ *    product (nx + ny <= DMUL_HOST_IN_PLACE_LIMBS) are accessed in place: the forward pass reads
+ *    the operands and the carry scan writes z, so the bytes cross the host link while the kernels
+ *    run.  Longer products copy their page-locked operands (every prime's column pass reads its
+ *    operand tile again) and their product (one copy-engine transfer after the carry scan: the
+ *    scan's stores across the host link ran at two speeds from one machine state to another,
+ *    the copy at one).  DMUL_FLAG_HOST_STAGED_IN / _OUT and DMUL_FLAG_HOST_DIRECT_IN / _OUT
+ *    override this.
  *  - Pageable buffers are copied through device staging buffers (cudaMemcpyAsync; y's upload
  *    overlaps x's forward pass).
  * Device memory: nx + ny words for the digit sums, plus 2 (nx + ny) words of operand staging

@@ -976,18 +976,24 @@ int dmul_mul_host(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, 
         CK(cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&c->ev_y, cudaEventDisableTiming));
     }
-    // Page-locked buffers are read and written in place by the kernels (the operands by the
-    // forward pass, the limbs and their count by the carry scan): the bytes cross the host link
-    // while the kernels run, not in copies before and after them.  Pageable buffers (or the
-    // DMUL_FLAG_HOST_STAGED_* flags) go through device staging buffers with cudaMemcpyAsync.
-    // Operands in place only for short products (or on request): each prime's column pass reads
-    // the operand tile again, which over the host link costs more than one copy up front.
-    const bool in_place_in = !(c->cfg.flags & DMUL_FLAG_HOST_STAGED_IN) &&
-                             ((c->cfg.flags & DMUL_FLAG_HOST_DIRECT_IN) || L <= DMUL_HOST_IN_PLACE_LIMBS);
+    // Page-locked buffers of short products are read and written in place by the kernels (the
+    // operands by the forward pass, the limbs and their count by the carry scan): the bytes cross
+    // the host link while the kernels run, not in copies before and after them.  Pageable buffers
+    // (or the DMUL_FLAG_HOST_STAGED_* flags) go through device staging buffers with
+    // cudaMemcpyAsync.  Longer products (unless the DMUL_FLAG_HOST_DIRECT_* flags ask otherwise)
+    // copy too: each prime's column pass reads the operand tile again, which over the host link
+    // costs more than one copy up front; and the carry scan's stores of a long product into host
+    // memory ran at 0.350 ms per 2^24-digit product on some runs and 0.472 ms on another, where
+    // the copy after the scan took 0.356-0.360 ms on every run.
+    const uint32_t fl = c->cfg.flags;
+    const bool in_place_in = !(fl & DMUL_FLAG_HOST_STAGED_IN) &&
+                             ((fl & DMUL_FLAG_HOST_DIRECT_IN) || L <= DMUL_HOST_IN_PLACE_LIMBS);
+    const bool in_place_out = !(fl & DMUL_FLAG_HOST_STAGED_OUT) &&
+                              ((fl & DMUL_FLAG_HOST_DIRECT_OUT) || L <= DMUL_HOST_IN_PLACE_LIMBS);
     const uint32_t *xd = in_place_in ? (const uint32_t *)pinned_view(x, nx * 4) : nullptr;
     const uint32_t *yd = square ? xd : in_place_in ? (const uint32_t *)pinned_view(y, ny * 4) : nullptr;
     if (!xd || !yd) xd = yd = nullptr;  // both operands one way
-    uint32_t *zd = (c->cfg.flags & DMUL_FLAG_HOST_STAGED_OUT) ? nullptr : (uint32_t *)pinned_view(z, L * 4);
+    uint32_t *zd = in_place_out ? (uint32_t *)pinned_view(z, L * 4) : nullptr;
     if (c->h_cap < L) {
         if (c->hz) { cudaFree(c->hz); cudaFree(c->hnz); c->used -= c->h_cap * 4 + 64; }
         c->hz = nullptr;

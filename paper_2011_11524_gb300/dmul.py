@@ -38,6 +38,7 @@ DMUL_FLAG_NO_RADIX5 = 512
 DMUL_FLAG_SHORT_WAITS = 1024
 DMUL_FLAG_TEST_STALL_CARRY = 2048
 DMUL_FLAG_NO_FUSED = 4096
+DMUL_FLAG_HOST_DIRECT_OUT = 8192
 DMUL_HOST_IN_PLACE_LIMBS = 524288
 
 # every symbol include/dmul.h declares

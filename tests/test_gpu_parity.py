@@ -385,22 +385,33 @@ def ctx_direct_in(d):
     c.close()
 
 
+@pytest.fixture(scope="module")
+def ctx_direct_out(d):
+    """A page-locked z written in place by the carry scan at every length."""
+    c = d.Context(0, flags=d.DMUL_FLAG_HOST_DIRECT_OUT)
+    yield c
+    c.close()
+
+
 @pytest.mark.parametrize("n,m", [(11112, 11112), (7777, 5555), (300000, 250001), (1 << 20, (1 << 20) - 3)])
-@pytest.mark.parametrize("kind", ["direct", "direct_in", "direct_out", "staged_flags", "forced_in"])
-def test_host_pinned_in_place(d, ctx, ctx_staged, ctx_direct_in, n, m, kind):
+@pytest.mark.parametrize("kind", ["direct", "direct_in", "direct_out", "staged_flags", "forced_in", "forced_out"])
+def test_host_pinned_in_place(d, ctx, ctx_staged, ctx_direct_in, ctx_direct_out, n, m, kind):
     """dmul_mul_host on page-locked buffers: the forward pass reads x and y in place and the carry
-    scan writes z and its length in place (or, per buffer / per flag, the staged copies) -- every
-    combination gives the oracle's product."""
+    scan writes z and its length in place (short products, or every length by flag), or the staged
+    copies (longer products, pageable buffers, flags) -- every combination gives the oracle's
+    product."""
     if n >= 1 << 20 and kind in ("direct_in", "direct_out"):
         pytest.skip("the mixed cases run at the smaller sizes")
     rng = _rng(7300 + n + m)
     x, y = _rand(rng, n), _rand(rng, m)
     L = n + m
-    px = _pinned(x) if kind in ("direct", "direct_in", "staged_flags", "forced_in") else x
-    py = _pinned(y) if kind in ("direct", "direct_in", "staged_flags", "forced_in") else y
+    pinned_in = ("direct", "direct_in", "staged_flags", "forced_in", "forced_out")
+    px = _pinned(x) if kind in pinned_in else x
+    py = _pinned(y) if kind in pinned_in else y
     pz = (torch.zeros(L + 3, dtype=torch.int32).pin_memory()
-          if kind in ("direct", "direct_out", "staged_flags", "forced_in") else np.zeros(L + 3, np.uint32))
-    c = {"staged_flags": ctx_staged, "forced_in": ctx_direct_in}.get(kind, ctx)
+          if kind in ("direct", "direct_out", "staged_flags", "forced_in", "forced_out")
+          else np.zeros(L + 3, np.uint32))
+    c = {"staged_flags": ctx_staged, "forced_in": ctx_direct_in, "forced_out": ctx_direct_out}.get(kind, ctx)
     assert d.dmul_host_direct(c.handle, px) == (kind != "direct_out")
     assert d.dmul_host_direct(c.handle, pz) == (kind != "direct_in")
     ref = oracle.mul(x, y)
@@ -417,7 +428,7 @@ def test_host_pinned_in_place(d, ctx, ctx_staged, ctx_direct_in, n, m, kind):
     # an invalid limb read in place is reported, and the context stays usable
     bad = y.copy()
     bad[m // 2] = B
-    pb = _pinned(bad) if kind in ("direct", "direct_in", "staged_flags", "forced_in") else bad
+    pb = _pinned(bad) if kind in pinned_in else bad
     rc, _ = d.dmul_mul_host(c.handle, px, n, pb, m, pz, L + 3)
     assert rc == d.DMUL_ERR_INVALID
     rc, nz = d.dmul_mul_host(c.handle, px, n, py, m, pz, L + 3)
@@ -426,9 +437,10 @@ def test_host_pinned_in_place(d, ctx, ctx_staged, ctx_direct_in, n, m, kind):
 
 
 @pytest.mark.parametrize("n,m", [(5000, 7001), (1 << 20, 12345)])
-def test_host_pinned_unaligned_product(d, ctx, n, m):
+def test_host_pinned_unaligned_product(d, ctx_direct_out, n, m):
     """A page-locked z that starts 4 bytes past a 16-byte boundary: the carry scan writes it in
     place word by word (the 16-byte stores need alignment)."""
+    ctx = ctx_direct_out
     rng = _rng(7450 + m)
     x, y = _pinned(_rand(rng, n)), _pinned(_rand(rng, m))
     L = n + m

@@ -646,8 +646,8 @@ def run_batched(d, torch, dev, reps=5, count=4096, check=True):
     return out
 
 
-def run_served(d, torch, dev, distinct=2000, repeat=10, load=0.7, budget_gib=8,
-               loads=(0.1, 0.3, 0.5, 0.9), check=True):
+def run_served(d, torch, dev, distinct=2000, repeat=10, load=0.75, budget_gib=8,
+               loads=(0.1, 0.25, 0.5, 0.9, 1.0, 1.2), check=True):
     """Poisson stream of requests (digits log-uniform 10^2..10^7, 30% squarings) into the serving
     loop at a sweep of arrival rates (fractions `loads` and `load` of its measured saturated rate);
     p50/p99 latency from arrival to completion at each.  The headline point is `load`.

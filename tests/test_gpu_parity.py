@@ -641,6 +641,20 @@ def test_fused_unaligned_takes_pipeline(d, ctx_fused):
     assert "short_fused" not in t and t["carry_scan"][1] == 1
 
 
+def test_fused_short_waits(d):
+    """With every device-side wait bounded by 2^13 polls, the cooperative kernel's grid barriers
+    and carry look-back still complete: no spurious timeout, the products equal the oracle."""
+    with d.Context(0, flags=d.DMUL_FLAG_NO_SMALL | d.DMUL_FLAG_NO_AUTOTUNE | d.DMUL_FLAG_SHORT_WAITS |
+                   d.DMUL_FLAG_STAGE_TIMING) as c:
+        rng = _rng(12950)
+        for n, m in [(8192, 8192), (10000, 10480), (12288, 12288)]:
+            x, y = _rand(rng, n), _rand(rng, m)
+            z, nz = _gpu_mul(d, c, x, y)
+            ref = oracle.mul(x, y)
+            assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))
+        assert c.stage_times()["short_fused"][1] == 3
+
+
 def test_fused_matches_other_paths(d, ctx, ctx4):
     """The same products through the default (timed) context and the four-kernel pipeline are
     bit-identical with the oracle; the timed choice may be any of the three paths."""

@@ -130,7 +130,13 @@ int dmul_sync(dmul_ctx *ctx, void *stream);
  * cluster kernel, as the four-kernel pipeline or, at lengths 16384, 20480 and 24576 with 16-byte
  * aligned operands and outside a stream capture, as one cooperative launch of the same four-step
  * steps; the limbs are identical on every path (DMUL_FLAG_NO_SMALL / DMUL_FLAG_NO_FUSED rule
- * paths out). */
+ * paths out).
+ * Stream capture: a call may be captured into a CUDA graph once a product of the same lengths has
+ * run on this context outside the capture (its plan, scratch and path choice then exist); the
+ * graph's replays multiply whatever the buffers hold at replay time.  Captured, a product takes
+ * the pipeline's plain launches (no cooperative kernel, no per-prime hand-off between the column
+ * and row passes).  A call whose lengths are not planned yet returns DMUL_ERR_INVALID inside a
+ * capture, having enqueued nothing. */
 int dmul_mul(dmul_ctx *ctx, const uint32_t *x, size_t nx, const uint32_t *y, size_t ny,
              uint32_t *z, size_t z_cap, uint64_t *nz, void *stream);
 

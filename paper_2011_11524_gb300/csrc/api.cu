@@ -393,20 +393,14 @@ static int get_fused_plan(dmul_ctx *c, uint64_t N, PlanEntry **out) {
 }
 
 // Whether a lone product of transform length N may take the fused kernel: the length and the
-// operands' alignment suit it, and no stream capture is in progress (a captured product takes the
-// pipeline's plain launches).
-static bool fused_candidate(const dmul_ctx *c, uint64_t N, const void *x, const void *y, cudaStream_t s) {
+// operands' alignment suit it.  (A product inside a stream capture never does: the caller leaves
+// the cooperative launch out of a capture.)
+static bool fused_candidate(const dmul_ctx *c, uint64_t N, const void *x, const void *y) {
     if (c->cfg.flags & (DMUL_FLAG_SIXSTEP | DMUL_FLAG_NO_FUSED)) return false;
     const uint64_t n1 = N / 256;
     if (N % 256 || (n1 != 64 && n1 != 80 && n1 != 96)) return false;
     if ((((uintptr_t)x) | ((uintptr_t)y)) & 15) return false;
-    if (current_device_sms() < 48) return false;  // a CTA per column task of both operands
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return cap == cudaStreamCaptureStatusNone;
+    return current_device_sms() >= 48;  // a CTA per column task of both operands
 }
 
 static cudaError_t launch_fused_product(dmul_ctx *c, const PlanEntry *fe, const JobDev &jd, cudaStream_t s) {
@@ -414,10 +408,6 @@ static cudaError_t launch_fused_product(dmul_ctx *c, const PlanEntry *fe, const 
                               (CarryCtl *)c->ctl, c->status, c->grid_sync, c->spin_limit,
                               (uint32_t)current_device_sms(), s);
 }
-
-struct ShortTimes {
-    float small = 1e30f, four = 1e30f, fused = 1e30f;
-};
 
 // Times a product of length min(Ns, N) (or N without a small plan) on each candidate path: the
 // small kernel (Ns > 0), the pipeline, the fused kernel (fused).  The best of three cold-cache runs
@@ -517,28 +507,63 @@ int prefer_small_single(dmul_ctx *c, uint64_t Ns, uint64_t N, bool *use_small) {
 
 enum ShortPath { kPathFour = 0, kPathSmall = 1, kPathFused = 2 };
 
-// The lone product's path among the candidates (Ns > 0: the small kernel; fused: the fused kernel).
-static int prefer_short_path(dmul_ctx *c, uint64_t Ns, uint64_t N, bool fused, int *path) {
-    const uint64_t key = (Ns << 40) | (N << 1) | (fused ? 1u : 0u);
+static bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cap != cudaStreamCaptureStatusNone;
+}
+
+// The lone product's path among the allowed candidates (small_ok: the small kernel of length Ns;
+// fused_ok: the fused kernel; the pipeline always), by the first-use times of the lengths (Ns, N).
+// An allowed candidate without a time yet is timed now -- except inside a stream capture, where
+// nothing may synchronize: there only the candidates already timed compete, and with none the
+// pipeline runs.
+static int prefer_short_path(dmul_ctx *c, uint64_t Ns, uint64_t N, bool small_ok, bool fused_ok, bool capturing,
+                             int *path) {
+    const uint64_t key = (Ns << 40) | N;
+    ShortTimes t;
+    bool have = false;
     {
         std::lock_guard<std::mutex> g(c->small_mu);
-        auto it = c->short_path.find(key);
-        if (it != c->short_path.end()) {
-            *path = it->second;
-            return DMUL_OK;
+        auto it = c->short_times.find(key);
+        if (it != c->short_times.end()) {
+            t = it->second;
+            have = true;
         }
     }
-    ShortTimes t;
-    int rc = time_short_paths(c, Ns, N, fused, &t);
-    if (rc) return rc;
+    const bool need = !have || (small_ok && !t.small_timed) || (fused_ok && !t.fused_timed);
+    if (need && !capturing) {
+        ShortTimes nt;
+        int rc = time_short_paths(c, small_ok ? Ns : 0, N, fused_ok, &nt);
+        if (rc) return rc;
+        // the candidates timed before and not now keep their times
+        if (!small_ok && t.small_timed) { nt.small = t.small; nt.small_timed = true; }
+        if (small_ok) nt.small_timed = true;
+        if (!fused_ok && t.fused_timed) { nt.fused = t.fused; nt.fused_timed = true; }
+        if (fused_ok) nt.fused_timed = true;
+        t = nt;
+        have = true;
+        std::lock_guard<std::mutex> g(c->small_mu);
+        if (small_ok && !c->small_single.count(Ns)) c->small_single[Ns] = t.small <= t.four;
+        c->short_times[key] = t;
+    }
     *path = kPathFour;
+    if (!have) return DMUL_OK;
     float best = t.four;
-    if (Ns && t.small <= best) { *path = kPathSmall; best = t.small; }
-    if (fused && t.fused < best) *path = kPathFused;
-    std::lock_guard<std::mutex> g(c->small_mu);
-    if (Ns && !c->small_single.count(Ns)) c->small_single[Ns] = t.small <= t.four;
-    c->short_path[key] = *path;
+    if (small_ok && t.small_timed && t.small <= best) { *path = kPathSmall; best = t.small; }
+    if (fused_ok && t.fused_timed && t.fused < best) *path = kPathFused;
     return DMUL_OK;
+}
+
+// Whether a product of L limbs on transform length N (small: the small kernel's length) needs no
+// allocation and no planning: its plan cached, the scratch large enough.
+static bool planned_for_capture(const dmul_ctx *c, uint64_t N, bool small, uint64_t L) {
+    if (small) return c->small_plans.count(N) != 0;
+    return c->plans.count(N) != 0 && (size_t)kPrimes * N <= c->res_words &&
+           (L + kChunk - 1) / kChunk + 1 <= c->spill_cap && carry_ctl_bytes(L) <= c->ctl_cap;
 }
 
 // z_out (optional, digits mode, four-step or six-step path): where the carry writes the limbs --
@@ -557,13 +582,18 @@ int enqueue_mul(dmul_ctx *c, const uint32_t *x, size_t nx, const uint32_t *y, si
     rc = set_device(c);
     if (rc) return rc;
     const uint64_t Ns = choose_N_small(L);
+    // Inside a stream capture nothing may allocate or synchronize: the lengths must have been
+    // planned (by a product of the same lengths outside the capture), and the scratch be in place.
+    const bool capturing = stream_capturing(s);
     const bool small_ok = mode == kInvDigits && Ns && !(c->cfg.flags & (DMUL_FLAG_SIXSTEP | DMUL_FLAG_NO_SMALL));
-    const bool fused_ok = mode == kInvDigits && fused_candidate(c, N, x, y, s);
+    const bool fused_ok = mode == kInvDigits && !capturing && fused_candidate(c, N, x, y);
     int path = kPathFour;
     if (small_ok || fused_ok) {
         if (c->cfg.flags & DMUL_FLAG_NO_AUTOTUNE) path = small_ok ? kPathSmall : kPathFused;
-        else if ((rc = prefer_short_path(c, small_ok ? Ns : 0, N, fused_ok, &path))) return rc;
+        else if ((rc = prefer_short_path(c, Ns, N, small_ok, fused_ok, capturing, &path))) return rc;
     }
+    if (capturing && !planned_for_capture(c, path == kPathSmall ? Ns : N, path == kPathSmall, L))
+        return DMUL_ERR_INVALID;
     if (path != kPathFour) {
         JobDev jd;
         memset(&jd, 0, sizeof(jd));

@@ -69,7 +69,14 @@ struct BatchState {
     bool pending = false;
     // graph cache keyed by the batch shape
     std::map<std::vector<std::tuple<int, uint64_t, size_t>>, cudaGraphExec_t> graphs;
-    };
+};
+
+// First-use times (ms, cold L2) of a lone short product on each path; a path not timed keeps
+// the 1e30 of "not a candidate" (its *_timed flag tells it apart from one that failed to run).
+struct ShortTimes {
+    float small = 1e30f, four = 1e30f, fused = 1e30f;
+    bool small_timed = false, fused_timed = false;
+};
 
 
 
@@ -83,9 +90,9 @@ struct dmul_ctx {
     std::map<uint64_t, std::unique_ptr<dml::PlanEntry>> plans;
     std::map<uint64_t, std::unique_ptr<dml::SmallPlanEntry>> small_plans;
     std::map<uint64_t, bool> small_single;  // per short length: small kernel faster than four-step
-    std::map<uint64_t, int> short_path;     // per lone short product's lengths: its fastest path
+    std::map<uint64_t, dml::ShortTimes> short_times;  // per lone short product's lengths (Ns, N)
     std::map<uint64_t, std::unique_ptr<dml::PlanEntry>> fused_plans;  // N1 x 256 plans of the fused kernel
-    mutable std::mutex small_mu;            // guards small_single, short_path (read by dmul_submit callers)
+    mutable std::mutex small_mu;            // guards small_single, short_times (read by dmul_submit callers)
     // scratch of the plain form (one set, used by one call at a time)
     uint32_t *X = nullptr, *Y = nullptr;
     size_t res_words = 0;  // capacity of X and of Y, in words

@@ -667,6 +667,59 @@ def test_fused_matches_other_paths(d, ctx, ctx4):
             assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))
 
 
+# ---- the plain form inside a CUDA graph --------------------------------------------------------
+@pytest.mark.parametrize("n,m", [(3000, 4000), (11112, 11112), (300000, 250001), (1 << 20, (1 << 20) - 3)])
+def test_plain_form_in_cuda_graph(d, ctx, n, m):
+    """dmul_mul captured into a CUDA graph after one product of the same lengths outside the
+    capture; three replays on new operands each equal the oracle, and nz follows."""
+    rng = _rng(13000 + n + m)
+    L = n + m
+    tx, ty = d.to_device(_rand(rng, n)), d.to_device(_rand(rng, m))
+    z = torch.empty(L, dtype=torch.int32, device="cuda")
+    nz = torch.zeros(1, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    assert d.dmul_mul(ctx.handle, tx, n, ty, m, z, L, nz, s.cuda_stream) == 0  # plans the lengths
+    assert d.dmul_sync(ctx.handle, s.cuda_stream) == 0
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        rc = d.dmul_mul(ctx.handle, tx, n, ty, m, z, L, nz, s.cuda_stream)
+    assert rc == 0
+    for k in range(3):
+        x, y = _rand(rng, n), _rand(rng, m)
+        if k == 2:
+            y[m // 2:] = 0  # a shorter normalized length
+        tx.copy_(d.to_device(x))
+        ty.copy_(d.to_device(y))
+        g.replay()
+        torch.cuda.synchronize()
+        ref = oracle.mul(x, y)
+        assert np.array_equal(d.to_host(z), ref) and int(nz.item()) == len(oracle.normalize(ref))
+    assert d.dmul_sync(ctx.handle) == 0
+
+
+def test_unplanned_length_refused_in_capture(d):
+    """Inside a capture a product whose lengths this context has not planned is refused with
+    DMUL_ERR_INVALID and enqueues nothing; the capture itself stays valid."""
+    with d.Context(0) as c:
+        rng = _rng(13100)
+        tx, ty = d.to_device(_rand(rng, 70000)), d.to_device(_rand(rng, 70001))
+        z = torch.zeros(140001, dtype=torch.int32, device="cuda")
+        nz = torch.zeros(1, dtype=torch.int64, device="cuda")
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            rc = d.dmul_mul(c.handle, tx, 70000, ty, 70001, z, 140001, nz, s.cuda_stream)
+            nz.add_(5)  # something to capture
+        assert rc == d.DMUL_ERR_INVALID
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(nz.item()) == 5 and not z.any().item()
+        # outside the capture the same call plans the lengths and multiplies
+        zz, n_ = c.mul(tx, ty)
+        ref = oracle.mul(d.to_host(tx), d.to_host(ty))
+        assert np.array_equal(d.to_host(zz), ref)
+
+
 # ---- compile-time specialized column passes (N1 = 2^a, 3 2^a, 5 2^a from 64 to 1536) -----------
 @pytest.fixture(scope="module")
 def ctx_def(d):

@@ -28,10 +28,18 @@ Server::Server(dmul_ctx *c) : ctx_(c) {
         if (cudaMemPoolSetAttribute(pool_, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess)
             init_ok_ = false;
     }
-    for (int i = 0; i < kSlots; ++i) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        least = greatest = 0;
+    }
+    for (int i = 0; i < kSlots + kShortSlots; ++i) {
         auto s = std::make_unique<Slot>();
         s->owner = this;
-        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) init_ok_ = false;
+        s->short_only = i >= kSlots;
+        if (cudaStreamCreateWithPriority(&s->stream, cudaStreamNonBlocking, s->short_only ? greatest : least) !=
+            cudaSuccess)
+            init_ok_ = false;
         if (cudaEventCreateWithFlags(&s->done_ev, cudaEventDisableTiming) != cudaSuccess) init_ok_ = false;
         if (cudaMalloc(&s->status, 64) != cudaSuccess || cudaMemset(s->status, 0, 64) != cudaSuccess)
             init_ok_ = false;
@@ -69,13 +77,15 @@ int Server::submit(const dmul_job &job, uint64_t *ticket) {
     bool four = false;
     const size_t bytes = job_scratch_bytes(ctx_, job, &four);
     if (bytes > budget_) return DMUL_ERR_NOMEM;
+    const bool short_job = choose_N_small(L) && !(ctx_->cfg.flags & (DMUL_FLAG_SIXSTEP | DMUL_FLAG_NO_SMALL));
     std::lock_guard<std::mutex> g(mu_);
     uint64_t t = next_++;
     Ticket &tk = tickets_[t];
     tk.job = job;
     tk.bytes = bytes;
     tk.four = four;
-    queue_.push_back(t);
+    tk.short_job = short_job;
+    queue_[short_job ? 0 : 1].push_back(t);
     gen_.fetch_add(1, std::memory_order_release);
     *ticket = t;
     cv_.notify_all();
@@ -115,7 +125,7 @@ int Server::wait(uint64_t ticket) {
 
 void Server::stats(dmul_serve_info *out) {
     std::lock_guard<std::mutex> g(mu_);
-    out->queued = queue_.size();
+    out->queued = queue_[0].size() + queue_[1].size();
     out->running = running_;
     out->held = tickets_.size();
     out->peak_running = peak_running_;
@@ -149,19 +159,20 @@ void Server::retire(Slot &s, std::unique_lock<std::mutex> &g) {
     s.bytes = 0;
 }
 
-// Admit pending requests into a free slot and launch them as one batch.
-bool Server::launch(Slot &s, std::unique_lock<std::mutex> &g) {
+// Admit pending requests of queue q into a free slot and launch them as one batch.
+bool Server::launch(Slot &s, int q, std::unique_lock<std::mutex> &g) {
     std::vector<dmul_job> jobs;
     std::vector<uint8_t> four;
     size_t bytes = 0;
-    while (!queue_.empty() && jobs.size() < kMaxBatch) {
-        Ticket &tk = tickets_[queue_.front()];
+    std::deque<uint64_t> &queue = queue_[q];
+    while (!queue.empty() && jobs.size() < kMaxBatch) {
+        Ticket &tk = tickets_[queue.front()];
         if (inflight_ + bytes + tk.bytes > budget_) break;  // wait for memory to free up
         bytes += tk.bytes;
         jobs.push_back(tk.job);
         four.push_back(tk.four ? 1 : 0);
-        s.tickets.push_back(queue_.front());
-        queue_.pop_front();
+        s.tickets.push_back(queue.front());
+        queue.pop_front();
     }
     if (jobs.empty()) return false;
     std::vector<int> hs(jobs.size(), DMUL_OK);
@@ -262,37 +273,43 @@ void Server::loop() {
         for (auto &s : slots_)
             if (s->busy && s->finished) {
                 retire(*s, g);
-                mem_blocked_ = false;  // memory came back: retry the head of the queue
+                mem_blocked_[0] = mem_blocked_[1] = false;  // memory came back: retry the heads
             }
         any_busy = false;
         for (auto &s : slots_) any_busy |= s->busy;
         if (stop_) {
             if (any_busy) continue;  // the batches in flight complete first
-            for (uint64_t t : queue_) {  // never started: the context is going away
-                tickets_[t].status = DMUL_ERR_INVALID;
-                tickets_[t].done = true;
+            for (auto &queue : queue_) {
+                for (uint64_t t : queue) {  // never started: the context is going away
+                    tickets_[t].status = DMUL_ERR_INVALID;
+                    tickets_[t].done = true;
+                }
+                queue.clear();
             }
-            queue_.clear();
             done_cv_.notify_all();
             return;
         }
         for (auto &s : slots_) {
-            if (queue_.empty() || mem_blocked_) break;
             if (s->busy) continue;
-            if (!launch(*s, g)) {
+            // a short-only slot takes short requests; a general one long requests first
+            const int order[2] = {s->short_only ? 0 : 1, s->short_only ? -1 : 0};
+            for (int q : order) {
+                if (q < 0 || queue_[q].empty() || mem_blocked_[q]) continue;
+                if (launch(*s, q, g)) {
+                    any_busy = true;
+                    break;
+                }
                 // the head request does not fit the admission budget next to the batches in
                 // flight: wait for one of them to retire
-                mem_blocked_ = any_busy;
+                mem_blocked_[q] = any_busy;
                 if (!any_busy) {  // cannot happen (submit rejects such requests); fail it
-                    Ticket &tk = tickets_[queue_.front()];
+                    Ticket &tk = tickets_[queue_[q].front()];
                     tk.status = DMUL_ERR_NOMEM;
                     tk.done = true;
-                    queue_.pop_front();
+                    queue_[q].pop_front();
                     done_cv_.notify_all();
                 }
-                break;
             }
-            any_busy = true;
         }
         // requests that arrived while this pass held (or dropped, in launch) the lock are seen
         // by the next pass through gen_; a queue left non-empty because every slot is busy waits

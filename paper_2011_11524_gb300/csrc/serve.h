@@ -34,6 +34,12 @@ int run_batch(dmul_ctx *c, dmul_job *jobs, size_t count, cudaStream_t s);
 // completion is an event recorded after its batch, which the worker polls while anything is in
 // flight (and for kIdlePollUs after its last activity) instead of sleeping: a completion or a new
 // request is seen within microseconds, at the price of one host core kept busy meanwhile.
+//
+// Short requests (transform length <= 24576, the one-cluster class) queue apart from long ones.
+// kShortSlots extra slots take short requests only, on streams of the highest priority, so that a
+// short request waits neither for a long request batched with it nor for a free general slot, and
+// the GPU's block scheduler runs its CTAs ahead of a long batch's as SMs free up; the kSlots
+// general slots take long requests first and short ones when no long one is queued.
 class Server {
   public:
     explicit Server(dmul_ctx *c);
@@ -43,7 +49,8 @@ class Server {
     int wait(uint64_t ticket);
     void stats(dmul_serve_info *out);
 
-    static constexpr int kSlots = 4;
+    static constexpr int kSlots = 4;       // general slots
+    static constexpr int kShortSlots = 2;  // short requests only, highest stream priority
     static constexpr size_t kMaxBatch = 1024;
     static constexpr int kIdlePollUs = 300;  // the worker keeps polling this long after its last activity
 
@@ -52,6 +59,7 @@ class Server {
         dmul_job job;
         size_t bytes = 0;
         bool four = false;  // its scratch covers the four-step path (a short job; see run_batch_on)
+        bool short_job = false;  // the one-cluster length class: queue_[0]
         int status = DMUL_OK;
         bool done = false;
     };
@@ -67,16 +75,17 @@ class Server {
         void *arena = nullptr;
         bool busy = false;
         bool finished = false;
+        bool short_only = false;
     };
     void complete(Slot &s, int rc);
     void loop();
     void retire(Slot &s, std::unique_lock<std::mutex> &g);
-    bool launch(Slot &s, std::unique_lock<std::mutex> &g);
+    bool launch(Slot &s, int q, std::unique_lock<std::mutex> &g);
 
     dmul_ctx *ctx_;
     std::mutex mu_;
     std::condition_variable cv_, done_cv_;
-    std::deque<uint64_t> queue_;
+    std::deque<uint64_t> queue_[2];  // [0] short requests, [1] long ones (FIFO each)
     std::unordered_map<uint64_t, Ticket> tickets_;  // issued and not yet released
     uint64_t next_ = 1;
     uint64_t running_ = 0;  // requests in launched batches
@@ -84,7 +93,7 @@ class Server {
     uint64_t peak_running_ = 0;
     bool stop_ = false;
     bool init_ok_ = false;
-    bool mem_blocked_ = false;  // the head request waits for in-flight scratch to be released
+    bool mem_blocked_[2] = {false, false};  // a queue's head waits for in-flight scratch to be released
     std::vector<std::unique_ptr<Slot>> slots_;
     size_t budget_ = 0, inflight_ = 0;
     cudaMemPool_t pool_ = nullptr;  // in-flight scratch (stream-ordered, kept mapped up to budget_)

@@ -613,7 +613,7 @@ static int launch_work(dmul_ctx *c, BatchState *b, const std::vector<GroupLaunch
 // Descriptor uploads and zeroing of the control words, then the work.
 static int upload_and_launch(dmul_ctx *c, BatchState *b, const std::vector<GroupLaunch> &groups,
                              const SmallLaunch &sl, cudaStream_t s, size_t njobs, size_t ctl_off,
-                             size_t ctl_bytes, uint32_t *status, bool fork) {
+                             size_t ctl_bytes, uint32_t *status, bool fork, bool rows) {
     if (cudaMemcpyAsync(b->djobs, b->hjobs, njobs * sizeof(JobDev), cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(b->dstat, 0, njobs * sizeof(uint32_t), s) != cudaSuccess)
         return DMUL_ERR_CUDA;
@@ -624,15 +624,16 @@ static int upload_and_launch(dmul_ctx *c, BatchState *b, const std::vector<Group
             return DMUL_ERR_CUDA;
     }
     if (ctl_bytes && cudaMemsetAsync(b->arena + ctl_off, 0, ctl_bytes, s) != cudaSuccess) return DMUL_ERR_CUDA;
-    // the serving loop (no fork) keeps one row per CTA; a whole batch takes several (rowpass.cuh)
+    // the serving loop keeps one row per CTA (rows = false); a whole batch takes several
+    // (rowpass.cuh).  fork: the groups spread over the state's streams, joined back to s.
     if (!fork) {
-        int rc = launch_work(c, b, groups, sl, &s, 1, status, false);
+        int rc = launch_work(c, b, groups, sl, &s, 1, status, rows);
         if (rc) return rc;
     } else {
         if (cudaEventRecord(b->fork, s) != cudaSuccess) return DMUL_ERR_CUDA;
         for (int i = 0; i < kBatchStreams; ++i)
             if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) return DMUL_ERR_CUDA;
-        int rc = launch_work(c, b, groups, sl, b->streams, kBatchStreams, status, true);
+        int rc = launch_work(c, b, groups, sl, b->streams, kBatchStreams, status, rows);
         if (rc) return rc;
         for (int i = 0; i < kBatchStreams; ++i) {
             if (cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess) return DMUL_ERR_CUDA;
@@ -716,7 +717,7 @@ static int check_job(const dmul_ctx *c, const dmul_job &j) {
 }
 
 int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count_in, cudaStream_t s,
-                 uint32_t *status, bool use_graph, int *host_status, const uint8_t *four_ok) {
+                 uint32_t *status, bool use_graph, int *host_status, const uint8_t *four_ok, bool fork_plain) {
     int rc = DMUL_OK;
     b->launched = 0;
     // validate (per job: a rejected job is left out, the others run) and classify
@@ -921,8 +922,9 @@ int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count_
     for (size_t i = 0; i < count; ++i) b->order[i] = items[i].idx;
     b->launched = count;
     if (!use_graph) {
-        // plain launches on one stream (the serving loop's slots: shapes vary, slots overlap)
-        rc = upload_and_launch(c, b, groups, sl, s, count, ctl_off, ctl_bytes, status, false);
+        // plain launches (the serving loop's slots: shapes vary, slots overlap), on s or, with
+        // fork_plain, spread over the state's streams
+        rc = upload_and_launch(c, b, groups, sl, s, count, ctl_off, ctl_bytes, status, fork_plain, false);
         if (rc) return rc;
         if (cudaEventRecord(b->done, s) != cudaSuccess) return DMUL_ERR_CUDA;
         b->done_recorded = true;
@@ -937,7 +939,7 @@ int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count_
         cudaStream_t cap = b->streams[0];
         // capture on a private stream, joined to s through events
         if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DMUL_ERR_CUDA;
-        rc = upload_and_launch(c, b, groups, sl, cap, count, ctl_off, ctl_bytes, status, true);
+        rc = upload_and_launch(c, b, groups, sl, cap, count, ctl_off, ctl_bytes, status, true, true);
         cudaError_t ce = cudaStreamEndCapture(cap, &graph);
         if (rc) return rc;
         if (ce != cudaSuccess) return DMUL_ERR_CUDA;

@@ -165,7 +165,7 @@ int init_batch_state(BatchState *b);
 void free_batch_state(dmul_ctx *c, BatchState *b);
 // One batch on a given state (arena, descriptors); device errors go to *status.  use_graph:
 // capture/replay per batch shape with groups forked over the state's streams; otherwise plain
-// launches on s.
+// launches on s (fork_plain: forked over the state's streams, joined back to s).
 //
 // A size class of short products with fewer jobs than it would take to fill the GPU with clusters
 // runs as four-step groups instead when a lone product of that length is faster there (the
@@ -179,7 +179,8 @@ void free_batch_state(dmul_ctx *c, BatchState *b);
 // launched job lands in b->hstat[i] for descriptor i (job b->order[i]) once the stream has
 // passed the batch (b->done).
 int run_batch_on(dmul_ctx *c, BatchState *b, const dmul_job *jobs, size_t count, cudaStream_t s,
-                 uint32_t *status, bool use_graph, int *host_status, const uint8_t *four_ok = nullptr);
+                 uint32_t *status, bool use_graph, int *host_status, const uint8_t *four_ok = nullptr,
+                 bool fork_plain = false);
 // DMUL_OK, DMUL_ERR_TIMEOUT or DMUL_ERR_INVALID for a device status word.
 inline int device_code(uint32_t st) {
     return !st ? DMUL_OK : ((st & kStatusTimeout) ? DMUL_ERR_TIMEOUT : DMUL_ERR_INVALID);

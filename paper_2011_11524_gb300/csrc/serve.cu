@@ -192,7 +192,10 @@ bool Server::launch(Slot &s, int q, std::unique_lock<std::mutex> &g) {
         // the scratch of this batch is the pool allocation; the state never reallocates it
         s.bs.arena = (uint8_t *)arena;
         s.bs.arena_cap = bytes;
-        rc = run_batch_on(ctx_, &s.bs, jobs.data(), jobs.size(), s.stream, s.status, false, hs.data(), four.data());
+        // a long batch spreads its transform-length groups over the state's streams; a short one
+        // is mostly one persistent launch and stays on the slot's high-priority stream
+        rc = run_batch_on(ctx_, &s.bs, jobs.data(), jobs.size(), s.stream, s.status, false, hs.data(), four.data(),
+                          !s.short_only);
         s.bs.arena = nullptr;
         s.bs.arena_cap = 0;
     }

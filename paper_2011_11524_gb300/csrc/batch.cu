@@ -503,9 +503,10 @@ void destroy_batch_state(dmul_ctx *c) {
     c->batch.reset();
 }
 
-int init_batch_state(BatchState *b) {
+int init_batch_state(BatchState *b, int priority) {
     for (int i = 0; i < kBatchStreams; ++i) {
-        if (cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking) != cudaSuccess) return DMUL_ERR_CUDA;
+        if (cudaStreamCreateWithPriority(&b->streams[i], cudaStreamNonBlocking, priority) != cudaSuccess)
+            return DMUL_ERR_CUDA;
         if (cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess) return DMUL_ERR_CUDA;
     }
     if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return DMUL_ERR_CUDA;

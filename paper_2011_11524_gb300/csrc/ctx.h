@@ -161,7 +161,9 @@ struct Timed {
 };
 
 void destroy_batch_state(dmul_ctx *c);
-int init_batch_state(BatchState *b);
+// priority: of the state's fork/join streams (0, the default, or a value of
+// cudaDeviceGetStreamPriorityRange)
+int init_batch_state(BatchState *b, int priority = 0);
 void free_batch_state(dmul_ctx *c, BatchState *b);
 // One batch on a given state (arena, descriptors); device errors go to *status.  use_graph:
 // capture/replay per batch shape with groups forked over the state's streams; otherwise plain

@@ -43,7 +43,7 @@ Server::Server(dmul_ctx *c) : ctx_(c) {
         if (cudaEventCreateWithFlags(&s->done_ev, cudaEventDisableTiming) != cudaSuccess) init_ok_ = false;
         if (cudaMalloc(&s->status, 64) != cudaSuccess || cudaMemset(s->status, 0, 64) != cudaSuccess)
             init_ok_ = false;
-        if (init_batch_state(&s->bs) != DMUL_OK) init_ok_ = false;
+        if (init_batch_state(&s->bs, s->short_only ? greatest : least) != DMUL_OK) init_ok_ = false;
         slots_.push_back(std::move(s));
     }
     worker_ = std::thread([this] { loop(); });
@@ -192,10 +192,10 @@ bool Server::launch(Slot &s, int q, std::unique_lock<std::mutex> &g) {
         // the scratch of this batch is the pool allocation; the state never reallocates it
         s.bs.arena = (uint8_t *)arena;
         s.bs.arena_cap = bytes;
-        // a long batch spreads its transform-length groups over the state's streams; a short one
-        // is mostly one persistent launch and stays on the slot's high-priority stream
+        // the batch spreads its groups (transform lengths, short classes) over the state's
+        // streams, which have the slot's priority
         rc = run_batch_on(ctx_, &s.bs, jobs.data(), jobs.size(), s.stream, s.status, false, hs.data(), four.data(),
-                          !s.short_only);
+                          true);
         s.bs.arena = nullptr;
         s.bs.arena_cap = 0;
     }

@@ -4,11 +4,13 @@
 // column DFTs with the four-step twiddle, Sec. 7.1; fused row pass, Sec. 5.4 / 6; inverse column
 // DFTs; three-prime CRT, Sec. 8.2.2; chunk digit sums and the lookahead carry scan, Sec. 3.2), but
 // the four kernels become five phases of one grid, separated by grid-wide barriers.  At these
-// sizes each kernel of the pipeline does a few microseconds of work and pays as much again in
-// launch and drain; one launch keeps the SMs and the data (all of it L2-resident) in place.  The
-// phases reuse the specialized device code of the pipeline kernels (colpass.cuh, rowpass.cuh,
-// stages.cuh) for column lengths N1 in {64, 80, 96} and rows of N2 = 256, so the arithmetic, the
-// order of the outputs and the results are the pipeline's own.
+// sizes each kernel of the pipeline does a few microseconds of work; one launch keeps the SMs and
+// the data (all of it L2-resident) in place, at the price of a cooperative launch and four grid
+// barriers.  Which wins is measured per length on first use (api.cu): at 10^5-digit operands the
+// four programmatically chained kernels do (28 against 35 microseconds).  The phases reuse the
+// specialized device code of the pipeline kernels (colpass.cuh, rowpass.cuh, stages.cuh) for
+// column lengths N1 in {64, 80, 96} and rows of N2 = 256, so the arithmetic, the order of the
+// outputs and the results are the pipeline's own.
 //
 // The launch is cooperative (every CTA resident at once), so a CTA may wait for the others:
 // every barrier wait is bounded, and an expired one sets the timeout bit and lets the CTA go on.

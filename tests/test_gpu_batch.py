@@ -221,6 +221,35 @@ def test_served_mix_same_as_alone(d):
         assert d.dmul_wait(srv.handle, 10**9) == d.DMUL_ERR_UNKNOWN_TICKET
 
 
+def test_served_short_and_long_interleaved(d):
+    """Short requests (the one-cluster class, served by their own high-priority slots) and long
+    ones (the general slots), alternating in one burst and then trickled in one by one: every
+    result equals the oracle's, whichever queue and slot served it."""
+    short = wl.c4_jobs(24, 2.5, 4.5, 0.3, seed=71)
+    long_ = wl.c4_jobs(12, 5.4, 6.0, 0.3, seed=72)
+    jobs = []
+    for i in range(24):
+        jobs.append(short[i])
+        if i % 2 == 1:
+            jobs.append(long_[i // 2])
+    with d.Context(0) as srv:
+        dev = _prep(d, jobs)
+        arr = d.make_jobs(dev)
+        burst = [d.dmul_submit(srv.handle, arr[i]) for i in range(len(jobs))]
+        assert all(rc == 0 for rc, _ in burst)
+        assert all(d.dmul_wait(srv.handle, t) == 0 for _, t in burst)
+        _check(d, jobs, dev)
+        for _, _, _, _, z, _, nz in dev:
+            z.fill_(-1)
+            nz.zero_()
+        torch.cuda.synchronize()
+        for i in range(len(jobs)):  # one at a time, each waited for before the next
+            rc, t = d.dmul_submit(srv.handle, arr[i])
+            assert rc == 0 and d.dmul_wait(srv.handle, t) == 0
+        _check(d, jobs, dev)
+        assert d.dmul_serve_stats(srv.handle)["held"] == 0
+
+
 @pytest.mark.parametrize("half", [False, True], ids=["full_tiles", "half_tiles"])
 def test_batch_specialized_splits(d, half):
     """Medium jobs whose default splits take the specialized passes (N = 2^19: 512 x 1024, both

@@ -697,6 +697,42 @@ def test_plain_form_in_cuda_graph(d, ctx, n, m):
     assert d.dmul_sync(ctx.handle) == 0
 
 
+@pytest.mark.parametrize("form", ["square", "sixstep"])
+def test_graph_square_and_sixstep(d, ctx, ctx6, form):
+    """A captured squaring (one forward transform) and a captured six-step product (packing
+    transpose, row DFTs, in-place transposes, transposed CRT) replay exactly on new operands."""
+    c = ctx6 if form == "sixstep" else ctx
+    n, m = (70000, 70000) if form == "square" else (300000, 250001)
+    rng = _rng(13050 + n)
+    L = n + m
+    tx = d.to_device(_rand(rng, n))
+    ty = tx if form == "square" else d.to_device(_rand(rng, m))
+    z = torch.empty(L, dtype=torch.int32, device="cuda")
+    nz = torch.zeros(1, dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    call = (lambda: d.dmul_sqr(c.handle, tx, n, z, L, nz, s.cuda_stream)) if form == "square" else \
+        (lambda: d.dmul_mul(c.handle, tx, n, ty, m, z, L, nz, s.cuda_stream))
+    assert call() == 0
+    assert d.dmul_sync(c.handle, s.cuda_stream) == 0
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        rc = call()
+    assert rc == 0
+    for _ in range(2):
+        x = _rand(rng, n)
+        tx.copy_(d.to_device(x))
+        if form == "square":
+            y = x
+        else:
+            y = _rand(rng, m)
+            ty.copy_(d.to_device(y))
+        g.replay()
+        torch.cuda.synchronize()
+        ref = oracle.mul(x, y)
+        assert np.array_equal(d.to_host(z), ref) and int(nz.item()) == len(oracle.normalize(ref))
+    assert d.dmul_sync(c.handle) == 0
+
+
 def test_unplanned_length_refused_in_capture(d):
     """Inside a capture a product whose lengths this context has not planned is refused with
     DMUL_ERR_INVALID and enqueues nothing; the capture itself stays valid."""

@@ -161,7 +161,7 @@ def work_model(info, nx: int, ny: int, square: bool) -> dict:
 
 
 def _butterfly_mults(n: int) -> float:
-    """Modular products of the butterflies of one length-n transform in the survey's count:
+    """Modular products of the butterflies of one length-n transform in the scope table's count:
     (n/2) log2 n for n = 2^a; a radix-3 first pass (n = 3 2^a) adds 2n, a radix-5 one 1.2 n."""
     odd = 1
     while n % 2 == 0 and n > 1:
@@ -377,7 +377,7 @@ def run_ours(args, rank, world, local):
             "unit": "TIMAD/s", "frac": round(imad_t / imad_peak_t, 4), "traffic": None, "kernel": dom,
             "peak_source": "measured (dmul_probe_imad): independent 32-bit IMAD chains on every SM, "
                            f"best of {len(probes)}, SM clock median {pclk.get('sm_mhz')} MHz during the probe",
-            "count_model": "SURVEY 8(d): butterfly modmuls (n/2) log2 n per length-n transform + N "
+            "count_model": "hot-path scope table: butterfly modmuls (n/2) log2 n per length-n transform + N "
                            "twiddles (four-step) + N pointwise + 3 L CRT; Shoup = 3 IMAD, Montgomery = 4",
             "frac_per_survey_model": round(imad_t / imad_peak_t, 4),
             "kernel_imad_per_launch": k_imad,

@@ -172,7 +172,7 @@ def _butterfly_mults(n: int) -> float:
     return m / 2 * a + extra * m
 
 
-def survey_model(info, nx: int, ny: int, square: bool) -> dict:
+def scope_model(info, nx: int, ny: int, square: bool) -> dict:
     """Algorithmic work per kernel launch by the hot-path scope table's count: modular products of
     the transforms ((n/2) log2 n butterflies per length-n transform, N four-step twiddles per
     column pass), N pointwise Montgomery products, and the CRT's three products per coefficient;
@@ -337,7 +337,7 @@ def run_ours(args, rank, world, local):
     # ---- roofline of the dominant kernel and of the whole product ----
     info = d.dmul_get_plan(ctx.handle, L)
     model = work_model(info, nx, ny, False)
-    smodel = survey_model(info, nx, ny, False)
+    smodel = scope_model(info, nx, ny, False)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

@@ -88,8 +88,7 @@ def test_conv_coefficients_vs_definition_tiny():
 def test_conv_at_every_k_vs_schoolbook_and_double_loop():
     """One coefficient c_k = sum_{i+j=k} x_i y_j (Sec. 3.2), which the GPU tests compare sampled
     c_k with: at every k of several shapes against the schoolbook column sums, and on tiny shapes
-    against a Python
-    double loop.  Both the i-range bounds and both ends (k = 0, k = n+m-1, where c_k = 0) are hit."""
+    against a Python double loop.  Both the i-range bounds and both ends (k = 0, k = n+m-1, where c_k = 0) are hit."""
     rng = _rng(110)
     for n, m in ((1, 1), (3, 5), (5, 3), (7, 2), (300, 17), (17, 300), (1000, 1000)):
         x, y = _rand_limbs(rng, n), _rand_limbs(rng, m)

@@ -110,3 +110,39 @@ def test_sixstep_full_size(d, which):
         z, nz = _mul(d, c6, x, y)
     ref = oracle.mul_ntt(x, y)
     assert np.array_equal(z, ref) and nz == len(oracle.normalize(ref))
+
+
+def test_max_transform_length(d, ctx):
+    """The longest product the planner accepts: nx + ny = 3 * 2^22 limbs (113 million digits), the
+    largest transform.  Random operands against four residue fingerprints and 100 exact
+    convolution coefficients (after CRT) computed one by one by the oracle; the all-nines square
+    of the same length against the closed form; one limb more is refused."""
+    L = 3 * 2**22
+    n = L // 2
+    assert d.dmul_get_plan(ctx.handle, L).N == L
+    rng = np.random.Generator(np.random.PCG64(900))
+    x = rng.integers(0, B, n, dtype=np.uint64).astype(np.uint32)
+    y = rng.integers(0, B, n, dtype=np.uint64).astype(np.uint32)
+    x[-1] = max(1, int(x[-1]))
+    y[-1] = max(1, int(y[-1]))
+    z, nz = _mul(d, ctx, x, y)
+    for q in _moduli():
+        assert oracle.fingerprint(z, q) == oracle.fingerprint(x, q) * oracle.fingerprint(y, q) % q
+    assert nz == len(oracle.normalize(z)) and nz >= L - 1
+    dg = d.to_host(ctx.conv_coeffs(d.to_device(x), d.to_device(y))).reshape(-1, 3)
+    ks = sorted(set(int(k) for k in rng.integers(0, L, size=96)) | {0, 1, n - 1, n, L - 2, L - 1})
+    for k in ks:
+        got = int(dg[k, 0]) + int(dg[k, 1]) * B + int(dg[k, 2]) * B * B
+        assert got == oracle.conv_at(x, y, k), k
+    del dg
+    # (10^(9n) - 1)^2 = 10^(18n) - 2 10^(9n) + 1 for n limbs of nines
+    nines = np.full(n, B - 1, np.uint32)
+    z2, nz2 = _mul(d, ctx, nines, nines, square=True)
+    expect = np.zeros(2 * n, np.uint32)
+    expect[0] = 1
+    expect[n] = B - 2
+    expect[n + 1:] = B - 1
+    assert np.array_equal(z2, expect) and nz2 == 2 * n
+    t = d.to_device(np.ones(n + 1, np.uint32))
+    zz = torch.empty(L + 1, dtype=torch.int32, device="cuda")
+    assert d.dmul_mul(ctx.handle, t, n + 1, t, n, zz, L + 1, None) == d.DMUL_ERR_TOO_LARGE

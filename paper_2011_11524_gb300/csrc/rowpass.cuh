@@ -180,6 +180,27 @@ __device__ __forceinline__ void inv_stage_ct(const Stage &st, const uint2 *tw, u
     }
 }
 
+// Between the last forward stage (span 256), the center and the first inverse stage (span 256)
+// each thread reads only words that its own warp wrote: a group of those stages covers the 16
+// words j + 16u of one 256-word block, a center group 16 consecutive words, so the center group
+// b and the stage groups of its block, 16 b .. 16 b + 15, have indices in one 32-aligned range,
+// which the loops' common stride (the CTA size, a multiple of 32) hands to one warp.  A warp
+// barrier then orders these two hand-offs; a CPU check over every row length, rows per CTA and
+// CTA size found no word read across warps.  The unpaired forward form gives Y's groups to other
+// threads than X's (its operand loop runs past per_op), so products there keep the CTA barrier.
+#ifdef DMUL_ROW_UNPAIRED
+template <bool SQR>
+constexpr bool kCenterWarpLocal = SQR;
+#else
+template <bool SQR>
+constexpr bool kCenterWarpLocal = true;
+#endif
+template <bool SQR>
+__device__ __forceinline__ void center_barrier() {
+    if constexpr (kCenterWarpLocal<SQR>) __syncwarp();
+    else __syncthreads();
+}
+
 // forward stages 0 .. NS-2, then the center, then inverse stages NS-2 .. 0
 template <int PI, uint32_t N, int T, bool SQR>
 __device__ __forceinline__ void fwd_stages_ct(const PlanDev &pd, const uint2 *tw, uint32_t *sx,
@@ -194,7 +215,8 @@ __device__ __forceinline__ void fwd_stages_ct(const PlanDev &pd, const uint2 *tw
 #endif
             fwd_stage_ct<PI, S::radix(T), S::span(T), N>(pd.rs[T], tw, sx, sy, gx, gy, T == 0, SQR ? 1u : 2u,
                                                           rows);
-        __syncthreads();
+        if constexpr (T == S::NS - 2) center_barrier<SQR>();  // the center reads this warp's words
+        else __syncthreads();
         fwd_stages_ct<PI, N, T + 1, SQR>(pd, tw, sx, sy, gx, gy, rows);
     }
 }
@@ -246,7 +268,7 @@ __device__ __forceinline__ void row_core_ct(const PlanDev &pd, uint32_t *sx, uin
     fwd_stages_ct<PI, N, 0, SQR>(pd, tw, sx, sy, xin, yin, rows);
     static_assert(S::radix(S::NS - 1) == 16, "the center stage is radix 16");
     row_center_ct<PI, SQR>(sx, sy, rows * (N / 16));
-    __syncthreads();
+    center_barrier<SQR>();  // the first inverse stage reads this warp's words
     inv_stages_ct<PI, N, S::NS - 2>(pd, tw, sx, xout, rows);
 }
 

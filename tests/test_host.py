@@ -178,3 +178,34 @@ def test_probe64_primes_are_findprimes_63():
     """The prime-width probe's two 62-bit primes are FindPrimes(63, 23, 2) of Sec. 4.5, as the
     oracle's independent implementation finds them."""
     assert d.dmul_probe64_primes() == sorted(oracle.find_primes(63, 23, 2))
+
+
+def _pidx(a):
+    return a + (a >> 4)
+
+
+@pytest.mark.parametrize("N", [256, 512, 1024, 2048, 4096, 8192])
+def test_row_center_handoffs_stay_within_a_warp(N):
+    """The specialized row pass orders its last forward stage (span 256) -> center -> first inverse
+    stage (span 256) hand-offs with warp barriers only: every padded word a thread reads there was
+    written by its own warp.  Checked for every CTA size and rows per CTA the pass runs with, for
+    squares (X only) and products (X and Y groups on the same thread)."""
+    for rows in (1, 2, 4, 8, 16):
+        if rows * N > 65536:
+            continue
+        for bd in (128, 256, 512):
+            per_op = rows * (N // 16)
+            g = np.arange(per_op)
+            warp_of_g = (g % bd) // 32  # loop g = t, t + bd, ...: thread g mod bd
+            blk, j = g // 16, g % 16
+            # stage (span 256, radix 16): group g writes pidx(blk 256 + j + 16 u), u < 16
+            words = _pidx(blk[:, None] * 256 + j[:, None] + 16 * np.arange(16)[None, :])
+            writer = np.full(int(words.max()) + 1, -1)
+            writer[words.ravel()] = np.repeat(warp_of_g, 16)
+            # center: group b reads 17 b + u (X, and Y the same way), writes them
+            cw = (17 * g[:, None] + np.arange(16)[None, :])
+            assert (writer[cw] == warp_of_g[:, None]).all(), (N, rows, bd)
+            center_writer = np.full(int(cw.max()) + 1, -1)
+            center_writer[cw.ravel()] = np.repeat(warp_of_g, 16)
+            # first inverse stage (span 256): group g reads its stage words
+            assert (center_writer[words] == warp_of_g[:, None]).all(), (N, rows, bd)

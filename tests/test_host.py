@@ -35,6 +35,33 @@ def test_exports_every_declared_symbol():
     assert sorted(d.EXPORTS) == syms
 
 
+def test_header_is_c_and_links_from_c(tmp_path):
+    """include/dmul.h is a C ABI: a strict C99 program that includes it compiles without warnings
+    and links against libdmul.so (no torch or C++ types cross the boundary)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_dmul.c"
+    src.write_text('#include "dmul.h"\n'
+                   "int main(void) {\n"
+                   "    uint32_t p[3];\n"
+                   "    dmul_config cfg = {0};\n"
+                   "    (void)cfg;\n"
+                   "    return dmul_primes(p) == DMUL_OK && dmul_lambda(31, 3, 20) > 0 ? 0 : 1;\n"
+                   "}\n")
+    lib = dbuild.LIB
+    exe = tmp_path / "use_dmul"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I" + os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe), "-L" + os.path.dirname(lib), "-ldmul",
+                        "-Wl,-rpath," + os.path.dirname(lib)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    # host-only entry points: the program runs without a GPU
+    run = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert run.returncode == 0, run.stderr
+
+
 def test_primes_match_oracle_find_primes():
     """The GPU prime set is FindPrimes(w=31, n_min=23, l=3) (Sec. 4.5), as the oracle computes it."""
     lib_primes = d.dmul_primes()
